@@ -1,0 +1,221 @@
+"""ctypes wrappers of the FP64 C oracle (test infrastructure only).
+
+Every function takes and returns numpy float64 arrays; node arrays are
+(N, 3) projections x*, (N, 3) unit normals n(x*) and (N,) weights
+w = J delta_eps(d) h^3.  Vectors of the discrete system are [psi; psin]
+(length 2N).  Citations refer to sections/equations of the paper.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "Phys", "lib", "num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
+    "rhs", "psi_rxn", "gpol", "area", "sphere_nodes", "gmres", "KCAL_PER_E2_A",
+]
+
+# Coulomb constant in kcal mol^-1 Angstrom e^-2 times 4 pi: energies in the
+# paper's convention psi = q/(4 pi eps r) (Sec. 4.2) are converted to kcal/mol
+# by this factor (a reading: the paper does not print the conversion).
+KCAL_PER_E2_A = 4.0 * np.pi * 332.0637
+
+
+class _Phys(ctypes.Structure):
+    _fields_ = [("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
+                ("tube_rule", ctypes.c_int)]
+
+
+class Phys:
+    """Physical and regularisation parameters (Sec. 2.1, Sec. 2.2.1)."""
+
+    def __init__(self, eps_in=1.0, eps_out=80.0, kappa=0.1257, tau=0.25, tube_rule=0):
+        self.eps_in, self.eps_out, self.kappa, self.tau, self.tube_rule = (
+            float(eps_in), float(eps_out), float(kappa), float(tau), int(tube_rule))
+
+    def c(self):
+        return _Phys(self.eps_in, self.eps_out, self.kappa, self.tau, self.tube_rule)
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_P = ctypes.POINTER(_Phys)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_delta_eps.restype = ctypes.c_double
+        L.orc_delta_eps.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_pair_kernels.restype = ctypes.c_int
+        L.orc_pair_kernels.argtypes = [_D, _D, _D, _D, _P, _D]
+        L.orc_matvec.restype = None
+        L.orc_matvec.argtypes = [ctypes.c_int64, _D, _D, _D, _P, _D, _D]
+        L.orc_matvec_rows.restype = None
+        L.orc_matvec_rows.argtypes = [ctypes.c_int64, _D, _D, _D, _P, _D, ctypes.c_int64, _I64, _D]
+        L.orc_dense.restype = None
+        L.orc_dense.argtypes = [ctypes.c_int64, _D, _D, _D, _P, _D]
+        L.orc_rhs.restype = None
+        L.orc_rhs.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_int64, _D, _D, ctypes.c_double, _D]
+        L.orc_psi_rxn.restype = None
+        L.orc_psi_rxn.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int64, _D, _P, _D, _D]
+        L.orc_gpol.restype = ctypes.c_double
+        L.orc_gpol.argtypes = [ctypes.c_int64, _D, _D]
+        L.orc_area.restype = ctypes.c_double
+        L.orc_area.argtypes = [ctypes.c_int64, _D]
+        L.orc_sphere_nodes.restype = ctypes.c_int64
+        L.orc_sphere_nodes.argtypes = [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int64, _D, _D, _D, _D, _I32]
+        L.orc_gmres.restype = ctypes.c_int
+        L.orc_gmres.argtypes = [ctypes.c_int64, _D, _D, _D, _P, _D, _D, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def delta_eps(eta, eps):
+    """Cosine weight of Sec. 3.2."""
+    return lib().orc_delta_eps(float(eta), float(eps))
+
+
+def pair_kernels(x, nx, y, ny, phys):
+    """(K11, K12, K21, K22), in_tube for one pair (Sec. 2.2, Sec. 2.2.1)."""
+    K = np.zeros(4)
+    P = phys.c()
+    t = lib().orc_pair_kernels(_d(_f64(x, 3)), _d(_f64(nx, 3)), _d(_f64(y, 3)), _d(_f64(ny, 3)),
+                               ctypes.byref(P), _d(K))
+    return K, bool(t)
+
+
+def _geom(xs, nrm, w):
+    xs = _f64(xs, (-1, 3))
+    nrm = _f64(nrm, (-1, 3))
+    w = _f64(w, -1)
+    assert xs.shape[0] == nrm.shape[0] == w.shape[0]
+    return xs, nrm, w
+
+
+def matvec(xs, nrm, w, phys, p):
+    """(Lambda + K W) p, Sec. 2.2 discrete system / Sec. 3.3."""
+    xs, nrm, w = _geom(xs, nrm, w)
+    N = w.shape[0]
+    p = _f64(p, 2 * N)
+    y = np.empty(2 * N)
+    P = phys.c()
+    lib().orc_matvec(N, _d(xs), _d(nrm), _d(w), ctypes.byref(P), _d(p), _d(y))
+    return y
+
+
+def matvec_rows(xs, nrm, w, phys, p, rows):
+    """Rows `rows` of (Lambda + K W) p; returns (y1[rows], y2[rows])."""
+    xs, nrm, w = _geom(xs, nrm, w)
+    N = w.shape[0]
+    p = _f64(p, 2 * N)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(2 * rows.shape[0])
+    P = phys.c()
+    lib().orc_matvec_rows(N, _d(xs), _d(nrm), _d(w), ctypes.byref(P), _d(p), rows.shape[0],
+                          rows.ctypes.data_as(_I64), _d(out))
+    return out[0::2].copy(), out[1::2].copy()
+
+
+def dense(xs, nrm, w, phys):
+    """Dense 2N x 2N matrix Lambda + K W (for brute force on tiny inputs)."""
+    xs, nrm, w = _geom(xs, nrm, w)
+    N = w.shape[0]
+    A = np.empty((2 * N, 2 * N))
+    P = phys.c()
+    lib().orc_dense(N, _d(xs), _d(nrm), _d(w), ctypes.byref(P), _d(A))
+    return A
+
+
+def rhs(xs, nrm, z, q, eps_in):
+    """g = [g1; g2] of Sec. 2.2."""
+    xs = _f64(xs, (-1, 3))
+    nrm = _f64(nrm, (-1, 3))
+    z = _f64(z, (-1, 3))
+    q = _f64(q, -1)
+    N = xs.shape[0]
+    g = np.empty(2 * N)
+    lib().orc_rhs(N, _d(xs), _d(nrm), z.shape[0], _d(z), _d(q), float(eps_in), _d(g))
+    return g
+
+
+def psi_rxn(xs, nrm, w, z, phys, p):
+    """Reaction potential at each charge centre (Sec. 3.5)."""
+    xs, nrm, w = _geom(xs, nrm, w)
+    z = _f64(z, (-1, 3))
+    N = w.shape[0]
+    p = _f64(p, 2 * N)
+    out = np.empty(z.shape[0])
+    P = phys.c()
+    lib().orc_psi_rxn(N, _d(xs), _d(nrm), _d(w), z.shape[0], _d(z), ctypes.byref(P), _d(p), _d(out))
+    return out
+
+
+def gpol(q, psi):
+    """G_pol = 1/2 sum q_k psi_rxn(z_k) in e^2/Angstrom (Sec. 3.5)."""
+    q = _f64(q, -1)
+    psi = _f64(psi, -1)
+    return lib().orc_gpol(q.shape[0], _d(q), _d(psi))
+
+
+def area(w):
+    """Surface area, the IBIM sum of f = 1 (Sec. 3.4)."""
+    w = _f64(w, -1)
+    return lib().orc_area(w.shape[0], _d(w))
+
+
+def sphere_nodes(R, centre=(0.0, 0.0, 0.0), h=0.25, eps=0.75, origin=(0.0, 0.0, 0.0)):
+    """Band nodes of an analytic sphere; dict of xs, nrm, w, d, ijk (lexicographic, x fastest)."""
+    c = _f64(centre, 3)
+    o = _f64(origin, 3)
+    L = lib()
+    n = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), 0, None, None, None, None, None)
+    xs = np.empty((n, 3))
+    nrm = np.empty((n, 3))
+    w = np.empty(n)
+    d = np.empty(n)
+    ijk = np.empty((n, 3), dtype=np.int32)
+    n2 = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), n, _d(xs), _d(nrm), _d(w),
+                            _d(d), ijk.ctypes.data_as(_I32))
+    assert n2 == n
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk}
+
+
+def gmres(xs, nrm, w, phys, g, x0=None, tol=1e-8, restart=100, maxit=500):
+    """Restarted GMRES(m), MGS, FP64 (Sec. 3.3).  Returns (x, iters, true_relres, converged)."""
+    xs, nrm, w = _geom(xs, nrm, w)
+    N = w.shape[0]
+    g = _f64(g, 2 * N)
+    x = np.zeros(2 * N) if x0 is None else _f64(x0, 2 * N).copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    P = phys.c()
+    rc = lib().orc_gmres(N, _d(xs), _d(nrm), _d(w), ctypes.byref(P), _d(g), _d(x), float(tol),
+                         int(restart), int(maxit), ctypes.byref(it), ctypes.byref(rr))
+    return x, it.value, rr.value, rc == 0

@@ -1,0 +1,118 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and the benchmark.
+
+This module holds no arithmetic of the method itself: it only draws random
+numbers (charge positions and values, atom chains, node clouds, vectors) with
+numpy's seeded generators.  Everything the method computes from these inputs
+is done separately by the CUDA library and by the oracle.
+"""
+import numpy as np
+
+# Seeds of the five standard workloads (Born sphere, Kirkwood sphere, 2,000-atom
+# globule, batch of 64 globules, learned warm start), one per workload.
+SEED_BORN = 1709080701
+SEED_KIRKWOOD = 1709080702
+SEED_PROTEIN = 1709080703
+SEED_BATCH = 1709080704
+SEED_LEARNED = 1709080705
+
+
+def kirkwood_charges(n=50, ball_radius=16.0, seed=SEED_KIRKWOOD):
+    """n charges of +-1 (random signs) uniform in a ball of the given radius."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = ball_radius * rng.random(n) ** (1.0 / 3.0)
+    z = u * r[:, None]
+    q = rng.choice([-1.0, 1.0], size=n)
+    return z, q
+
+
+def random_vector(n, seed=0, scale=1.0):
+    """Gaussian test vector of length n."""
+    return scale * np.random.default_rng(seed).standard_normal(n)
+
+
+def random_rows(n_total, n_rows, seed=0):
+    """Sorted distinct row indices for sampled checks."""
+    rng = np.random.default_rng(seed)
+    n_rows = min(n_rows, n_total)
+    return np.sort(rng.choice(n_total, size=n_rows, replace=False)).astype(np.int64)
+
+
+def sphere_cloud(n, radius=10.0, jitter=0.0, seed=0, weight_range=(0.01, 0.06)):
+    """A node cloud for operator checks on caller-given geometry: n points
+    uniformly on a sphere (optionally jittered radially), outward unit normals,
+    positive random weights.  Points are ordered by a coarse spatial key so
+    that neighbouring indices are close in space."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = radius + jitter * rng.standard_normal(n)
+    xs = u * r[:, None]
+    w = rng.uniform(weight_range[0], weight_range[1], size=n)
+    key = np.lexsort((np.floor(u[:, 0] * 8), np.floor(u[:, 1] * 8), np.floor(u[:, 2] * 8)))
+    return xs[key], u[key], w[key]
+
+
+def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, vol_per_atom=20.0,
+                  radius_range=(1.2, 1.9), charge_range=(-0.8, 0.8), max_tries=200):
+    """Seeded self-avoiding random-walk chain confined to a ball (a compact
+    globule): step `step` A, non-bonded distances >= `min_dist` A, ball volume
+    n_atoms * vol_per_atom A^3.  Radii uniform in `radius_range`; partial
+    charges uniform in `charge_range` shifted to a net charge of zero.
+    Returns (centres (n,3), radii (n,), charges (n,))."""
+    rng = np.random.default_rng(seed)
+    R_ball = (3.0 * n_atoms * vol_per_atom / (4.0 * np.pi)) ** (1.0 / 3.0)
+    cell = min_dist
+    for _attempt in range(max_tries):
+        pos = np.zeros((n_atoms, 3))
+        grid = {}
+
+        def key(p):
+            return tuple(np.floor(p / cell).astype(np.int64))
+
+        def ok(p, upto):
+            k = key(p)
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for idx in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                            if idx == upto - 1:
+                                continue
+                            if np.sum((pos[idx] - p) ** 2) < min_dist * min_dist:
+                                return False
+            return True
+
+        pos[0] = 0.0
+        grid.setdefault(key(pos[0]), []).append(0)
+        good = True
+        for i in range(1, n_atoms):
+            placed = False
+            for _t in range(64):
+                d = rng.standard_normal(3)
+                d /= np.linalg.norm(d)
+                p = pos[i - 1] + step * d
+                if np.linalg.norm(p) > R_ball:
+                    continue
+                if ok(p, i):
+                    pos[i] = p
+                    grid.setdefault(key(p), []).append(i)
+                    placed = True
+                    break
+            if not placed:
+                good = False
+                break
+        if good:
+            radii = rng.uniform(radius_range[0], radius_range[1], size=n_atoms)
+            q = rng.uniform(charge_range[0], charge_range[1], size=n_atoms)
+            q -= q.mean()
+            return pos - pos.mean(axis=0), radii, q
+    raise RuntimeError("self-avoiding walk failed after %d restarts" % max_tries)
+
+
+def batch_sizes(n_mol=64, lo=50, hi=3000, seed=SEED_BATCH):
+    """Atom counts log-uniform in [lo, hi] and screening constants kappa ~ U[0, 0.2]."""
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_mol)).round().astype(int)
+    kappa = rng.uniform(0.0, 0.2, size=n_mol)
+    return n, kappa
