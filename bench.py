@@ -1,0 +1,329 @@
+"""Benchmark of the IBIM hot path on GB300.
+
+Step = one full solve of the Kirkwood-sphere workload (radius 20 A, 50 seeded
++-1 charges, eps_I = 2, eps_E = 80, kappa = 0.1257, h = 0.5 A, band 2h,
+tau = h, about 80k nodes): right-hand side, restarted GMRES to a 1e-6
+relative residual with the FP32 compensated pair-sum operator and FP64
+Arnoldi/Givens on the device, then G_pol and area.  The metric is operator
+(matvec) interactions per second over the whole step; each interaction is one
+(target, source) pair with all four kernels evaluated.
+
+Also reported once per run (outside the timed steps): the same solve with an
+FP64-certified residual, the plain FP64 GPU solve it is compared with, and
+the FP64 oracle timed on the host cores on a bounded sample of operator rows.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the workload does not
+shard), value = interactions of all ranks / max rank time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "kirkwood_sphere", "R": 20.0, "h": 0.5, "band_k": 2, "tau_k": 1.0, "n_charges": 50,
+            "charge_ball": 16.0, "eps_in": 2.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64}
+# FP32-pipe (FFMA/FMUL/FADD) instructions per interaction of the compensated
+# pair kernel, counted from its source: geometry 16, kernel values 25,
+# two Kahan-compensated accumulations 8.
+F32_OPS_PER_INTERACTION = 49
+FP32_LANES_PER_SM = 128
+METRIC = "IBIM matvec interactions/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                smax.append(float(v[2]))
+                power.append(float(v[3]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        busy = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _kirkwood_inputs():
+    from paper_1709_08070_gb300 import inputs
+    W = WORKLOAD
+    z, q = inputs.kirkwood_charges(W["n_charges"], W["charge_ball"])
+    return z, q
+
+
+def cpu_oracle_rate(target_s=10.0, max_rows=None):
+    """FP64 oracle operator rows on the host cores, bounded sample: returns
+    (interactions/s, threads, sample description, elapsed)."""
+    import oracle
+    from paper_1709_08070_gb300 import inputs
+    W = WORKLOAD
+    g = oracle.sphere_nodes(W["R"], h=W["h"], eps=W["band_k"] * W["h"])
+    N = g["w"].size
+    P = oracle.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * W["h"], 0)
+    p = inputs.random_vector(2 * N, seed=3)
+    rows = inputs.random_rows(N, 256, seed=4)
+    t0 = time.perf_counter()
+    oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
+    dt = time.perf_counter() - t0
+    nrows = int(min(N, max(256, 256 * target_s / max(dt, 1e-3))))
+    if max_rows:
+        nrows = min(nrows, max_rows)
+    rows = inputs.random_rows(N, nrows, seed=5)
+    t0 = time.perf_counter()
+    oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
+    dt = time.perf_counter() - t0
+    return nrows * N / dt, oracle.num_threads(), "%d of %d operator rows of the %d-node workload (%d interactions)" % (
+        nrows, N, N, nrows * N), dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    vals = []
+    desc, cores = "", 0
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        v, cores, desc, dt = cpu_oracle_rate(target_s=per_step)
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = float(np.mean([v for v, _ in vals]))
+    ms = float(np.mean([dt for _, dt in vals]) * 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="n/a (host)"),
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_08070_gb300 import ibim
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    W = WORKLOAD
+    z, q = _kirkwood_inputs()
+    h = W["h"]
+    stream = torch.cuda.current_stream()
+    ctx = ibim.Context.sphere(W["R"], h=h, band_eps=W["band_k"] * h)
+    ctx.set_charges(z, q)
+    N = ctx.N
+    P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
+    opts = dict(precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=1000, start=0, certify=0)
+    dp = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.solve(P, dp, **opts)
+    ctx.timing_enable(True)
+    ctx.timing_reset()
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        infos.append(ctx.solve(P, dp, **opts))
+        ev[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tim = ctx.timing()
+    ctx.timing_enable(False)
+    total_ms = float(sum(step_ms))
+    interactions = sum(int(i["matvecs_f32"] + i["matvecs_f64"]) for i in infos) * N * N
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([float(interactions)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        interactions_all = float(c.item())
+    else:
+        interactions_all = float(interactions)
+    value = interactions_all / (total_ms * 1e-3)
+
+    # ---- dominant kernel roofline (pair_f32_kernel), live CUDA-event timing
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    avg_pair_ms = tim["pair_ms"] / max(1, tim["pair_launches"])
+    per_launch = tim["pair_interactions"] / max(1, tim["pair_launches"])
+    achieved_ops = F32_OPS_PER_INTERACTION * per_launch / (avg_pair_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": achieved_ops / peak_ops, "traffic": None,
+                "kernel": "pair_f32_kernel", "ops_per_interaction": F32_OPS_PER_INTERACTION,
+                "interactions_per_launch": per_launch, "avg_launch_ms": avg_pair_ms,
+                "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock, measured peaks file)" % (
+                    props.multi_processor_count, FP32_LANES_PER_SM, sm_max)}
+    if ck.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved_ops / (peak_ops * ck["sm_mhz"] / sm_max)
+
+    extra = {}
+    if rank == 0:
+        # ---- e2e through the C ABI with host buffers (pinned), per step
+        zp = torch.from_numpy(np.ascontiguousarray(z)).pin_memory()
+        qp = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
+        hp = torch.empty(2 * N, dtype=torch.float64).pin_memory()
+        e2e_ms, e2e_inter = [], 0
+        for i in range(max(3, args.steps)):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf = ctx.solve_host(P, zp.numpy(), qp.numpy(), hp.numpy(), **opts)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_inter += int(inf["matvecs_f32"] + inf["matvecs_f64"]) * N * N
+        e2e = {"value": e2e_inter / (sum(e2e_ms) * 1e-3), "unit": "interactions/s",
+               "h2d_bytes_per_step": int(zp.numel() * 8 + qp.numel() * 8),
+               "d2h_bytes_per_step": int(hp.numel() * 8 + 8)}
+        # ---- time to 1e-6 residual: certified FP32 path vs plain FP64 GPU solve
+        t0 = time.perf_counter()
+        icert = ctx.solve(P, dp, **dict(opts, certify=1))
+        torch.cuda.synchronize()
+        cert_ms = (time.perf_counter() - t0) * 1e3
+        fp64 = None
+        if not args.skip_fp64:
+            t0 = time.perf_counter()
+            d64 = torch.empty_like(dp)
+            i64 = ctx.solve(P, d64, **dict(opts, precision=ibim.IBIM_F64))
+            torch.cuda.synchronize()
+            fp64_ms = (time.perf_counter() - t0) * 1e3
+            fp64 = {"ms": fp64_ms, "iters": i64["iters"], "relres": i64["relres"], "gpol_kcal": i64["gpol_kcal"]}
+        from oracle import closed_forms as cf
+        Gs = cf.kirkwood_energy(W["R"], z, q, W["eps_in"], W["eps_out"], W["kappa"]) * ibim.KCAL_PER_E2_A
+        extra = {"time_to_residual": {
+            "tol": W["tol"], "f32_step_ms": total_ms / args.steps, "f32_iters": infos[-1]["iters"],
+            "f32_certified_ms": cert_ms, "f32_certified_relres_f64": icert["relres"],
+            "f32_certified_iters": icert["iters"], "f64_plain": fp64,
+            "speedup_certified_vs_f64": (fp64["ms"] / cert_ms) if fp64 else None,
+            "speedup_uncertified_vs_f64": (fp64["ms"] / (total_ms / args.steps)) if fp64 else None},
+            "energy": {"gpol_kcal_f32": infos[-1]["gpol_kcal"], "gpol_kcal_f64": fp64["gpol_kcal"] if fp64 else None,
+                       "kirkwood_series_kcal": Gs,
+                       "rel_err_f32_vs_f64": abs(infos[-1]["gpol_kcal"] - fp64["gpol_kcal"]) / abs(fp64["gpol_kcal"])
+                       if fp64 else None,
+                       "rel_err_vs_series": abs(infos[-1]["gpol_kcal"] - Gs) / abs(Gs)}}
+        if not args.skip_cpu:
+            v, cores, desc, _ = cpu_oracle_rate(target_s=args.cpu_seconds)
+            extra["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                                     "sample": desc}
+        extra["e2e"] = e2e
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
+                               l2="256 MB buffer written between timed steps"),
+                "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
+                "wall_s_timed": wall}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

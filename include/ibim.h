@@ -1,0 +1,206 @@
+/*
+ * ibim.h -- C ABI of the GB300 (sm_103a) implementation of the implicit
+ * boundary integral method (IBIM) for the linearized Poisson-Boltzmann
+ * equation (Zhong, Ren, Tsai, arXiv 1709.08070).
+ *
+ * Conventions shared by every entry point
+ *   - Lengths in Angstrom, charges in units of e.  Potentials follow the
+ *     paper's psi = q / (4 pi eps r) convention (Sec. 4.2); energies are
+ *     returned in e^2/Angstrom and, where stated, in kcal/mol
+ *     (x 4 pi 332.0637).
+ *   - The unknown of the discrete system (Sec. 2.2, Sec. 3.3) is the 2N vector
+ *     p = [psi_bar(0..N-1); psin_bar(0..N-1)] of FP64 values, where psin is
+ *     the interior-side normal derivative (Sec. 2.1).  Node j carries its
+ *     projection x*_j, unit normal n(x*_j) and weight w_j = J delta_eps(d_j) h^3.
+ *   - Pointers named d_* are device pointers on the context's device;
+ *     pointers named h_* (or plain host arrays) are host memory.  Caller
+ *     arrays are borrowed for the duration of the call only; the context owns
+ *     every buffer it allocates and frees them in ibim_destroy.
+ *   - All GPU work of a context is issued on the CUDA stream given at build
+ *     time (a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream).  Calls returning host values synchronise that stream.
+ *   - No entry point throws, exits or traps.  Each returns an ibim_status;
+ *     ibim_last_error() gives a message for the last failure on the calling
+ *     thread.  A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef IBIM_H
+#define IBIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibim_ctx ibim_ctx;
+
+typedef enum {
+    IBIM_OK = 0,
+    IBIM_ERR_ARG = 1,            /* invalid argument (NULL, size, parameter range) */
+    IBIM_ERR_EMPTY_BAND = 2,     /* the narrowband holds no grid node */
+    IBIM_ERR_NONFINITE = 3,      /* NaN/Inf in an input */
+    IBIM_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has details) */
+    IBIM_ERR_NOT_CONVERGED = 5,  /* GMRES spent maxit iterations above tolerance */
+    IBIM_ERR_DEVICE_TIMEOUT = 6, /* a bounded device-side wait gave up */
+    IBIM_ERR_STATE = 7           /* call not valid in the context's state (e.g. no charges) */
+} ibim_status;
+
+/* Arithmetic of the pair sums (the N x N kernel evaluations). */
+typedef enum {
+    IBIM_F64 = 64,  /* plain FP64 pair sums */
+    IBIM_F32C = 32  /* FP32 pair sums, Kahan-compensated per source tile, tile sums in FP64 */
+} ibim_precision;
+
+/*
+ * Physical and regularisation parameters.
+ *   eps_in, eps_out : dielectric constants eps_I, eps_E (> 0), Sec. 1.
+ *   kappa           : screening constant kappa >= 0 (1/Angstrom), used directly
+ *                     in G_kappa = exp(-kappa r)/(4 pi r), Sec. 2.1.
+ *   tau             : regularisation radius (> 0, Angstrom), Sec. 2.2.1.
+ *   tube_rule       : 0 = a pair is regularised iff its tangent-plane distance
+ *                     ||x*-y*||_P < tau and |x*-y*| < 2 tau; 1 = the tangent-plane
+ *                     test alone, as printed in Sec. 2.2.1.
+ * Inside the tube K11 = K21 = K22 = 0 and
+ * K12 = (exp(-kappa tau) - 1 + kappa tau)/(2 pi kappa tau^2) (0 at kappa = 0).
+ */
+typedef struct {
+    double eps_in;
+    double eps_out;
+    double kappa;
+    double tau;
+    int tube_rule;
+} ibim_phys;
+
+/* ------------------------------------------------------------------ build */
+
+/*
+ * Narrowband of an analytic sphere (signed distance d(x) = |x - c| - R),
+ * Sec. 2.2 and Sec. 3.2 with J = 1.  Grid U_h = origin + h Z^3; nodes with
+ * |d| < band_eps are kept, x* = c + R (x - c)/|x - c|, n = (x - c)/|x - c|,
+ * w = delta_eps(d) h^3 (cosine weight).  Nodes are stored in Morton order of
+ * their grid coordinates (use ibim_get_nodes for the coordinates).
+ *   R > 0, h > 0, band_eps > 0; centre/origin: host double[3] (origin may be NULL = 0).
+ * Errors: IBIM_ERR_ARG, IBIM_ERR_EMPTY_BAND, IBIM_ERR_CUDA.
+ */
+ibim_status ibim_build_sphere(double R, const double* centre, const double* origin, double h,
+                              double band_eps, void* stream, ibim_ctx** out);
+
+/*
+ * Context from caller-given nodes (host arrays, copied): x* (N x 3, row-major),
+ * unit normals (N x 3), weights w (N).  h is informational (> 0).  Nodes keep
+ * the caller's order.  Errors: IBIM_ERR_ARG (N <= 0, NULL), IBIM_ERR_NONFINITE.
+ */
+ibim_status ibim_build_from_nodes(int64_t N, const double* xstar, const double* normal,
+                                  const double* w, double h, void* stream, ibim_ctx** out);
+
+/* Point charges z_k (Nc x 3 host, row-major) and q_k (Nc host) used by the
+ * right-hand side and the energy; replaces earlier charges.  Nc >= 1. */
+ibim_status ibim_set_charges(ibim_ctx* ctx, int64_t Nc, const double* z, const double* q);
+
+ibim_status ibim_num_nodes(const ibim_ctx* ctx, int64_t* N);
+
+/* Host copies of the node data in the context's order; any pointer may be NULL.
+ * xstar, normal: N x 3; w, d: N; ijk: N x 3 grid coordinates (int32; all -1 for
+ * caller-given nodes); d is the signed distance (0 for caller-given nodes). */
+ibim_status ibim_get_nodes(const ibim_ctx* ctx, double* xstar, double* normal, double* w,
+                           double* d, int32_t* ijk);
+
+/* ----------------------------------------------------------- operator etc. */
+
+/*
+ * d_out = (Lambda + K W) d_in, the discrete system of Sec. 2.2 / final linear
+ * system of Sec. 3.3, with Lambda = diag((1+eps_E/eps_I)/2 I, (1+eps_I/eps_E)/2 I)
+ * and the regularised kernels of Sec. 2.2.1:
+ *   y1_i = lambda1 psi_i  + sum_j [K11(i,j) w_j psi_j - K12(i,j) w_j psin_j]
+ *   y2_i = lambda2 psin_i + sum_j [K21(i,j) w_j psi_j - K22(i,j) w_j psin_j]
+ * d_in, d_out: device, 2N doubles each, must not overlap.  Asynchronous on
+ * the context stream.  precision: IBIM_F64 or IBIM_F32C.
+ */
+ibim_status ibim_matvec(ibim_ctx* ctx, const ibim_phys* phys, int precision, const double* d_in,
+                        double* d_out);
+
+/* Same product with host buffers (copies in, computes, copies out, synchronises). */
+ibim_status ibim_matvec_host(ibim_ctx* ctx, const ibim_phys* phys, int precision,
+                             const double* h_in, double* h_out);
+
+/* Right-hand side g = [g1; g2] (Sec. 2.2): g1_i = sum_k q_k/eps_I G0(x*_i, z_k),
+ * g2_i = sum_k q_k/eps_I dG0(x*_i, z_k)/dn(x*_i).  d_g: device, 2N doubles.
+ * Needs charges (IBIM_ERR_STATE otherwise). */
+ibim_status ibim_rhs(ibim_ctx* ctx, double eps_in, double* d_g);
+
+/*
+ * Reaction potential psi_rxn(z_k) (Sec. 3.5, IBIM sum over the band nodes) and
+ * G_pol = 1/2 sum_k q_k psi_rxn(z_k).  d_p: device 2N solution; d_psi_rxn:
+ * device Nc doubles or NULL; gpol: host, e^2/Angstrom.  Synchronises.
+ */
+ibim_status ibim_energy(ibim_ctx* ctx, const ibim_phys* phys, int precision, const double* d_p,
+                        double* d_psi_rxn, double* gpol);
+
+/* Surface area sum_j w_j (Sec. 3.4, f = 1).  Synchronises. */
+ibim_status ibim_area(ibim_ctx* ctx, double* area);
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+    int precision;  /* IBIM_F64 or IBIM_F32C: operator used inside GMRES                */
+    double tol;     /* relative residual ||g - A p||_2 / ||g||_2 target (e.g. 1e-6)      */
+    int maxit;      /* maximum Arnoldi steps in total                                    */
+    int restart;    /* GMRES restart length m (1..128)                                   */
+    int start;      /* 0: p0 = 0; 1: p0 = Lambda^-1 g (Sec. 3.3); 3: caller's d_p on entry */
+    int certify;    /* 1: after convergence recompute the residual with the FP64
+                       operator and restart from the current p while it is above tol
+                       (iterative refinement); 0: residuals use the chosen operator   */
+} ibim_solve_opts;
+
+typedef struct {
+    int iters;           /* Arnoldi steps taken (the paper's GMRES iteration count)     */
+    int cycles;          /* GMRES cycles (restarts + refinement passes)                 */
+    int converged;       /* 1 when the reported residual is below tol                   */
+    double relres;       /* final ||g - A p|| / ||g|| (FP64 operator when certify = 1)  */
+    double gpol;         /* G_pol, e^2/Angstrom                                          */
+    double gpol_kcal;    /* G_pol, kcal/mol                                              */
+    double area;         /* surface area (Angstrom^2)                                    */
+    int64_t matvecs_f32; /* operator applications by precision                           */
+    int64_t matvecs_f64;
+} ibim_solve_info;
+
+/*
+ * Solve (Lambda + K W) p = g by restarted GMRES (Sec. 3.3) with FP64 Arnoldi
+ * (classical Gram-Schmidt with one re-orthogonalisation), FP64 Givens
+ * least squares on the device and the operator of opts->precision, then
+ * evaluate G_pol (Sec. 3.5) and the area (Sec. 3.4).  Each Arnoldi step runs
+ * as one CUDA graph replay with no host synchronisation inside the step.
+ * d_p: device 2N doubles; start vector on entry when opts->start == 3,
+ * solution [psi; psin] on exit.  Needs charges.  Returns IBIM_ERR_NOT_CONVERGED
+ * (info filled) when maxit is reached above tol.
+ */
+ibim_status ibim_solve(ibim_ctx* ctx, const ibim_phys* phys, const ibim_solve_opts* opts,
+                       double* d_p, ibim_solve_info* info);
+
+/* ibim_solve with host buffers: charges (Nc x 3, Nc) are uploaded first, the
+ * solution is copied back into h_p (2N doubles) when h_p is not NULL. */
+ibim_status ibim_solve_host(ibim_ctx* ctx, const ibim_phys* phys, const ibim_solve_opts* opts,
+                            int64_t Nc, const double* z, const double* q, double* h_p,
+                            ibim_solve_info* info);
+
+/* ----------------------------------------------------------- diagnostics */
+
+/*
+ * Kernel timing: when enabled, the pair-sum kernel launches of this context
+ * are bracketed by CUDA events on the context stream.  ibim_timing_get returns
+ * the summed event time (ms), the number of pair-kernel launches, the pair
+ * interactions they evaluated and the total number of kernels this context
+ * launched since the last reset.  Reading synchronises.
+ */
+ibim_status ibim_timing_enable(ibim_ctx* ctx, int enable);
+ibim_status ibim_timing_reset(ibim_ctx* ctx);
+ibim_status ibim_timing_get(ibim_ctx* ctx, double* pair_ms, int64_t* pair_launches,
+                            int64_t* pair_interactions, int64_t* total_launches);
+
+const char* ibim_last_error(void);
+void ibim_destroy(ibim_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBIM_H */

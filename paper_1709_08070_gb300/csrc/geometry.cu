@@ -1,0 +1,208 @@
+// Narrowband geometry on the GPU (Sec. 2.2, Sec. 3.2): band extraction
+// {|d| < eps} over the Cartesian grid, closest-point projection
+// x* = x - d grad d, unit normals and weights w = J delta_eps(d) h^3 (J = 1,
+// cosine weight).  Grid nodes are enumerated in Morton (Z-curve) order of
+// their box-local coordinates, so consecutive nodes are close in space; the
+// compaction keeps that order (block counts, one scan, ordered writes).
+#include <math.h>
+
+#include <vector>
+
+#include "ibim_internal.cuh"
+
+namespace ibim {
+
+__host__ __device__ __forceinline__ uint32_t compact1by2(uint64_t v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return (uint32_t)v;
+}
+
+struct SphereBox {
+    int64_t lo[3];
+    int64_t n[3];
+    double c[3], o[3];
+    double R, h, eps;
+};
+
+// Band test for one Morton code; returns true and fills the node when kept.
+__device__ __forceinline__ bool sphere_node(const SphereBox& B, uint64_t code, double* x, double* nrm,
+                                            double* d, int32_t* ijk)
+{
+    const uint32_t a = compact1by2(code), b = compact1by2(code >> 1), cc = compact1by2(code >> 2);
+    if (a >= B.n[0] || b >= B.n[1] || cc >= B.n[2]) return false;
+    const int64_t gi = B.lo[0] + a, gj = B.lo[1] + b, gk = B.lo[2] + cc;
+    const double p0 = B.o[0] + B.h * (double)gi, p1 = B.o[1] + B.h * (double)gj, p2 = B.o[2] + B.h * (double)gk;
+    const double v0 = p0 - B.c[0], v1 = p1 - B.c[1], v2 = p2 - B.c[2];
+    const double len = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    const double dd = len - B.R;  // signed distance, negative inside
+    if (!(fabs(dd) < B.eps) || len == 0.0) return false;
+    nrm[0] = v0 / len;
+    nrm[1] = v1 / len;
+    nrm[2] = v2 / len;
+    x[0] = p0 - dd * nrm[0];
+    x[1] = p1 - dd * nrm[1];
+    x[2] = p2 - dd * nrm[2];
+    *d = dd;
+    ijk[0] = (int32_t)gi;
+    ijk[1] = (int32_t)gj;
+    ijk[2] = (int32_t)gk;
+    return true;
+}
+
+constexpr int kCompactBlock = 1024;
+
+__global__ void sphere_count_kernel(SphereBox B, uint64_t ncodes, int* __restrict__ counts)
+{
+    const uint64_t code = (uint64_t)blockIdx.x * kCompactBlock + threadIdx.x;
+    double x[3], n[3], d;
+    int32_t ijk[3];
+    const bool keep = code < ncodes && sphere_node(B, code, x, n, &d, ijk);
+    const int c = __syncthreads_count(keep);
+    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of the block counts in one CTA (sequential per thread chunk).
+__global__ void scan_counts_kernel(int* __restrict__ counts, int64_t nblocks, int64_t* __restrict__ total)
+{
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (nblocks + 1023) / 1024;
+    const int64_t b0 = t * per, b1 = (b0 + per < nblocks) ? b0 + per : nblocks;
+    int64_t s = 0;
+    for (int64_t b = b0; b < b1; ++b) s += counts[b];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int q = 0; q < 1024; ++q) {
+            const int64_t v = part[q];
+            part[q] = run;
+            run += v;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    int64_t run = part[t];
+    for (int64_t b = b0; b < b1; ++b) {
+        const int v = counts[b];
+        counts[b] = (int)run;
+        run += v;
+    }
+}
+
+__global__ void sphere_write_kernel(SphereBox B, uint64_t ncodes, const int* __restrict__ offsets, int64_t N,
+                                    double* __restrict__ geo, double* __restrict__ dist,
+                                    int32_t* __restrict__ ijk_out)
+{
+    __shared__ int warp_tot[kCompactBlock / 32];
+    const uint64_t code = (uint64_t)blockIdx.x * kCompactBlock + threadIdx.x;
+    double x[3], n[3], d = 0.0;
+    int32_t ijk[3];
+    const bool keep = code < ncodes && sphere_node(B, code, x, n, &d, ijk);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int q = 0; q < warp; ++q) before += warp_tot[q];
+    if (!keep) return;
+    const int64_t j = (int64_t)offsets[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+    const double w = (1.0 + cos(kPi * d / B.eps)) / (2.0 * B.eps) * B.h * B.h * B.h;
+    geo[j] = x[0];
+    geo[N + j] = x[1];
+    geo[2 * N + j] = x[2];
+    geo[3 * N + j] = n[0];
+    geo[4 * N + j] = n[1];
+    geo[5 * N + j] = n[2];
+    geo[6 * N + j] = w;
+    dist[j] = d;
+    ijk_out[3 * j] = ijk[0];
+    ijk_out[3 * j + 1] = ijk[1];
+    ijk_out[3 * j + 2] = ijk[2];
+}
+
+ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, const double* origin, double h,
+                               double eps)
+{
+    SphereBox B;
+    int64_t P = 1;
+    for (int a = 0; a < 3; ++a) {
+        B.c[a] = centre[a];
+        B.o[a] = origin[a];
+        B.lo[a] = (int64_t)floor((centre[a] - R - eps - origin[a]) / h) - 1;
+        const int64_t hi = (int64_t)ceil((centre[a] + R + eps - origin[a]) / h) + 1;
+        B.n[a] = hi - B.lo[a] + 1;
+        while (P < B.n[a]) P <<= 1;
+    }
+    B.R = R;
+    B.h = h;
+    B.eps = eps;
+    const uint64_t ncodes = (uint64_t)P * P * P;
+    const int64_t nblocks = (int64_t)((ncodes + kCompactBlock - 1) / kCompactBlock);
+    int* d_counts = nullptr;
+    int64_t* d_total = nullptr;
+    IBIM_CUDA(cudaMalloc((void**)&d_counts, sizeof(int) * nblocks));
+    IBIM_CUDA(cudaMalloc((void**)&d_total, sizeof(int64_t)));
+    sphere_count_kernel<<<(unsigned)nblocks, kCompactBlock, 0, c->stream>>>(B, ncodes, d_counts);
+    scan_counts_kernel<<<1, 1024, 0, c->stream>>>(d_counts, nblocks, d_total);
+    count_launch(c, 2);
+    int64_t N = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&N, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess || N == 0) {
+        cudaFree(d_counts);
+        cudaFree(d_total);
+        if (e != cudaSuccess) return cuda_fail(e, "sphere band count", __FILE__, __LINE__);
+        set_error("the narrowband holds no grid node");
+        return IBIM_ERR_EMPTY_BAND;
+    }
+    c->N = N;
+    e = cudaMalloc((void**)&c->d_geo64, sizeof(double) * 7 * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dist, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ijk, sizeof(int32_t) * 3 * N);
+    if (e == cudaSuccess) {
+        sphere_write_kernel<<<(unsigned)nblocks, kCompactBlock, 0, c->stream>>>(B, ncodes, d_counts, N, c->d_geo64,
+                                                                                c->d_dist, c->d_ijk);
+        count_launch(c);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_counts);
+    cudaFree(d_total);
+    if (e != cudaSuccess) return cuda_fail(e, "sphere band write", __FILE__, __LINE__);
+    return IBIM_OK;
+}
+
+// FP32 copies of the geometry, positions relative to the centroid.
+__global__ void pack_geometry_f32_kernel(const double* __restrict__ geo, int64_t N, double c0, double c1,
+                                         double c2, float4* __restrict__ pos, float4* __restrict__ nrm)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    pos[j] = make_float4((float)(geo[j] - c0), (float)(geo[N + j] - c1), (float)(geo[2 * N + j] - c2),
+                         (float)geo[6 * N + j]);
+    nrm[j] = make_float4((float)geo[3 * N + j], (float)geo[4 * N + j], (float)geo[5 * N + j], 0.0f);
+}
+
+ibim_status finish_geometry(ibim_ctx* c)
+{
+    const int64_t N = c->N;
+    IBIM_CUDA(cudaMalloc((void**)&c->d_pos32, sizeof(float4) * N));
+    IBIM_CUDA(cudaMalloc((void**)&c->d_nrm32, sizeof(float4) * N));
+    const int bs = 256;
+    pack_geometry_f32_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
+        c->d_geo64, N, c->centroid[0], c->centroid[1], c->centroid[2], c->d_pos32, c->d_nrm32);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    return IBIM_OK;
+}
+
+}  // namespace ibim

@@ -1,0 +1,551 @@
+// Restarted GMRES for (Lambda + K W) p = g (Sec. 3.3), all vector work in FP64
+// on the device.
+//
+// One Arnoldi step is a fixed sequence of launches that reads the step index
+// k from a device-resident state, so the same sequence can be captured once
+// into a CUDA graph and replayed for every step:
+//   pack/pairs/fixup        w = A v_k                       (operator of the chosen precision)
+//   dots, reduce, update    classical Gram-Schmidt, twice   (CGS2)
+//   norm reduce, scale      v_{k+1} = w / ||w||
+//   givens                  rotate column k of H, update the residual estimate,
+//                           set `done` on convergence / end of cycle
+// Every launch first reads `done` and returns at once when it is set, so the
+// host can replay a few steps ahead and poll the flag only occasionally.
+//
+// Outer loop: r = g - A_out x, one GMRES cycle on A_in d = r from d = 0,
+// x += d.  Without certification A_out = A_in (plain restarted GMRES).  With
+// certification A_out is the FP64 operator and each cycle works to half the
+// tolerance with A_in (iterative refinement), so the reported residual is the
+// FP64 one.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ibim_internal.cuh"
+
+namespace ibim {
+
+constexpr int kMaxRestart = 128;
+constexpr int kVecThreads = 256;
+
+struct GmState {
+    int k;       // current Arnoldi step within the cycle
+    int done;    // stop expanding (converged, cycle full or breakdown)
+    int conv;    // residual estimate below target
+    int kmax;    // steps allowed in this cycle
+    int m;       // restart length (row stride of H)
+    int pad;
+    double target;     // absolute residual target of the cycle
+    double resid;      // |e_{k}| after the last rotation
+    double hn;         // ||w|| of the current step
+    double coef[kMaxRestart + 1];  // Gram-Schmidt coefficients of the current pass
+    double hcol[kMaxRestart + 1];  // accumulated column k of H
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double e[kMaxRestart + 1];
+    double y[kMaxRestart];
+    double H[(kMaxRestart + 1) * kMaxRestart];  // row-major, row stride m
+};
+
+struct GmresWork {
+    int m = 0;
+    int64_t len = 0;
+    double* V = nullptr;       // (m + 1) x len
+    double* x = nullptr;       // len: current iterate (solution accumulator)
+    double* r = nullptr;       // len: residual / scratch
+    double* t = nullptr;       // len: operator output scratch
+    double* g = nullptr;       // len: right-hand side
+    double* part = nullptr;    // per-block partial sums ((m + 1) x nblk)
+    int nblk = 0;
+    GmState* st = nullptr;     // device state
+    GmState* h_st = nullptr;   // pinned host mirror (small fields only are read)
+    cudaStream_t gs = nullptr; // capture-capable stream owned by the solver
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_prec = 0;
+    PairConsts graph_k;
+    bool graph_valid = false;
+};
+
+// ------------------------------------------------------------ vector kernels
+
+// part[b * (k+1) + j] = sum over this block's elements of V_j . V_{k+1}, j <= k
+__global__ void __launch_bounds__(kVecThreads)
+    gs_dots_kernel(const double* __restrict__ V, int64_t len, const GmState* __restrict__ st,
+                   double* __restrict__ part)
+{
+    if (st->done) return;
+    __shared__ double red[kVecThreads / 32][kMaxRestart + 1];
+    const int k = st->k;
+    const double* w = V + (int64_t)(k + 1) * len;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j <= k; ++j) {
+        const double* v = V + (int64_t)j * len;
+        double s = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < len; i += (int64_t)gridDim.x * kVecThreads)
+            s += v[i] * w[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp][j] = s;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= k; j += kVecThreads) {
+        double s = 0.0;
+        for (int q = 0; q < kVecThreads / 32; ++q) s += red[q][j];
+        part[(int64_t)blockIdx.x * (kMaxRestart + 1) + j] = s;
+    }
+}
+
+// coef[j] = sum_b part[b][j]; hcol[j] (+)= coef[j]  (pass 0 sets, pass 1 adds)
+__global__ void gs_reduce_kernel(const double* __restrict__ part, int nblk, GmState* __restrict__ st, int pass)
+{
+    if (st->done) return;
+    const int k = st->k;
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * (kMaxRestart + 1) + j];
+        st->coef[j] = s;
+        st->hcol[j] = (pass == 0) ? s : st->hcol[j] + s;
+    }
+}
+
+// V_{k+1} -= sum_j coef[j] V_j; optional per-block partial of ||V_{k+1}||^2 into part[b * (m+1) + 0]
+__global__ void __launch_bounds__(kVecThreads)
+    gs_update_kernel(double* __restrict__ V, int64_t len, const GmState* __restrict__ st,
+                     double* __restrict__ part, int with_norm)
+{
+    if (st->done) return;
+    __shared__ double coef[kMaxRestart + 1];
+    __shared__ double red[kVecThreads / 32];
+    const int k = st->k;
+    for (int j = threadIdx.x; j <= k; j += kVecThreads) coef[j] = st->coef[j];
+    __syncthreads();
+    double* w = V + (int64_t)(k + 1) * len;
+    double nn = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < len; i += (int64_t)gridDim.x * kVecThreads) {
+        double s = w[i];
+        for (int j = 0; j <= k; ++j) s -= coef[j] * V[(int64_t)j * len + i];
+        w[i] = s;
+        nn += s * s;
+    }
+    if (!with_norm) return;
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kVecThreads / 32; ++q) s += red[q];
+        part[(int64_t)blockIdx.x * (kMaxRestart + 1)] = s;
+    }
+}
+
+__global__ void norm_reduce_kernel(const double* __restrict__ part, int nblk, GmState* __restrict__ st)
+{
+    if (st->done) return;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(int64_t)b * (kMaxRestart + 1)];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->hn = sqrt(red[0]);
+}
+
+__global__ void scale_kernel(double* __restrict__ V, int64_t len, const GmState* __restrict__ st)
+{
+    if (st->done) return;
+    const double hn = st->hn;
+    if (!(hn > 0.0)) return;
+    const double inv = 1.0 / hn;
+    double* w = V + (int64_t)(st->k + 1) * len;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] *= inv;
+}
+
+// Column k of H: earlier rotations, new rotation, residual estimate |e_{k+1}|.
+__global__ void givens_kernel(GmState* __restrict__ st)
+{
+    if (st->done) return;
+    const int k = st->k, m = st->m;
+    double* H = st->H;
+    for (int j = 0; j <= k; ++j) H[j * m + k] = st->hcol[j];
+    const double hn = st->hn;
+    H[(k + 1) * m + k] = hn;
+    for (int j = 0; j < k; ++j) {
+        const double a = H[j * m + k], b = H[(j + 1) * m + k];
+        H[j * m + k] = st->cs[j] * a + st->sn[j] * b;
+        H[(j + 1) * m + k] = -st->sn[j] * a + st->cs[j] * b;
+    }
+    const double a = H[k * m + k], b = H[(k + 1) * m + k];
+    const double rr = hypot(a, b);
+    const double c = (rr > 0.0) ? a / rr : 1.0;
+    const double s = (rr > 0.0) ? b / rr : 0.0;
+    st->cs[k] = c;
+    st->sn[k] = s;
+    H[k * m + k] = rr;
+    H[(k + 1) * m + k] = 0.0;
+    st->e[k + 1] = -s * st->e[k];
+    st->e[k] = c * st->e[k];
+    st->resid = fabs(st->e[k + 1]);
+    st->k = k + 1;
+    if (st->resid <= st->target) st->conv = 1;
+    if (st->conv || st->k >= st->kmax || !(hn > 0.0)) st->done = 1;
+}
+
+// Back substitution H y = e (k x k upper triangular), then nothing else.
+__global__ void trisolve_kernel(GmState* __restrict__ st)
+{
+    const int k = st->k, m = st->m;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = st->e[i];
+        for (int j = i + 1; j < k; ++j) s -= st->H[i * m + j] * st->y[j];
+        st->y[i] = s / st->H[i * m + i];
+    }
+}
+
+// x += sum_{j<k} y_j V_j
+__global__ void xupdate_kernel(double* __restrict__ x, const double* __restrict__ V, int64_t len,
+                               const GmState* __restrict__ st)
+{
+    __shared__ double y[kMaxRestart];
+    const int k = st->k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) y[j] = st->y[j];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int j = 0; j < k; ++j) s += y[j] * V[(int64_t)j * len + i];
+        x[i] = s;
+    }
+}
+
+// r = g - t and per-block partial of ||r||^2 (part[b * (m+1)])
+__global__ void __launch_bounds__(kVecThreads)
+    residual_kernel(const double* __restrict__ g, const double* __restrict__ t, double* __restrict__ r, int64_t len,
+                    double* __restrict__ part)
+{
+    __shared__ double red[kVecThreads / 32];
+    double nn = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < len; i += (int64_t)gridDim.x * kVecThreads) {
+        const double v = g[i] - (t ? t[i] : 0.0);
+        r[i] = v;
+        nn += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kVecThreads / 32; ++q) s += red[q];
+        part[(int64_t)blockIdx.x * (kMaxRestart + 1)] = s;
+    }
+}
+
+// New cycle: beta = sqrt(sum part), V_0 = r / beta, state reset with e = (beta, 0, ...).
+__global__ void cycle_begin_reduce_kernel(const double* __restrict__ part, int nblk, GmState* __restrict__ st,
+                                          double target, int kmax)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(int64_t)b * (kMaxRestart + 1)];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(red[0]);
+        st->hn = beta;  // carries beta to the scaling kernel
+        st->k = 0;
+        st->conv = (beta <= target) ? 1 : 0;
+        st->done = st->conv;
+        st->kmax = kmax;
+        st->target = target;
+        st->resid = beta;
+        for (int j = 0; j <= st->m; ++j) st->e[j] = 0.0;
+        st->e[0] = beta;
+    }
+}
+
+__global__ void cycle_begin_scale_kernel(const double* __restrict__ r, double* __restrict__ V0, int64_t len,
+                                         const GmState* __restrict__ st)
+{
+    const double beta = st->hn;
+    const double inv = (beta > 0.0) ? 1.0 / beta : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        V0[i] = r[i] * inv;
+}
+
+// x0 = Lambda^{-1} g (Sec. 3.3 initial guess with D = 0)
+__global__ void lambda_inv_kernel(const double* __restrict__ g, double* __restrict__ x, int64_t N, double l1,
+                                  double l2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    x[i] = g[i] / l1;
+    x[N + i] = g[N + i] / l2;
+}
+
+// ------------------------------------------------------------------ host side
+
+void gmres_free(ibim_ctx* c)
+{
+    GmresWork* w = c->gm;
+    if (w == nullptr) return;
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    if (w->ev) cudaEventDestroy(w->ev);
+    if (w->gs) cudaStreamDestroy(w->gs);
+    cudaFree(w->V);
+    cudaFree(w->x);
+    cudaFree(w->r);
+    cudaFree(w->t);
+    cudaFree(w->g);
+    cudaFree(w->part);
+    cudaFree(w->st);
+    cudaFreeHost(w->h_st);
+    delete w;
+    c->gm = nullptr;
+}
+
+static ibim_status gmres_alloc(ibim_ctx* c, int m)
+{
+    const int64_t len = 2 * c->N;
+    if (c->gm && c->gm->m >= m && c->gm->len == len) return IBIM_OK;
+    gmres_free(c);
+    GmresWork* w = new GmresWork();
+    c->gm = w;
+    w->m = m;
+    w->len = len;
+    w->nblk = (int)std::min<int64_t>(2 * c->num_sms, (len + kVecThreads - 1) / kVecThreads);
+    if (w->nblk < 1) w->nblk = 1;
+    IBIM_CUDA(cudaMalloc((void**)&w->V, sizeof(double) * (size_t)(m + 1) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->x, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->r, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->t, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->g, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->part, sizeof(double) * (size_t)w->nblk * (kMaxRestart + 1)));
+    IBIM_CUDA(cudaMalloc((void**)&w->st, sizeof(GmState)));
+    IBIM_CUDA(cudaMallocHost((void**)&w->h_st, sizeof(GmState)));
+    IBIM_CUDA(cudaStreamCreateWithFlags(&w->gs, cudaStreamNonBlocking));
+    IBIM_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
+    return IBIM_OK;
+}
+
+// One Arnoldi step (see the file comment), all launches on c->stream.
+static ibim_status arnoldi_step(ibim_ctx* c, const PairConsts& k, int precision)
+{
+    GmresWork* w = c->gm;
+    const int64_t len = w->len;
+    const int* skip = &w->st->done;
+    VecRef in{w->V, &w->st->k, len, 0};
+    OutRef out{w->V, &w->st->k, len, 1};
+    IBIM_TRY(apply_operator(c, k, precision, in, out, skip));
+    for (int pass = 0; pass < 2; ++pass) {
+        gs_dots_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st, w->part);
+        gs_reduce_kernel<<<1, 128, 0, c->stream>>>(w->part, w->nblk, w->st, pass);
+        gs_update_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st, w->part, pass == 1);
+    }
+    norm_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st);
+    scale_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st);
+    givens_kernel<<<1, 1, 0, c->stream>>>(w->st);
+    count_launch(c, 9);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+// r = g - A_out x (or r = g when x is known to be zero); starts a cycle on r.
+static ibim_status begin_cycle(ibim_ctx* c, const PairConsts& k, int prec_out, bool x_zero, double target,
+                               int kmax, double* beta_host)
+{
+    GmresWork* w = c->gm;
+    const int64_t len = w->len;
+    if (!x_zero)
+        IBIM_TRY(apply_operator(c, k, prec_out, VecRef{w->x, nullptr, 0, 0}, OutRef{w->t, nullptr, 0, 0}, nullptr));
+    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->g, x_zero ? nullptr : w->t, w->r, len, w->part);
+    cycle_begin_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, target, kmax);
+    cycle_begin_scale_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->r, w->V, len, w->st);
+    count_launch(c, 3);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_CUDA(cudaMemcpyAsync(w->h_st, w->st, 64, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    *beta_host = w->h_st->resid;
+    return IBIM_OK;
+}
+
+static ibim_status capture_step(ibim_ctx* c, const PairConsts& k, int precision)
+{
+    GmresWork* w = c->gm;
+    if (w->graph_valid && w->graph_prec == precision && memcmp(&w->graph_k, &k, sizeof(k)) == 0) return IBIM_OK;
+    if (w->exec) {
+        cudaGraphExecDestroy(w->exec);
+        w->exec = nullptr;
+    }
+    w->graph_valid = false;
+    // make sure every workspace the step touches exists before capture
+    if (precision == IBIM_F32C) {
+        IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 2 * sizeof(float4)));
+        const PairSchedule s = make_schedule(c->N, kF32TTile, c->N, kF32STile, f32_grid_cap(c));
+        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, (size_t)s.grid * s.max_segs * 2 * kF32TTile * sizeof(double)));
+    } else {
+        IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 8 * sizeof(double)));
+        const PairSchedule s = make_schedule(c->N, kF64TTile, c->N, kF64STile, f64_grid_cap(c));
+        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, (size_t)s.grid * s.max_segs * 2 * kF64TTile * sizeof(double)));
+    }
+    cudaGraph_t graph = nullptr;
+    IBIM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t launches_before = c->timing.total_launches;
+    ibim_status s = arnoldi_step(c, k, precision);
+    c->timing.total_launches = launches_before;  // capture does not launch
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (s != IBIM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "capture of the Arnoldi step", __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&w->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate", __FILE__, __LINE__);
+    w->graph_valid = true;
+    w->graph_prec = precision;
+    w->graph_k = k;
+    return IBIM_OK;
+}
+
+// Runs steps until the device sets `done`; returns the steps taken.
+static ibim_status run_cycle(ibim_ctx* c, const PairConsts& k, int precision, bool use_graph, int* steps,
+                             int* conv)
+{
+    GmresWork* w = c->gm;
+    const int per_poll = 2;
+    int launched = 0;
+    for (;;) {
+        for (int q = 0; q < per_poll; ++q) {
+            if (use_graph) {
+                IBIM_CUDA(cudaGraphLaunch(w->exec, c->stream));
+                count_launch(c, 12);  // kernels in one captured step
+            } else {
+                IBIM_TRY(arnoldi_step(c, k, precision));
+            }
+            ++launched;
+        }
+        IBIM_CUDA(cudaMemcpyAsync(w->h_st, w->st, 64, cudaMemcpyDeviceToHost, c->stream));
+        IBIM_CUDA(cudaStreamSynchronize(c->stream));
+        if (w->h_st->done) break;
+        if (launched > kMaxRestart + 4) {
+            set_error("GMRES cycle did not terminate");
+            return IBIM_ERR_CUDA;
+        }
+    }
+    *steps = w->h_st->k;
+    *conv = w->h_st->conv;
+    return IBIM_OK;
+}
+
+ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& o, double* d_p,
+                        ibim_solve_info* info)
+{
+    const int m = std::min(o.restart, kMaxRestart);
+    IBIM_TRY(gmres_alloc(c, m));
+    GmresWork* w = c->gm;
+    const int64_t len = w->len, N = c->N;
+    const PairConsts k = make_consts(p);
+    const int prec_in = o.precision;
+    const int prec_out = o.certify ? IBIM_F64 : o.precision;
+
+    // Work on the solver's own stream (graph capture needs a non-legacy
+    // stream), ordered after everything already queued on the caller's.
+    cudaStream_t user = c->stream;
+    IBIM_CUDA(cudaEventRecord(w->ev, user));
+    IBIM_CUDA(cudaStreamWaitEvent(w->gs, w->ev, 0));
+    c->stream = w->gs;
+    struct Restore {
+        ibim_ctx* c;
+        cudaStream_t user;
+        ~Restore()
+        {
+            cudaEventRecord(c->gm->ev, c->stream);
+            cudaStreamWaitEvent(user, c->gm->ev, 0);
+            c->stream = user;
+        }
+    } restore{c, user};
+
+    GmState init;
+    memset(&init, 0, sizeof(init));
+    init.m = m;
+    IBIM_CUDA(cudaMemcpyAsync(w->st, &init, sizeof(GmState), cudaMemcpyHostToDevice, c->stream));
+
+    IBIM_TRY(rhs_launch(c, p.eps_in, w->g));
+    // ||g||
+    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->g, nullptr, w->r, len, w->part);
+    cycle_begin_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, 0.0, 0);
+    count_launch(c, 2);
+    IBIM_CUDA(cudaMemcpyAsync(w->h_st, w->st, 64, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    const double gnorm = w->h_st->resid;
+
+    bool x_zero = false;
+    if (o.start == 0) {
+        IBIM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * len, c->stream));
+        x_zero = true;
+    } else if (o.start == 1) {
+        lambda_inv_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(w->g, w->x, N, k.lambda1, k.lambda2);
+        count_launch(c);
+    } else {
+        IBIM_CUDA(cudaMemcpyAsync(w->x, d_p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    }
+
+    const bool use_graph = !c->timing.enabled;
+    const double target_abs = o.tol * gnorm;
+    const double inner_target = o.certify ? 0.5 * target_abs : target_abs;
+    int iters = 0, cycles = 0;
+    double beta = 0.0;
+    bool converged = false;
+    if (gnorm == 0.0) {
+        IBIM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * len, c->stream));
+        converged = true;
+    }
+    while (!converged) {
+        const int kmax = std::min(m, o.maxit - iters);
+        if (!x_zero) {
+            if (prec_out == IBIM_F32C) info->matvecs_f32 += 1;
+            else info->matvecs_f64 += 1;
+        }
+        IBIM_TRY(begin_cycle(c, k, prec_out, x_zero, inner_target, std::max(kmax, 0), &beta));
+        x_zero = false;
+        if (beta <= target_abs) {
+            converged = true;
+            break;
+        }
+        if (kmax <= 0) break;
+        if (use_graph) IBIM_TRY(capture_step(c, k, prec_in));
+        int steps = 0, conv = 0;
+        IBIM_TRY(run_cycle(c, k, prec_in, use_graph, &steps, &conv));
+        iters += steps;
+        ++cycles;
+        info->matvecs_f32 += (prec_in == IBIM_F32C) ? steps : 0;
+        info->matvecs_f64 += (prec_in == IBIM_F64) ? steps : 0;
+        if (steps > 0) {
+            trisolve_kernel<<<1, 1, 0, c->stream>>>(w->st);
+            xupdate_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->x, w->V, len, w->st);
+            count_launch(c, 2);
+            IBIM_CUDA(cudaGetLastError());
+        }
+    }
+    info->iters = iters;
+    info->cycles = cycles;
+    info->converged = converged ? 1 : 0;
+    info->relres = (gnorm > 0.0) ? beta / gnorm : 0.0;
+    IBIM_CUDA(cudaMemcpyAsync(d_p, w->x, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+
+    double gpol = 0.0, area = 0.0;
+    IBIM_TRY(energy_launch(c, p, w->x, nullptr, &gpol));
+    IBIM_TRY(area_launch(c, &area));
+    info->gpol = gpol;
+    info->gpol_kcal = gpol * kKcalPerE2A;
+    info->area = area;
+    return converged ? IBIM_OK : IBIM_ERR_NOT_CONVERGED;
+}
+
+}  // namespace ibim

@@ -1,0 +1,344 @@
+"""Thin ctypes binding of the C ABI in ``include/ibim.h`` (argument marshalling only).
+
+Every compute step runs in ``libibim.so`` (hand-written sm_103a CUDA).  There
+is no CPU fallback: importing this module raises when the library has not been
+built, and the entry points raise ``IbimError`` on any non-OK status.
+Device buffers are passed as torch CUDA tensors (float64, contiguous) or raw
+integer device pointers; the stream is the current torch stream unless given.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "IbimError", "Phys", "SolveOpts", "SolveInfo", "lib", "library_path",
+    "ibim_build_sphere", "ibim_build_from_nodes", "ibim_set_charges", "ibim_num_nodes", "ibim_get_nodes",
+    "ibim_matvec", "ibim_matvec_host", "ibim_rhs", "ibim_energy", "ibim_area", "ibim_solve", "ibim_solve_host",
+    "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
+    "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A",
+]
+
+IBIM_F64 = 64
+IBIM_F32C = 32
+KCAL_PER_E2_A = 4.0 * np.pi * 332.0637
+
+_STATUS = {0: "IBIM_OK", 1: "IBIM_ERR_ARG", 2: "IBIM_ERR_EMPTY_BAND", 3: "IBIM_ERR_NONFINITE",
+           4: "IBIM_ERR_CUDA", 5: "IBIM_ERR_NOT_CONVERGED", 6: "IBIM_ERR_DEVICE_TIMEOUT", 7: "IBIM_ERR_STATE"}
+
+
+class IbimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Phys(ctypes.Structure):
+    _fields_ = [("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("tau", ctypes.c_double), ("tube_rule", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("restart", ctypes.c_int), ("start", ctypes.c_int), ("certify", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres", ctypes.c_double), ("gpol", ctypes.c_double), ("gpol_kcal", ctypes.c_double),
+                ("area", ctypes.c_double), ("matvecs_f32", ctypes.c_int64), ("matvecs_f64", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+_V = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_CTXP = ctypes.POINTER(_V)
+_SIGS = {
+    "ibim_build_sphere": [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double, _V, _CTXP],
+    "ibim_build_from_nodes": [ctypes.c_int64, _D, _D, _D, ctypes.c_double, _V, _CTXP],
+    "ibim_set_charges": [_V, ctypes.c_int64, _D, _D],
+    "ibim_num_nodes": [_V, _I64P],
+    "ibim_get_nodes": [_V, _D, _D, _D, _D, ctypes.POINTER(ctypes.c_int32)],
+    "ibim_matvec": [_V, ctypes.POINTER(Phys), ctypes.c_int, _V, _V],
+    "ibim_matvec_host": [_V, ctypes.POINTER(Phys), ctypes.c_int, _D, _D],
+    "ibim_rhs": [_V, ctypes.c_double, _V],
+    "ibim_energy": [_V, ctypes.POINTER(Phys), ctypes.c_int, _V, _V, _D],
+    "ibim_area": [_V, _D],
+    "ibim_solve": [_V, ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts), _V, ctypes.POINTER(SolveInfo)],
+    "ibim_solve_host": [_V, ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts), ctypes.c_int64, _D, _D, _D,
+                        ctypes.POINTER(SolveInfo)],
+    "ibim_timing_enable": [_V, ctypes.c_int],
+    "ibim_timing_reset": [_V],
+    "ibim_timing_get": [_V, _D, _I64P, _I64P, _I64P],
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libibim.so (raises when it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError("libibim.so is not built (%s); run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.ibim_last_error.restype = ctypes.c_char_p
+        L.ibim_last_error.argtypes = []
+        L.ibim_destroy.restype = None
+        L.ibim_destroy.argtypes = [_V]
+        _lib = L
+    return _lib
+
+
+def ibim_last_error():
+    return lib().ibim_last_error().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise IbimError(status, ibim_last_error())
+    return status
+
+
+def _dptr(x):
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return x.data_ptr()
+
+
+def _host(a, dtype=np.float64):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _phys(p):
+    if isinstance(p, Phys):
+        return p
+    if isinstance(p, dict):
+        return Phys(p["eps_in"], p["eps_out"], p["kappa"], p["tau"], p.get("tube_rule", 0))
+    return Phys(*p)
+
+
+# ----------------------------------------------------------------- raw calls
+
+def ibim_build_sphere(R, centre, origin, h, band_eps, stream=None):
+    c = _host(centre)
+    o = None if origin is None else _host(origin)
+    ctx = _V()
+    _check(lib().ibim_build_sphere(float(R), c.ctypes.data_as(_D), None if o is None else o.ctypes.data_as(_D),
+                                   float(h), float(band_eps), _stream(stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def ibim_build_from_nodes(xstar, normal, w, h, stream=None):
+    xs = _host(xstar).reshape(-1, 3)
+    nr = _host(normal).reshape(-1, 3)
+    ww = _host(w).reshape(-1)
+    ctx = _V()
+    _check(lib().ibim_build_from_nodes(xs.shape[0], xs.ctypes.data_as(_D), nr.ctypes.data_as(_D),
+                                       ww.ctypes.data_as(_D), float(h), _stream(stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def ibim_set_charges(ctx, z, q):
+    z = _host(z).reshape(-1, 3)
+    q = _host(q).reshape(-1)
+    _check(lib().ibim_set_charges(ctx, q.shape[0], z.ctypes.data_as(_D), q.ctypes.data_as(_D)))
+
+
+def ibim_num_nodes(ctx):
+    n = ctypes.c_int64(0)
+    _check(lib().ibim_num_nodes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def ibim_get_nodes(ctx):
+    N = ibim_num_nodes(ctx)
+    xs = np.empty((N, 3))
+    nr = np.empty((N, 3))
+    w = np.empty(N)
+    d = np.empty(N)
+    ijk = np.empty((N, 3), dtype=np.int32)
+    _check(lib().ibim_get_nodes(ctx, xs.ctypes.data_as(_D), nr.ctypes.data_as(_D), w.ctypes.data_as(_D),
+                                d.ctypes.data_as(_D), ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return {"xs": xs, "nrm": nr, "w": w, "d": d, "ijk": ijk}
+
+
+def ibim_matvec(ctx, phys, precision, d_in, d_out):
+    p = _phys(phys)
+    _check(lib().ibim_matvec(ctx, ctypes.byref(p), int(precision), _dptr(d_in), _dptr(d_out)))
+
+
+def ibim_matvec_host(ctx, phys, precision, h_in):
+    p = _phys(phys)
+    x = _host(h_in)
+    y = np.empty_like(x)
+    _check(lib().ibim_matvec_host(ctx, ctypes.byref(p), int(precision), x.ctypes.data_as(_D),
+                                  y.ctypes.data_as(_D)))
+    return y
+
+
+def ibim_rhs(ctx, eps_in, d_g):
+    _check(lib().ibim_rhs(ctx, float(eps_in), _dptr(d_g)))
+
+
+def ibim_energy(ctx, phys, precision, d_p, d_psi_rxn=None):
+    p = _phys(phys)
+    g = ctypes.c_double(0.0)
+    _check(lib().ibim_energy(ctx, ctypes.byref(p), int(precision), _dptr(d_p), _dptr(d_psi_rxn), ctypes.byref(g)))
+    return g.value
+
+
+def ibim_area(ctx):
+    a = ctypes.c_double(0.0)
+    _check(lib().ibim_area(ctx, ctypes.byref(a)))
+    return a.value
+
+
+def _opts(precision=IBIM_F32C, tol=1e-6, maxit=500, restart=64, start=0, certify=0):
+    return SolveOpts(int(precision), float(tol), int(maxit), int(restart), int(start), int(certify))
+
+
+def ibim_solve(ctx, phys, d_p, allow_not_converged=False, **opts):
+    p = _phys(phys)
+    o = _opts(**opts)
+    info = SolveInfo()
+    st = lib().ibim_solve(ctx, ctypes.byref(p), ctypes.byref(o), _dptr(d_p), ctypes.byref(info))
+    if not (allow_not_converged and st == 5):
+        _check(st)
+    return info.as_dict()
+
+
+def ibim_solve_host(ctx, phys, z, q, h_p=None, allow_not_converged=False, **opts):
+    p = _phys(phys)
+    o = _opts(**opts)
+    z = _host(z).reshape(-1, 3)
+    q = _host(q).reshape(-1)
+    info = SolveInfo()
+    out = h_p if h_p is not None else np.empty(2 * ibim_num_nodes(ctx))
+    st = lib().ibim_solve_host(ctx, ctypes.byref(p), ctypes.byref(o), q.shape[0], z.ctypes.data_as(_D),
+                               q.ctypes.data_as(_D), out.ctypes.data_as(_D), ctypes.byref(info))
+    if not (allow_not_converged and st == 5):
+        _check(st)
+    return out, info.as_dict()
+
+
+def ibim_timing_enable(ctx, enable=True):
+    _check(lib().ibim_timing_enable(ctx, 1 if enable else 0))
+
+
+def ibim_timing_reset(ctx):
+    _check(lib().ibim_timing_reset(ctx))
+
+
+def ibim_timing_get(ctx):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    inter = ctypes.c_int64(0)
+    tot = ctypes.c_int64(0)
+    _check(lib().ibim_timing_get(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(inter), ctypes.byref(tot)))
+    return {"pair_ms": ms.value, "pair_launches": n.value, "pair_interactions": inter.value,
+            "total_launches": tot.value}
+
+
+def ibim_destroy(ctx):
+    if ctx:
+        lib().ibim_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper of an ibim_ctx handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def sphere(cls, R, centre=(0.0, 0.0, 0.0), h=0.25, band_eps=None, origin=None, stream=None):
+        return cls(ibim_build_sphere(R, centre, origin, h, 2 * h if band_eps is None else band_eps, stream))
+
+    @classmethod
+    def from_nodes(cls, xstar, normal, w, h, stream=None):
+        return cls(ibim_build_from_nodes(xstar, normal, w, h, stream))
+
+    @property
+    def N(self):
+        return ibim_num_nodes(self.handle)
+
+    def nodes(self):
+        return ibim_get_nodes(self.handle)
+
+    def set_charges(self, z, q):
+        ibim_set_charges(self.handle, z, q)
+
+    def matvec(self, phys, d_in, d_out, precision=IBIM_F32C):
+        ibim_matvec(self.handle, phys, precision, d_in, d_out)
+
+    def matvec_host(self, phys, h_in, precision=IBIM_F32C):
+        return ibim_matvec_host(self.handle, phys, precision, h_in)
+
+    def rhs(self, eps_in, d_g):
+        ibim_rhs(self.handle, eps_in, d_g)
+
+    def energy(self, phys, d_p, d_psi=None, precision=IBIM_F64):
+        return ibim_energy(self.handle, phys, precision, d_p, d_psi)
+
+    def area(self):
+        return ibim_area(self.handle)
+
+    def solve(self, phys, d_p, **opts):
+        return ibim_solve(self.handle, phys, d_p, **opts)
+
+    def solve_host(self, phys, z, q, h_p=None, **opts):
+        return ibim_solve_host(self.handle, phys, z, q, h_p, **opts)
+
+    def timing_enable(self, enable=True):
+        ibim_timing_enable(self.handle, enable)
+
+    def timing_reset(self):
+        ibim_timing_reset(self.handle)
+
+    def timing(self):
+        return ibim_timing_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            ibim_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
