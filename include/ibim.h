@@ -183,6 +183,36 @@ ibim_status ibim_solve_host(ibim_ctx* ctx, const ibim_phys* phys, const ibim_sol
                             int64_t Nc, const double* z, const double* q, double* h_p,
                             ibim_solve_info* info);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/*
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory -- code that runs where cudaMalloc is not
+ * allowed or not wanted (a host callback, a process whose device allocator is
+ * owned by another runtime or frozen after start-up, a service with a fixed
+ * device-memory budget).  It computes the same product as ibim_matvec with
+ * IBIM_F32C, without a context, from caller-owned device arrays:
+ *   d_xstar, d_normal : N x 3 row-major FP64 projections x* and unit normals,
+ *   d_w               : N FP64 weights w_j = J delta_eps(d_j) h^3,
+ *   d_in, d_out       : 2N FP64 vectors [psi; psin] (must not overlap),
+ *   stream            : cudaStream_t (NULL = legacy default stream).
+ * Working memory (FP32 node copies, packed sources, partial sums, an error
+ * word) comes from one fixed-size static device array, about 16.8 MB, that
+ * every GPU loading this library holds until the process exits.  The call
+ * allocates and frees nothing.  Limits: 1 <= N <= IBIM_NOALLOC_MAX_NODES;
+ * larger N returns IBIM_ERR_ARG.
+ * The first call on each device looks up that device's address of the array
+ * (with the device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (on different streams, or from different host
+ * threads) race on it and must be serialised by the caller.  The call
+ * synchronises `stream` before returning and reports IBIM_ERR_DEVICE_TIMEOUT
+ * when a bounded device wait gave up.
+ */
+#define IBIM_NOALLOC_MAX_NODES 131072
+ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, const double* d_normal, const double* d_w,
+                                const ibim_phys* phys, const double* d_in, double* d_out, void* stream);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /*

@@ -1,0 +1,164 @@
+// Allocation-free FP32 compensated operator application.
+//
+// Some callers cannot allocate device memory: code running where cudaMalloc
+// is off limits (inside a host callback, under a memory pool owned by another
+// runtime, in a process whose allocator is frozen after start-up) or that must
+// not add allocations a memory budget does not account for.  This entry point
+// computes the same product as ibim_matvec with IBIM_F32C from caller-owned
+// geometry and vectors, and takes its working memory (FP32 node copies, the
+// packed source payload, the per-CTA partial sums, an error word) from one
+// file-scope device array of fixed size.  The array exists on every GPU that
+// loads the library, from load until process exit.
+#include <mutex>
+
+#include "ibim_internal.cuh"
+
+namespace ibim {
+
+PairSchedule make_schedule(int64_t n_targets, int ttile, int64_t n_sources, int stile, int grid_cap, int64_t);
+int f32_occupancy_per_sm();
+cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
+                                const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
+                                cudaStream_t stream);
+cudaError_t launch_fixup_raw(const double* part, const PairSchedule& s, int64_t N, const PairConsts& k,
+                             const double* d_in, double* d_out, cudaStream_t stream);
+
+namespace {
+
+constexpr int64_t kMaxNodes = IBIM_NOALLOC_MAX_NODES;
+constexpr int kMaxCtas = 1024;  // persistent CTAs per launch at most
+constexpr int kMaxSegs = 2;     // partial slots per CTA (enough once the grid has >= one CTA per target tile)
+constexpr size_t kHeadBytes = 256;  // error word + centroid
+constexpr size_t kPosBytes = sizeof(float4) * (size_t)kMaxNodes;
+constexpr size_t kSrcBytes = 2 * sizeof(float4) * (size_t)kMaxNodes;
+constexpr size_t kPartDoubles = (size_t)kMaxCtas * kMaxSegs * 2 * kF32TTile;
+constexpr size_t kScratchBytes = kHeadBytes + 2 * kPosBytes + kSrcBytes + kPartDoubles * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_addr[128] = {};  // device address of g_noalloc_scratch per device ordinal
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the lookup must not happen inside a stream capture).
+ibim_status scratch_address(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= 128) {
+        set_error("device ordinal out of range");
+        return IBIM_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_addr[dev] == nullptr) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)", __FILE__, __LINE__);
+        g_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_addr[dev]);
+    return IBIM_OK;
+}
+
+// Centroid of the caller's nodes (one CTA, fixed summation order).
+__global__ void noalloc_centroid_kernel(const double* __restrict__ xs, int64_t N, double* __restrict__ cen)
+{
+    __shared__ double red[3][1024];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        s0 += xs[3 * j];
+        s1 += xs[3 * j + 1];
+        s2 += xs[3 * j + 2];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) cen[threadIdx.x] = red[threadIdx.x][0] / (double)N;
+}
+
+// FP32 target geometry and source payload from the caller's FP64 arrays.
+__global__ void noalloc_pack_kernel(const double* __restrict__ xs, const double* __restrict__ nrm,
+                                    const double* __restrict__ w, const double* __restrict__ p, int64_t N,
+                                    const double* __restrict__ cen, float4* __restrict__ tpos,
+                                    float4* __restrict__ tnrm, float4* __restrict__ src)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const float x = (float)(xs[3 * j] - cen[0]), y = (float)(xs[3 * j + 1] - cen[1]),
+                z = (float)(xs[3 * j + 2] - cen[2]);
+    const float n0 = (float)nrm[3 * j], n1 = (float)nrm[3 * j + 1], n2 = (float)nrm[3 * j + 2];
+    const double wj = w[j];
+    tpos[j] = make_float4(x, y, z, (float)wj);
+    tnrm[j] = make_float4(n0, n1, n2, 0.0f);
+    src[2 * j] = make_float4(x, y, z, (float)(wj * p[j]));
+    src[2 * j + 1] = make_float4(n0, n1, n2, (float)(wj * p[N + j]));
+}
+
+}  // namespace
+}  // namespace ibim
+
+using namespace ibim;
+
+extern "C" ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, const double* d_normal,
+                                           const double* d_w, const ibim_phys* phys, const double* d_in,
+                                           double* d_out, void* stream)
+{
+    if (N < 1 || N > kMaxNodes) {
+        set_error("ibim_matvec_noalloc: N must be in [1, IBIM_NOALLOC_MAX_NODES = 131072]");
+        return IBIM_ERR_ARG;
+    }
+    if (!d_xstar || !d_normal || !d_w || !d_in || !d_out) {
+        set_error("ibim_matvec_noalloc: NULL pointer");
+        return IBIM_ERR_ARG;
+    }
+    if (d_in == d_out) {
+        set_error("ibim_matvec_noalloc: d_in and d_out must not overlap");
+        return IBIM_ERR_ARG;
+    }
+    IBIM_TRY(check_phys(phys));
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    IBIM_CUDA(cudaGetDevice(&dev));
+    IBIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned char* base = nullptr;
+    IBIM_TRY(scratch_address(dev, &base));
+    unsigned* err = reinterpret_cast<unsigned*>(base);
+    double* cen = reinterpret_cast<double*>(base + 64);
+    float4* tpos = reinterpret_cast<float4*>(base + kHeadBytes);
+    float4* tnrm = reinterpret_cast<float4*>(base + kHeadBytes + kPosBytes);
+    float4* src = reinterpret_cast<float4*>(base + kHeadBytes + 2 * kPosBytes);
+    double* part = reinterpret_cast<double*>(base + kHeadBytes + 2 * kPosBytes + kSrcBytes);
+
+    const PairConsts k = make_consts(*phys);
+    // At least one CTA per target tile keeps every CTA within two target tiles.
+    const int n_ttiles = (int)((N + kF32TTile - 1) / kF32TTile);
+    int cap = f32_occupancy_per_sm() * sms;
+    if (cap < n_ttiles) cap = n_ttiles;
+    if (cap > kMaxCtas) cap = kMaxCtas;
+    const PairSchedule s = make_schedule(N, kF32TTile, N, kF32STile, cap, 0);
+    if ((size_t)s.grid * s.max_segs * 2 * kF32TTile > kPartDoubles) {
+        set_error("ibim_matvec_noalloc: schedule needs more partial slots than the static region holds");
+        return IBIM_ERR_ARG;
+    }
+    IBIM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+    noalloc_centroid_kernel<<<1, 1024, 0, st>>>(d_xstar, N, cen);
+    IBIM_CUDA(cudaGetLastError());
+    const int bs = 256;
+    noalloc_pack_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(d_xstar, d_normal, d_w, d_in, N, cen, tpos,
+                                                                     tnrm, src);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_CUDA(launch_pair_f32_raw(tpos, tnrm, src, N, s, k, part, err, st));
+    IBIM_CUDA(launch_fixup_raw(part, s, N, k, d_in, d_out, st));
+    unsigned h_err = 0;
+    IBIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    IBIM_CUDA(cudaStreamSynchronize(st));
+    if (h_err & kDevErrTimeout) {
+        set_error("ibim_matvec_noalloc: a bounded device wait gave up");
+        return IBIM_ERR_DEVICE_TIMEOUT;
+    }
+    return IBIM_OK;
+}

@@ -315,4 +315,30 @@ ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, V
     return fixup_launch(c, k, s, kF32TTile, in, out, d_skip);
 }
 
+// Launchers on caller-supplied buffers (used by the allocation-free entry point).
+int f32_occupancy_per_sm()
+{
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel, kF32Threads, 0);
+    return occ < 1 ? 1 : occ;
+}
+
+cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
+                                const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
+                                cudaStream_t stream)
+{
+    pair_f32_kernel<<<s.grid, kF32Threads, 0, stream>>>(tpos, tnrm, src, N, s, f32_consts(k), part, err, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_raw(const double* part, const PairSchedule& s, int64_t N, const PairConsts& k,
+                             const double* d_in, double* d_out, cudaStream_t stream)
+{
+    const int bs = 256;
+    fixup_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, stream>>>(part, s, kF32TTile, N, k.lambda1, k.lambda2,
+                                                                  VecRef{d_in, nullptr, 0, 0},
+                                                                  OutRef{d_out, nullptr, 0, 0}, nullptr);
+    return cudaGetLastError();
+}
+
 }  // namespace ibim

@@ -18,11 +18,13 @@ __all__ = [
     "ibim_build_sphere", "ibim_build_from_nodes", "ibim_set_charges", "ibim_num_nodes", "ibim_get_nodes",
     "ibim_matvec", "ibim_matvec_host", "ibim_rhs", "ibim_energy", "ibim_area", "ibim_solve", "ibim_solve_host",
     "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
+    "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A",
 ]
 
 IBIM_F64 = 64
 IBIM_F32C = 32
+IBIM_NOALLOC_MAX_NODES = 131072
 KCAL_PER_E2_A = 4.0 * np.pi * 332.0637
 
 _STATUS = {0: "IBIM_OK", 1: "IBIM_ERR_ARG", 2: "IBIM_ERR_EMPTY_BAND", 3: "IBIM_ERR_NONFINITE",
@@ -75,6 +77,7 @@ _SIGS = {
     "ibim_timing_enable": [_V, ctypes.c_int],
     "ibim_timing_reset": [_V],
     "ibim_timing_get": [_V, _D, _I64P, _I64P, _I64P],
+    "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
 }
 
 _lib = None
@@ -265,6 +268,14 @@ def ibim_timing_get(ctx):
     _check(lib().ibim_timing_get(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(inter), ctypes.byref(tot)))
     return {"pair_ms": ms.value, "pair_launches": n.value, "pair_interactions": inter.value,
             "total_launches": tot.value}
+
+
+def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=None):
+    """Allocation-free FP32 compensated product from caller-owned device arrays
+    (see include/ibim.h); synchronises the stream before returning."""
+    p = _phys(phys)
+    _check(lib().ibim_matvec_noalloc(int(N), _dptr(d_xstar), _dptr(d_normal), _dptr(d_w), ctypes.byref(p),
+                                     _dptr(d_in), _dptr(d_out), _stream(stream)))
 
 
 def ibim_destroy(ctx):
