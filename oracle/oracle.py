@@ -15,6 +15,7 @@ from . import build as _build
 __all__ = [
     "Phys", "lib", "num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
     "rhs", "psi_rxn", "gpol", "area", "sphere_nodes", "gmres", "KCAL_PER_E2_A",
+    "ls_grid", "grid_coords", "ls_ses", "ls_steps", "ls_band", "ses_nodes",
 ]
 
 # Coulomb constant in kcal mol^-1 Angstrom e^-2 times 4 pi: energies in the
@@ -219,3 +220,99 @@ def gmres(xs, nrm, w, phys, g, x0=None, tol=1e-8, restart=100, maxit=500):
     rc = lib().orc_gmres(N, _d(xs), _d(nrm), _d(w), ctypes.byref(P), _d(g), _d(x), float(tol),
                          int(restart), int(maxit), ctypes.byref(it), ctypes.byref(rr))
     return x, it.value, rr.value, rc == 0
+
+
+# ------------------------------------------------------------- level set (Sec. 3.1-3.2)
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64 * 3), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double)]
+
+
+def _ls_lib():
+    L = lib()
+    if not getattr(L, "_ls_ready", False):
+        G = ctypes.POINTER(_Grid)
+        L.orc_ls_grid.restype = None
+        L.orc_ls_grid.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, G]
+        L.orc_ls_vdw.restype = None
+        L.orc_ls_vdw.argtypes = [G, ctypes.c_int64, _D, _D, ctypes.c_double, _D]
+        L.orc_ls_eikonal.restype = ctypes.c_int
+        L.orc_ls_eikonal.argtypes = [G, _D, ctypes.c_double]
+        L.orc_ls_reinit.restype = ctypes.c_int
+        L.orc_ls_reinit.argtypes = [G, _D, ctypes.c_double]
+        L.orc_ls_cavity.restype = ctypes.c_int64
+        L.orc_ls_cavity.argtypes = [G, _D, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
+        L.orc_ls_band.restype = ctypes.c_int64
+        L.orc_ls_band.argtypes = [G, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D, _I32]
+        L.orc_ls_ses.restype = ctypes.c_int64
+        L.orc_ls_ses.argtypes = [G, ctypes.c_int64, _D, _D, ctypes.c_double, ctypes.c_double, _D]
+        L._ls_ready = True
+    return L
+
+
+def ls_grid(z, r, probe, h, eps):
+    """Grid box of the level-set construction: dict(lo, n, h)."""
+    z = _f64(z, (-1, 3))
+    r = _f64(r, -1)
+    g = _Grid()
+    _ls_lib().orc_ls_grid(r.shape[0], _d(z), _d(r), float(probe), float(h), float(eps), ctypes.byref(g))
+    return g
+
+
+def grid_coords(g):
+    """Node coordinates (n2, n1, n0, 3) of a level-set grid."""
+    ax = [g.h * (g.lo[a] + np.arange(g.n[a])) for a in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return np.stack([X, Y, Z], axis=-1)
+
+
+def ls_ses(z, r, probe=1.4, h=0.5, eps=1.0):
+    """Stage 1 (Sec. 3.1): phi_SES on the grid.  Returns (grid, phi (n2, n1, n0), changed)."""
+    z = _f64(z, (-1, 3))
+    r = _f64(r, -1)
+    g = ls_grid(z, r, probe, h, eps)
+    phi = np.empty(g.n[0] * g.n[1] * g.n[2])
+    ch = _ls_lib().orc_ls_ses(ctypes.byref(g), r.shape[0], _d(z), _d(r), float(probe), float(eps), _d(phi))
+    return g, phi.reshape(g.n[2], g.n[1], g.n[0]), ch
+
+
+def ls_steps(z, r, probe=1.4, h=0.5, eps=1.0):
+    """Stage 1 step by step: dict of the grids after F, eikonal flow, cavity removal, reinit."""
+    z = _f64(z, (-1, 3))
+    r = _f64(r, -1)
+    L = _ls_lib()
+    g = ls_grid(z, r, probe, h, eps)
+    M = g.n[0] * g.n[1] * g.n[2]
+    shape = (g.n[2], g.n[1], g.n[0])
+    F = np.empty(M)
+    L.orc_ls_vdw(ctypes.byref(g), r.shape[0], _d(z), _d(r), 2.0 * probe + eps + 6.0 * h, _d(F))
+    phi = F - probe
+    sas = phi.copy()
+    L.orc_ls_eikonal(ctypes.byref(g), _d(phi), float(probe))
+    flowed = phi.copy()
+    lab = np.zeros(M, dtype=np.uint8)
+    ch = L.orc_ls_cavity(ctypes.byref(g), _d(phi), float(eps), lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    cav = phi.copy()
+    L.orc_ls_reinit(ctypes.byref(g), _d(phi), float(eps))
+    return {"grid": g, "F": F.reshape(shape), "sas": sas.reshape(shape), "flowed": flowed.reshape(shape),
+            "labels": lab.reshape(shape), "cavity": cav.reshape(shape), "phi": phi.reshape(shape), "changed": ch}
+
+
+def ls_band(g, phi, eps):
+    """Band nodes of a level-set grid (Sec. 3.2): dict of xs, nrm, w, d, ijk (grid order)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+    L = _ls_lib()
+    n = L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), 0, None, None, None, None, None)
+    xs = np.empty((n, 3))
+    nrm = np.empty((n, 3))
+    w = np.empty(n)
+    d = np.empty(n)
+    ijk = np.empty((n, 3), dtype=np.int32)
+    L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), n, _d(xs), _d(nrm), _d(w), _d(d), ijk.ctypes.data_as(_I32))
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk}
+
+
+def ses_nodes(z, r, probe=1.4, h=0.5, eps=1.0):
+    """Stages 1-2: band nodes of the solvent excluded surface of atoms (z, r)."""
+    g, phi, _ = ls_ses(z, r, probe, h, eps)
+    return ls_band(g, phi, eps)
