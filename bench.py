@@ -33,10 +33,13 @@ if ROOT not in sys.path:
 
 WORKLOAD = {"workload": "kirkwood_sphere", "R": 20.0, "h": 0.5, "band_k": 2, "tau_k": 1.0, "n_charges": 50,
             "charge_ball": 16.0, "eps_in": 2.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64}
-# FP32-pipe (FFMA/FMUL/FADD) instructions per interaction of the compensated
-# pair kernel, counted from its source: geometry 16, kernel values 25,
-# two Kahan-compensated accumulations 8.
-F32_OPS_PER_INTERACTION = 49
+# FP32-pipe (FFMA/FMUL/FADD) instructions per interaction of the pair kernel's
+# far-field formula, counted from its source: pair geometry (r, |r|^2, s_x, s_y,
+# c) 15, rho and the two exponential arguments 3, kernel scalars (E x, 1-E, g,
+# 3-B, 1/rho^2, 1/rho^3, the two theta terms) 9, the four kernel products fused
+# into the two running sums 13.  The chunked compensation adds 0.5 per pair;
+# the two MUFU operations (rsqrt, ex2) run on the XU pipe and are not counted.
+F32_OPS_PER_INTERACTION = 40
 FP32_LANES_PER_SM = 128
 METRIC = "IBIM matvec interactions/s"
 
@@ -181,6 +184,7 @@ def run_ours(args):
     ctx.set_charges(z, q)
     N = ctx.N
     P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
+    tpt, bps, tune_ms = ctx.autotune(P)
     opts = dict(precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=1000, start=0, certify=0)
     dp = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -295,7 +299,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
-                               l2="256 MB buffer written between timed steps"),
+                               l2="256 MB buffer written between timed steps",
+                               f32_variant={"targets_per_thread": tpt, "ctas_per_sm": bps}),
                 "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
                 "wall_s_timed": wall}
         line.update(extra)

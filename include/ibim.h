@@ -74,6 +74,30 @@ typedef struct {
 /* ------------------------------------------------------------------ build */
 
 /*
+ * Solvent excluded surface of a molecule and its narrowband (paper Stages 1-2,
+ * Sec. 3.1-3.2), all on the GPU in FP64: vdW level set F = min_k(|x-z_k|-r_k)
+ * (clamped at 2 probe + band_eps + 6h), phi_SAS = F - probe, inward eikonal
+ * flow for t in (0, probe] (TVD-RK3, Godunov, WENO5, zero Neumann), cavity
+ * removal (flood fill of phi > 0 from the box boundary; other phi > 0 nodes and
+ * every node within band_eps of them set to -band_eps), reinitialisation
+ * (ceil((k1+4)/k0) steps, dt = k0 h, k0 = 1/2, k1 = band_eps/h), band
+ * {|phi| < band_eps} with WENO5 normals, projections x* = x - phi n and
+ * weights delta_eps(phi) h^3.  Grid: nodes h * (integer coordinates) covering
+ * the atoms' extent plus probe + band_eps + 8h.  Nodes are in Morton order.
+ *   xyz: Na x 3 host centres (A); radii: Na host (> 0); charges: Na host or
+ *   NULL (when given they become the context's charges at the centres);
+ *   probe >= 0 (rho0), h > 0, band_eps > 0 (eps).
+ * Errors: IBIM_ERR_ARG, IBIM_ERR_NONFINITE, IBIM_ERR_EMPTY_BAND, IBIM_ERR_CUDA.
+ */
+ibim_status ibim_build(const double* xyz, const double* radii, const double* charges, int64_t Na, double probe,
+                       double h, double band_eps, void* stream, ibim_ctx** out);
+
+/* Level-set grid of a context built by ibim_build: integer coordinate of node
+ * (0,0,0) in lo[3], node counts in n[3], and (when phi is not NULL) the final
+ * phi on the grid, n[0] n[1] n[2] doubles with x fastest.  Synchronises. */
+ibim_status ibim_get_levelset(const ibim_ctx* ctx, int64_t* lo, int64_t* n, double* phi);
+
+/*
  * Narrowband of an analytic sphere (signed distance d(x) = |x - c| - R),
  * Sec. 2.2 and Sec. 3.2 with J = 1.  Grid U_h = origin + h Z^3; nodes with
  * |d| < band_eps are kept, x* = c + R (x - c)/|x - c|, n = (x - c)/|x - c|,
@@ -182,6 +206,23 @@ ibim_status ibim_solve(ibim_ctx* ctx, const ibim_phys* phys, const ibim_solve_op
 ibim_status ibim_solve_host(ibim_ctx* ctx, const ibim_phys* phys, const ibim_solve_opts* opts,
                             int64_t Nc, const double* z, const double* q, double* h_p,
                             ibim_solve_info* info);
+
+/* ---------------------------------------------------------------- tuning */
+
+/*
+ * Autotuner of the FP32 pair-sum kernel (not part of the paper's method):
+ * times every variant (2 or 4 targets per thread; the occupancy-limited
+ * number of CTAs per SM or half of it) on this context's geometry with CUDA
+ * events, keeps the fastest for this context and caches it for contexts built
+ * later in the process with N in the same power-of-two bucket.  Outputs may be
+ * NULL.  Synchronises; call it outside any stream capture.
+ */
+ibim_status ibim_autotune(ibim_ctx* ctx, const ibim_phys* phys, int* targets_per_thread, int* ctas_per_sm,
+                          double* best_ms);
+
+/* Manual choice of the FP32 pair-kernel variant: targets_per_thread 2 or 4,
+ * ctas_per_sm >= 1 (clamped to the occupancy limit) or 0 for the limit. */
+ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int targets_per_thread, int ctas_per_sm);
 
 /* ------------------------------------------------- allocation-free variant */
 

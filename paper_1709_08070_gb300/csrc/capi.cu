@@ -142,7 +142,7 @@ ibim_status apply_operator(ibim_ctx* c, const PairConsts& k, int precision, VecR
 {
     const int64_t N = c->N;
     if (precision == IBIM_F32C) {
-        const PairSchedule s = make_schedule(N, kF32TTile, N, kF32STile, f32_grid_cap(c));
+        const PairSchedule s = f32_schedule(c);
         IBIM_TRY(f32_pack(c, in, d_skip));
         IBIM_TRY(timing_begin(c));
         IBIM_TRY(f32_pairs(c, k, s, d_skip));
@@ -211,6 +211,9 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_ijk);
     cudaFree(c->d_pos32);
     cudaFree(c->d_nrm32);
+    cudaFree(c->d_tb32_2);
+    cudaFree(c->d_tb32_4);
+    cudaFree(c->d_sb32);
     cudaFree(c->d_z);
     cudaFree(c->d_q);
     cudaFree(c->d_src);
@@ -218,6 +221,7 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_red);
     cudaFree(c->d_err);
     cudaFree(c->d_io);
+    cudaFree(c->d_phi);
     delete c;
 }
 
@@ -246,6 +250,55 @@ ibim_status ibim_build_sphere(double R, const double* centre, const double* orig
         return s;
     }
     *out = c;
+    return IBIM_OK;
+}
+
+ibim_status ibim_build(const double* xyz, const double* radii, const double* charges, int64_t Na, double probe,
+                       double h, double band_eps, void* stream, ibim_ctx** out)
+{
+    if (xyz == nullptr || radii == nullptr || Na < 1) return fail(IBIM_ERR_ARG, "need Na >= 1 atoms with centres and radii");
+    if (!(h > 0.0) || !(band_eps > 0.0) || !(probe >= 0.0) || !isfinite(h) || !isfinite(band_eps) || !isfinite(probe))
+        return fail(IBIM_ERR_ARG, "need h > 0, band_eps > 0, probe >= 0 (finite)");
+    double cen[3] = {0, 0, 0};
+    for (int64_t k = 0; k < Na; ++k) {
+        if (!isfinite(radii[k]) || !(radii[k] > 0.0)) return fail(IBIM_ERR_ARG, "atom radii must be finite and > 0");
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(xyz[3 * k + a])) return fail(IBIM_ERR_NONFINITE, "non-finite atom centre");
+            cen[a] += xyz[3 * k + a];
+        }
+        if (charges != nullptr && !isfinite(charges[k])) return fail(IBIM_ERR_NONFINITE, "non-finite charge");
+    }
+    ibim_ctx* c = nullptr;
+    IBIM_TRY(ctx_new(stream, &c));
+    c->h = h;
+    for (int a = 0; a < 3; ++a) c->centroid[a] = cen[a] / (double)Na;
+    ibim_status s = build_levelset(c, Na, xyz, radii, probe, h, band_eps);
+    if (s == IBIM_OK) s = finish_geometry(c);
+    if (s == IBIM_OK && charges != nullptr) s = ibim_set_charges(c, Na, xyz, charges);
+    if (s != IBIM_OK) {
+        std::string msg = g_err;
+        ibim_destroy(c);
+        g_err = msg;
+        return s;
+    }
+    *out = c;
+    return IBIM_OK;
+}
+
+ibim_status ibim_get_levelset(const ibim_ctx* cc, int64_t* lo, int64_t* n, double* phi)
+{
+    if (cc == nullptr) return fail(IBIM_ERR_ARG, "ctx is NULL");
+    ibim_ctx* c = const_cast<ibim_ctx*>(cc);
+    if (c->d_phi == nullptr) return fail(IBIM_ERR_STATE, "context was not built from atoms");
+    for (int a = 0; a < 3; ++a) {
+        if (lo) lo[a] = c->ls_lo[a];
+        if (n) n[a] = c->ls_n[a];
+    }
+    if (phi != nullptr) {
+        const int64_t M = c->ls_n[0] * c->ls_n[1] * c->ls_n[2];
+        IBIM_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+        IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    }
     return IBIM_OK;
 }
 

@@ -201,6 +201,8 @@ ibim_status finish_geometry(ibim_ctx* c)
         c->d_geo64, N, c->centroid[0], c->centroid[1], c->centroid[2], c->d_pos32, c->d_nrm32);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
+    IBIM_TRY(f32_tile_bounds(c));
+    apply_cached_tuning(c);
     IBIM_CUDA(cudaStreamSynchronize(c->stream));
     return IBIM_OK;
 }

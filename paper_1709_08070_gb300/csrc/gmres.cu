@@ -386,8 +386,9 @@ static ibim_status capture_step(ibim_ctx* c, const PairConsts& k, int precision)
     // make sure every workspace the step touches exists before capture
     if (precision == IBIM_F32C) {
         IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 2 * sizeof(float4)));
-        const PairSchedule s = make_schedule(c->N, kF32TTile, c->N, kF32STile, f32_grid_cap(c));
-        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, (size_t)s.grid * s.max_segs * 2 * kF32TTile * sizeof(double)));
+        const PairSchedule s = f32_schedule(c);
+        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes,
+                        (size_t)s.grid * s.max_segs * 2 * f32_ttile(c) * sizeof(double)));
     } else {
         IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 8 * sizeof(double)));
         const PairSchedule s = make_schedule(c->N, kF64TTile, c->N, kF64STile, f64_grid_cap(c));

@@ -37,7 +37,7 @@ enum : unsigned { kDevErrTimeout = 1u, kDevErrBounds = 2u };
 // thread owns kF32Tpt targets, sources stream through shared memory in tiles
 // of kF32STile nodes (two float4 per node).
 constexpr int kF32Threads = 128;
-constexpr int kF32Tpt = 2;
+constexpr int kF32Tpt = 4;
 constexpr int kF32TTile = kF32Threads * kF32Tpt;
 constexpr int kF32STile = 256;
 constexpr int kF32Stages = 2;
@@ -100,6 +100,20 @@ struct ibim_ctx {
     // FP32 geometry: float4 (x* - centroid, w) and float4 (n, 0)
     float4* d_pos32 = nullptr;
     float4* d_nrm32 = nullptr;
+    // bounding spheres (centre, radius) of FP32 target tiles (for 2 and 4
+    // targets per thread) and of source tiles
+    float4* d_tb32_2 = nullptr;
+    float4* d_tb32_4 = nullptr;
+    float4* d_sb32 = nullptr;
+    // level-set grid of contexts built from atoms (kept for inspection)
+    double* d_phi = nullptr;
+    int64_t ls_lo[3] = {0, 0, 0};
+    int64_t ls_n[3] = {0, 0, 0};
+    int64_t ls_cavity_nodes = 0;
+    // FP32 pair-kernel variant: targets per thread and CTAs per SM (0 = occupancy limit)
+    int f32_tpt = 2;
+    int f32_bps = 0;
+    int tuned = 0;
     // charges
     int64_t Nc = 0;
     double* d_z = nullptr;  // Nc x 3
@@ -156,6 +170,10 @@ ibim_status f32_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, c
 ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, VecRef in, OutRef out,
                       const int* d_skip);
 int f32_grid_cap(ibim_ctx* c);
+int f32_ttile(const ibim_ctx* c);
+int f32_max_bps(int tpt);
+PairSchedule f32_schedule(ibim_ctx* c);
+ibim_status f32_tile_bounds(ibim_ctx* c);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,
                          OutRef out, const int* d_skip);
 // FP64 path pieces (pair_f64.cu)
@@ -175,6 +193,10 @@ ibim_status area_launch(ibim_ctx* c, double* area_host);
 ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, const double* origin,
                                double h, double eps);
 ibim_status finish_geometry(ibim_ctx* c);  // FP32 packing relative to c->centroid
+// Level-set SES (levelset.cu)
+ibim_status build_levelset(ibim_ctx* c, int64_t Na, const double* z, const double* r, double probe, double h,
+                           double eps);
+void apply_cached_tuning(ibim_ctx* c);      // tune.cu
 
 // GMRES (gmres.cu)
 ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& o, double* d_p,

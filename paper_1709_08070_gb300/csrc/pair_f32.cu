@@ -8,19 +8,28 @@
 //   K21 = [(1 - A) c - (3 - B) s_x s_y / rho^2] / rho^3
 //   K22 = -s_x (1 - th2 A) / rho^3
 // where E = exp(-kappa rho), A = E (1 + kappa rho), B = E (3 + 3 kappa rho + kappa^2 rho^2).
-// The differences 1 - A and 3 - B cancel for small x = kappa rho; they are
-// formed as g = 1 - A and 3 - B = 3 g - E x^2, with g taken from its Taylor
-// series in x (from the exponential series) when any lane of the warp has
-// x < 0.5, and 1 - E = g + E x.
+// With x = kappa rho the differences are formed as g = 1 - A = (1 - E) - E x,
+// 3 - B = 3 g - E x^2 and 1 - E = g + E x.
 //
 // Schedule: persistent CTAs walk a stream-K range of (target tile, source
 // tile) steps.  Source tiles (kF32STile nodes, 32 B each) are brought into
 // shared memory by bulk async copies with an mbarrier per stage (double
-// buffered).  Each thread owns kF32Tpt targets; per target the two sums are
-// Kahan-compensated in FP32 within a source tile and the tile result is added
-// to FP64 accumulators.  Every CTA writes one FP64 partial per target tile it
-// touched; the fixup kernel adds the partials, scales by 1/(4 pi) and adds
-// the diagonal Lambda p.
+// buffered).  Each thread owns TPT targets.
+//
+// Near/far split: every step compares the bounding spheres of its target tile
+// and source tile.  When they are at least `far_dist` apart (>= 2 tau and
+// >= 1.5 A), no pair of the step can lie in the regularisation tube
+// (tube rule 0) and the cancellation in g is harmless, so the step runs a
+// branch-free loop with no tube masks.  Otherwise every pair gets the tube
+// test and, when any lane of the warp has x < 0.5, g from its Taylor series
+// (from the exponential series).  The choice is uniform over the CTA.
+//
+// Accumulation: per target the two sums run in FP32 over chunks of
+// kChunk sources (fused into the FMAs), each chunk sum is Kahan-added into a
+// compensated FP32 pair (s, c), and at the end of each source tile the
+// compensated value s - c is added to FP64 accumulators.  Every CTA writes one
+// FP64 partial per target tile it touched; the fixup kernel adds the
+// partials, scales by 1/(4 pi) and adds the diagonal Lambda p.
 #include "ibim_internal.cuh"
 #include "ptx.cuh"
 
@@ -28,7 +37,10 @@ namespace ibim {
 
 struct F32Consts {
     float th1, th2, omth1, omth2;
-    float kappa, tau2, four_tau2, k12t;
+    float kappa, kl2e;        // kappa and -kappa log2(e)
+    float tau2, four_tau2, k12t;
+    float far_dist;           // minimum bounding-sphere gap of a far step (A)
+    int rule0;                // tube rule 0 (far steps allowed)
 };
 
 static F32Consts f32_consts(const PairConsts& k)
@@ -39,9 +51,13 @@ static F32Consts f32_consts(const PairConsts& k)
     c.omth1 = (float)(1.0 - k.th1);
     c.omth2 = (float)(1.0 - k.th2);
     c.kappa = (float)k.kappa;
+    c.kl2e = (float)(-k.kappa * 1.4426950408889634);
     c.tau2 = (float)k.tau2;
-    c.four_tau2 = (k.four_tau2 > 3.0e38) ? __builtin_huge_valf() : (float)k.four_tau2;
+    c.rule0 = (k.four_tau2 < 3.0e38) ? 1 : 0;
+    c.four_tau2 = c.rule0 ? (float)k.four_tau2 : __builtin_huge_valf();
     c.k12t = (float)k.k12_tube;
+    const double two_tau = 2.0 * sqrt(k.tau2);
+    c.far_dist = (float)((two_tau > 1.5 ? two_tau : 1.5) * 1.001 + 1e-3);
     return c;
 }
 
@@ -68,14 +84,46 @@ __device__ __forceinline__ float g_series(float x)
     return p * x * x;
 }
 
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kChunk = 16;
 
+// Far pair: no tube, exp-form g.  Accumulates into t1, t2.
+__device__ __forceinline__ void pair_far(const float3& xi, const float3& ni, const float4& y, const float4& m,
+                                         const F32Consts& k, float& t1, float& t2)
+{
+    const float rx = xi.x - y.x, ry = xi.y - y.y, rz = xi.z - y.z;
+    const float rr = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float sx = fmaf(rx, ni.x, fmaf(ry, ni.y, rz * ni.z));
+    const float sy = fmaf(rx, m.x, fmaf(ry, m.y, rz * m.z));
+    const float cc = fmaf(ni.x, m.x, fmaf(ni.y, m.y, ni.z * m.z));
+    const float inv = ptx::rsqrt_approx(rr);
+    const float rho = rr * inv;
+    const float x = k.kappa * rho;
+    const float E = ptx::ex2_approx(rho * k.kl2e);
+    const float Ex = E * x;
+    const float f = 1.0f - E;
+    const float g = f - Ex;
+    const float hh = fmaf(3.0f, g, -Ex * x);
+    const float inv2 = inv * inv;
+    const float inv3 = inv2 * inv;
+    const float u1 = fmaf(k.th1, g, k.omth1);
+    const float u2 = fmaf(k.th2, g, k.omth2);
+    const float A1 = inv3 * y.w;
+    t1 = fmaf(sy * u1, A1, t1);
+    t1 = fmaf(-f, inv * m.w, t1);
+    const float w21 = fmaf(g, cc, -(hh * sx) * (sy * inv2));
+    t2 = fmaf(w21, A1, t2);
+    t2 = fmaf(sx * u2, inv3 * m.w, t2);
+}
+
+template <int TPT>
 __global__ void __launch_bounds__(kF32Threads)
     pair_f32_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm,
                     const float4* __restrict__ src, int64_t N, PairSchedule s, F32Consts k,
-                    double* __restrict__ part, unsigned* __restrict__ err, const int* __restrict__ skip)
+                    double* __restrict__ part, unsigned* __restrict__ err, const int* __restrict__ skip,
+                    const float4* __restrict__ tbound, const float4* __restrict__ sbound)
 {
+    constexpr int TTILE = kF32Threads * TPT;
     if (skip != nullptr && *skip) return;
     __shared__ __align__(128) float4 sbuf[kF32Stages][2 * kF32STile];
     __shared__ __align__(8) uint64_t bars[kF32Stages];
@@ -107,13 +155,14 @@ __global__ void __launch_bounds__(kF32Threads)
 
     const int64_t t_first = s0 / s.n_stiles;
     int64_t t = t_first;
-    float3 xi[kF32Tpt], ni[kF32Tpt];
-    double D1[kF32Tpt], D2[kF32Tpt];
+    float3 xi[TPT], ni[TPT];
+    double D1[TPT], D2[TPT];
+    float4 tb = make_float4(0.0f, 0.0f, 0.0f, __builtin_huge_valf());
 
     auto load_targets = [&](int64_t tile) {
 #pragma unroll
-        for (int q = 0; q < kF32Tpt; ++q) {
-            const int64_t i = tile * kF32TTile + q * kF32Threads + tid;
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t i = tile * TTILE + q * kF32Threads + tid;
             if (i < N) {
                 const float4 a = tpos[i];
                 const float4 b = tnrm[i];
@@ -126,6 +175,7 @@ __global__ void __launch_bounds__(kF32Threads)
             D1[q] = 0.0;
             D2[q] = 0.0;
         }
+        if (tbound != nullptr) tb = tbound[tile];
     };
     load_targets(t);
 
@@ -144,60 +194,99 @@ __global__ void __launch_bounds__(kF32Threads)
         const int cnt = (int)((N - j0 < kF32STile) ? N - j0 : kF32STile);
         const float4* sb = &sbuf[stage][0];
 
-        float S1[kF32Tpt], C1[kF32Tpt], S2[kF32Tpt], C2[kF32Tpt];
-#pragma unroll
-        for (int q = 0; q < kF32Tpt; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+        bool far = false;
+        if (tbound != nullptr && k.rule0) {
+            const float4 b = sbound[st];
+            const float dx = tb.x - b.x, dy = tb.y - b.y, dz = tb.z - b.z;
+            const float lim = k.far_dist + tb.w + b.w;
+            far = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim;
+        }
 
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j) {
-            const float4 y = sb[2 * j];
-            const float4 m = sb[2 * j + 1];
-            float rr[kF32Tpt], sx[kF32Tpt], sy[kF32Tpt], cc[kF32Tpt], inv[kF32Tpt], x[kF32Tpt],
-                E[kF32Tpt];
-            bool tube[kF32Tpt];
-            bool need = false;
+        float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
 #pragma unroll
-            for (int q = 0; q < kF32Tpt; ++q) {
-                const float rx = xi[q].x - y.x, ry = xi[q].y - y.y, rz = xi[q].z - y.z;
-                rr[q] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                sx[q] = fmaf(rx, ni[q].x, fmaf(ry, ni[q].y, rz * ni[q].z));
-                sy[q] = fmaf(rx, m.x, fmaf(ry, m.y, rz * m.z));
-                cc[q] = fmaf(ni[q].x, m.x, fmaf(ni[q].y, m.y, ni[q].z * m.z));
-                const float rp2 = fmaf(-sx[q], sx[q], rr[q]);
-                tube[q] = (rp2 < k.tau2) & (rr[q] < k.four_tau2);
-                const float rrs = fmaxf(rr[q], 1.0e-30f);
-                inv[q] = ptx::rsqrt_approx(rrs);
-                const float rho = rrs * inv[q];
-                x[q] = k.kappa * rho;
-                E[q] = ptx::ex2_approx(x[q] * -kLog2e);
-                need |= (x[q] < 0.5f);
-            }
-            const bool series = __any_sync(0xffffffffu, need);
+        for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+
+        if (far) {
+            for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                const int c1 = (c0 + kChunk < cnt) ? c0 + kChunk : cnt;
+                float t1[TPT], t2[TPT];
 #pragma unroll
-            for (int q = 0; q < kF32Tpt; ++q) {
-                const float Ex = E[q] * x[q];
-                float f = 1.0f - E[q];
-                float g = f - Ex;
-                if (series && x[q] < 0.5f) {
-                    g = g_series(x[q]);
-                    f = g + Ex;
+                for (int q = 0; q < TPT; ++q) t1[q] = t2[q] = 0.0f;
+#pragma unroll 4
+                for (int j = c0; j < c1; ++j) {
+                    const float4 y = sb[2 * j];
+                    const float4 m = sb[2 * j + 1];
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) pair_far(xi[q], ni[q], y, m, k, t1[q], t2[q]);
                 }
-                const float hh = fmaf(3.0f, g, -Ex * x[q]);
-                const float inv2 = inv[q] * inv[q];
-                const float inv3 = inv2 * inv[q];
-                const float u1 = fmaf(k.th1, g, k.omth1);
-                const float u2 = fmaf(k.th2, g, k.omth2);
-                const float i3 = tube[q] ? 0.0f : inv3;
-                const float Q = tube[q] ? k.k12t : f * inv[q];
-                const float v1 = fmaf(i3, sy[q] * u1 * y.w, -Q * m.w);
-                const float w21 = fmaf(g, cc[q], -hh * sx[q] * sy[q] * inv2);
-                const float v2 = i3 * fmaf(w21, y.w, sx[q] * u2 * m.w);
-                kahan_add(S1[q], C1[q], v1);
-                kahan_add(S2[q], C2[q], v2);
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) {
+                    kahan_add(S1[q], C1[q], t1[q]);
+                    kahan_add(S2[q], C2[q], t2[q]);
+                }
+            }
+        } else {
+            for (int c0 = 0; c0 < cnt; c0 += kChunk) {
+                const int c1 = (c0 + kChunk < cnt) ? c0 + kChunk : cnt;
+                float t1[TPT], t2[TPT];
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) t1[q] = t2[q] = 0.0f;
+                for (int j = c0; j < c1; ++j) {
+                    const float4 y = sb[2 * j];
+                    const float4 m = sb[2 * j + 1];
+                    float rr[TPT], sx[TPT], sy[TPT], cc[TPT], inv[TPT], x[TPT], E[TPT];
+                    bool tube[TPT];
+                    bool need = false;
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) {
+                        const float rx = xi[q].x - y.x, ry = xi[q].y - y.y, rz = xi[q].z - y.z;
+                        rr[q] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        sx[q] = fmaf(rx, ni[q].x, fmaf(ry, ni[q].y, rz * ni[q].z));
+                        sy[q] = fmaf(rx, m.x, fmaf(ry, m.y, rz * m.z));
+                        cc[q] = fmaf(ni[q].x, m.x, fmaf(ni[q].y, m.y, ni[q].z * m.z));
+                        const float rp2 = fmaf(-sx[q], sx[q], rr[q]);
+                        tube[q] = (rp2 < k.tau2) & (rr[q] < k.four_tau2);
+                        const float rrs = fmaxf(rr[q], 1.0e-30f);
+                        inv[q] = ptx::rsqrt_approx(rrs);
+                        const float rho = rrs * inv[q];
+                        x[q] = k.kappa * rho;
+                        E[q] = ptx::ex2_approx(rho * k.kl2e);
+                        need |= (x[q] < 0.5f);
+                    }
+                    const bool series = __any_sync(0xffffffffu, need);
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) {
+                        const float Ex = E[q] * x[q];
+                        float f = 1.0f - E[q];
+                        float g = f - Ex;
+                        if (series && x[q] < 0.5f) {
+                            g = g_series(x[q]);
+                            f = g + Ex;
+                        }
+                        const float hh = fmaf(3.0f, g, -Ex * x[q]);
+                        const float inv2 = inv[q] * inv[q];
+                        const float inv3 = inv2 * inv[q];
+                        const float u1 = fmaf(k.th1, g, k.omth1);
+                        const float u2 = fmaf(k.th2, g, k.omth2);
+                        const float i3 = tube[q] ? 0.0f : inv3;
+                        const float Q = tube[q] ? k.k12t : f * inv[q];
+                        const float A1 = i3 * y.w;
+                        t1[q] = fmaf(sy[q] * u1, A1, t1[q]);
+                        t1[q] = fmaf(-Q, m.w, t1[q]);
+                        const float w21 = fmaf(g, cc[q], -(hh * sx[q]) * (sy[q] * inv2));
+                        t2[q] = fmaf(w21, A1, t2[q]);
+                        t2[q] = fmaf(sx[q] * u2, i3 * m.w, t2[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) {
+                    kahan_add(S1[q], C1[q], t1[q]);
+                    kahan_add(S2[q], C2[q], t2[q]);
+                }
             }
         }
 #pragma unroll
-        for (int q = 0; q < kF32Tpt; ++q) {
+        for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
             D2[q] += (double)S2[q] - (double)C2[q];
         }
@@ -209,11 +298,11 @@ __global__ void __launch_bounds__(kF32Threads)
 
         if (st == s.n_stiles - 1 || u + 1 == s1) {
             const int seg = (int)(t - t_first);
-            double* dst = part + ((int64_t)blockIdx.x * s.max_segs + seg) * 2 * kF32TTile;
+            double* dst = part + ((int64_t)blockIdx.x * s.max_segs + seg) * 2 * TTILE;
 #pragma unroll
-            for (int q = 0; q < kF32Tpt; ++q) {
+            for (int q = 0; q < TPT; ++q) {
                 dst[q * kF32Threads + tid] = D1[q];
-                dst[kF32TTile + q * kF32Threads + tid] = D2[q];
+                dst[TTILE + q * kF32Threads + tid] = D2[q];
             }
             if (st == s.n_stiles - 1 && u + 1 < s1) {
                 ++t;
@@ -221,6 +310,45 @@ __global__ void __launch_bounds__(kF32Threads)
             }
         }
     }
+}
+
+// Bounding sphere (centre, radius) of each tile of `tile` consecutive nodes,
+// in the FP32 centroid frame, radius padded by 1e-3 A for rounding.
+__global__ void tile_bounds_kernel(const float4* __restrict__ pos, int64_t N, int tile, float4* __restrict__ out)
+{
+    __shared__ float red[4][256];
+    const int64_t j0 = (int64_t)blockIdx.x * tile;
+    const int64_t j1 = (j0 + tile < N) ? j0 + tile : N;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        sx += pos[j].x;
+        sy += pos[j].y;
+        sz += pos[j].z;
+    }
+    red[0][threadIdx.x] = sx;
+    red[1][threadIdx.x] = sy;
+    red[2][threadIdx.x] = sz;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) red[a][threadIdx.x] += red[a][threadIdx.x + o];
+        __syncthreads();
+    }
+    const float inv = 1.0f / (float)(j1 - j0);
+    const float cx = red[0][0] * inv, cy = red[1][0] * inv, cz = red[2][0] * inv;
+    __syncthreads();
+    float r2 = 0.0f;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const float dx = pos[j].x - cx, dy = pos[j].y - cy, dz = pos[j].z - cz;
+        r2 = fmaxf(r2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    red[3][threadIdx.x] = r2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[3][threadIdx.x] = fmaxf(red[3][threadIdx.x], red[3][threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = make_float4(cx, cy, cz, sqrtf(red[3][0]) * 1.0001f + 1e-3f);
 }
 
 // Source payload: node j -> float4 (y* - centroid, w psi), float4 (n, w psin).
@@ -264,12 +392,47 @@ __global__ void fixup_kernel(const double* __restrict__ part, PairSchedule s, in
     y[N + i] = lambda2 * p[N + i] + kInv4Pi * a2;
 }
 
-int f32_grid_cap(ibim_ctx* c)
+static int occupancy_per_sm(int tpt)
 {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel, kF32Threads, 0);
-    if (occ < 1) occ = 1;
-    return occ * c->num_sms;
+    if (tpt == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel<4>, kF32Threads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel<2>, kF32Threads, 0);
+    return occ < 1 ? 1 : occ;
+}
+
+int f32_max_bps(int tpt) { return occupancy_per_sm(tpt); }
+
+int f32_ttile(const ibim_ctx* c) { return kF32Threads * (c->f32_tpt == 4 ? 4 : 2); }
+
+int f32_grid_cap(ibim_ctx* c)
+{
+    const int occ = occupancy_per_sm(c->f32_tpt);
+    const int bps = (c->f32_bps > 0 && c->f32_bps < occ) ? c->f32_bps : occ;
+    return bps * c->num_sms;
+}
+
+PairSchedule f32_schedule(ibim_ctx* c)
+{
+    return make_schedule(c->N, f32_ttile(c), c->N, kF32STile, f32_grid_cap(c));
+}
+
+ibim_status f32_tile_bounds(ibim_ctx* c)
+{
+    const int64_t N = c->N;
+    const int64_t n2 = (N + 2 * kF32Threads - 1) / (2 * kF32Threads);
+    const int64_t n4 = (N + 4 * kF32Threads - 1) / (4 * kF32Threads);
+    const int64_t ns = (N + kF32STile - 1) / kF32STile;
+    IBIM_CUDA(cudaMalloc((void**)&c->d_tb32_2, sizeof(float4) * n2));
+    IBIM_CUDA(cudaMalloc((void**)&c->d_tb32_4, sizeof(float4) * n4));
+    IBIM_CUDA(cudaMalloc((void**)&c->d_sb32, sizeof(float4) * ns));
+    tile_bounds_kernel<<<(unsigned)n2, 256, 0, c->stream>>>(c->d_pos32, N, 2 * kF32Threads, c->d_tb32_2);
+    tile_bounds_kernel<<<(unsigned)n4, 256, 0, c->stream>>>(c->d_pos32, N, 4 * kF32Threads, c->d_tb32_4);
+    tile_bounds_kernel<<<(unsigned)ns, 256, 0, c->stream>>>(c->d_pos32, N, kF32STile, c->d_sb32);
+    count_launch(c, 3);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
 }
 
 ibim_status f32_pack(ibim_ctx* c, VecRef in, const int* d_skip)
@@ -287,12 +450,18 @@ ibim_status f32_pack(ibim_ctx* c, VecRef in, const int* d_skip)
 
 ibim_status f32_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, const int* d_skip)
 {
-    const size_t need = (size_t)s.grid * s.max_segs * 2 * kF32TTile * sizeof(double);
+    const int ttile = f32_ttile(c);
+    const size_t need = (size_t)s.grid * s.max_segs * 2 * ttile * sizeof(double);
     IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, need));
-    pair_f32_kernel<<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32,
-                                                            (const float4*)c->d_src, c->N, s,
-                                                            f32_consts(k), c->d_part, c->d_err,
-                                                            d_skip);
+    const F32Consts kk = f32_consts(k);
+    if (ttile == 4 * kF32Threads)
+        pair_f32_kernel<4><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, (const float4*)c->d_src,
+                                                                   c->N, s, kk, c->d_part, c->d_err, d_skip,
+                                                                   c->d_tb32_4, c->d_sb32);
+    else
+        pair_f32_kernel<2><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, (const float4*)c->d_src,
+                                                                   c->N, s, kk, c->d_part, c->d_err, d_skip,
+                                                                   c->d_tb32_2, c->d_sb32);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -312,22 +481,18 @@ ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s
 ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, VecRef in, OutRef out,
                       const int* d_skip)
 {
-    return fixup_launch(c, k, s, kF32TTile, in, out, d_skip);
+    return fixup_launch(c, k, s, f32_ttile(c), in, out, d_skip);
 }
 
 // Launchers on caller-supplied buffers (used by the allocation-free entry point).
-int f32_occupancy_per_sm()
-{
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel, kF32Threads, 0);
-    return occ < 1 ? 1 : occ;
-}
+int f32_occupancy_per_sm() { return occupancy_per_sm(kF32Tpt); }
 
 cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
                                 const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
                                 cudaStream_t stream)
 {
-    pair_f32_kernel<<<s.grid, kF32Threads, 0, stream>>>(tpos, tnrm, src, N, s, f32_consts(k), part, err, nullptr);
+    pair_f32_kernel<kF32Tpt><<<s.grid, kF32Threads, 0, stream>>>(tpos, tnrm, src, N, s, f32_consts(k), part, err,
+                                                                  nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 

@@ -15,10 +15,10 @@ from . import build as _build
 
 __all__ = [
     "IbimError", "Phys", "SolveOpts", "SolveInfo", "lib", "library_path",
-    "ibim_build_sphere", "ibim_build_from_nodes", "ibim_set_charges", "ibim_num_nodes", "ibim_get_nodes",
+    "ibim_build", "ibim_get_levelset", "ibim_build_sphere", "ibim_build_from_nodes", "ibim_set_charges", "ibim_num_nodes", "ibim_get_nodes",
     "ibim_matvec", "ibim_matvec_host", "ibim_rhs", "ibim_energy", "ibim_area", "ibim_solve", "ibim_solve_host",
     "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
-    "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES",
+    "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A",
 ]
 
@@ -78,6 +78,10 @@ _SIGS = {
     "ibim_timing_reset": [_V],
     "ibim_timing_get": [_V, _D, _I64P, _I64P, _I64P],
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
+    "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
+    "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
+    "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
+    "ibim_get_levelset": [_V, _I64P, _I64P, _D],
 }
 
 _lib = None
@@ -149,6 +153,25 @@ def _phys(p):
 
 
 # ----------------------------------------------------------------- raw calls
+
+def ibim_build(xyz, radii, charges, probe, h, band_eps, stream=None):
+    z = _host(xyz).reshape(-1, 3)
+    r = _host(radii).reshape(-1)
+    q = None if charges is None else _host(charges).reshape(-1)
+    ctx = _V()
+    _check(lib().ibim_build(z.ctypes.data_as(_D), r.ctypes.data_as(_D), None if q is None else q.ctypes.data_as(_D),
+                            r.shape[0], float(probe), float(h), float(band_eps), _stream(stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def ibim_get_levelset(ctx):
+    lo = (ctypes.c_int64 * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(lib().ibim_get_levelset(ctx, lo, n, None))
+    phi = np.empty(n[0] * n[1] * n[2])
+    _check(lib().ibim_get_levelset(ctx, lo, n, phi.ctypes.data_as(_D)))
+    return list(lo), list(n), phi.reshape(n[2], n[1], n[0])
+
 
 def ibim_build_sphere(R, centre, origin, h, band_eps, stream=None):
     c = _host(centre)
@@ -278,6 +301,20 @@ def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=Non
                                      _dptr(d_in), _dptr(d_out), _stream(stream)))
 
 
+def ibim_autotune(ctx, phys):
+    """Pick the fastest FP32 pair-kernel variant; returns (targets_per_thread, ctas_per_sm, ms)."""
+    p = _phys(phys)
+    t = ctypes.c_int(0)
+    b = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().ibim_autotune(ctx, ctypes.byref(p), ctypes.byref(t), ctypes.byref(b), ctypes.byref(ms)))
+    return t.value, b.value, ms.value
+
+
+def ibim_set_f32_variant(ctx, targets_per_thread, ctas_per_sm=0):
+    _check(lib().ibim_set_f32_variant(ctx, int(targets_per_thread), int(ctas_per_sm)))
+
+
 def ibim_destroy(ctx):
     if ctx:
         lib().ibim_destroy(ctx)
@@ -292,6 +329,13 @@ class Context:
     @classmethod
     def sphere(cls, R, centre=(0.0, 0.0, 0.0), h=0.25, band_eps=None, origin=None, stream=None):
         return cls(ibim_build_sphere(R, centre, origin, h, 2 * h if band_eps is None else band_eps, stream))
+
+    @classmethod
+    def molecule(cls, xyz, radii, charges=None, probe=1.4, h=0.5, band_eps=None, stream=None):
+        return cls(ibim_build(xyz, radii, charges, probe, h, 2 * h if band_eps is None else band_eps, stream))
+
+    def levelset(self):
+        return ibim_get_levelset(self.handle)
 
     @classmethod
     def from_nodes(cls, xstar, normal, w, h, stream=None):
@@ -327,6 +371,12 @@ class Context:
 
     def solve_host(self, phys, z, q, h_p=None, **opts):
         return ibim_solve_host(self.handle, phys, z, q, h_p, **opts)
+
+    def autotune(self, phys):
+        return ibim_autotune(self.handle, phys)
+
+    def set_f32_variant(self, targets_per_thread, ctas_per_sm=0):
+        ibim_set_f32_variant(self.handle, targets_per_thread, ctas_per_sm)
 
     def timing_enable(self, enable=True):
         ibim_timing_enable(self.handle, enable)

@@ -54,60 +54,62 @@ def sphere_cloud(n, radius=10.0, jitter=0.0, seed=0, weight_range=(0.01, 0.06)):
     return xs[key], u[key], w[key]
 
 
-def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, vol_per_atom=20.0,
-                  radius_range=(1.2, 1.9), charge_range=(-0.8, 0.8), max_tries=200):
-    """Seeded self-avoiding random-walk chain confined to a ball (a compact
-    globule): step `step` A, non-bonded distances >= `min_dist` A, ball volume
-    n_atoms * vol_per_atom A^3.  Radii uniform in `radius_range`; partial
-    charges uniform in `charge_range` shifted to a net charge of zero.
-    Returns (centres (n,3), radii (n,), charges (n,))."""
+def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, beta=3.0, n_cand=16,
+                  radius_range=(1.2, 1.9), charge_range=(-0.8, 0.8)):
+    """Seeded self-avoiding random-walk chain compacted into a globule:
+    bond length `step` A, non-bonded distances >= `min_dist` A.  Each new bead
+    is drawn from `n_cand` random bond directions that keep the chain
+    self-avoiding, with probability proportional to exp(-beta * (distance to the
+    chain's centre of mass - the smallest such distance)), which packs the
+    chain towards its centre; a walk with no admissible candidate backs up 8
+    beads.  Radii uniform in `radius_range`; partial charges uniform in
+    `charge_range` shifted to a net charge of zero.
+    Returns (centres (n,3) about their mean, radii, charges)."""
     rng = np.random.default_rng(seed)
-    R_ball = (3.0 * n_atoms * vol_per_atom / (4.0 * np.pi)) ** (1.0 / 3.0)
     cell = min_dist
-    for _attempt in range(max_tries):
-        pos = np.zeros((n_atoms, 3))
-        grid = {}
+    pos = np.zeros((n_atoms, 3))
+    grid = {}
 
-        def key(p):
-            return tuple(np.floor(p / cell).astype(np.int64))
+    def key(p):
+        return (int(np.floor(p[0] / cell)), int(np.floor(p[1] / cell)), int(np.floor(p[2] / cell)))
 
-        def ok(p, upto):
-            k = key(p)
-            for dx in (-1, 0, 1):
-                for dy in (-1, 0, 1):
-                    for dz in (-1, 0, 1):
-                        for idx in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
-                            if idx == upto - 1:
-                                continue
-                            if np.sum((pos[idx] - p) ** 2) < min_dist * min_dist:
-                                return False
-            return True
+    def ok(p, i):
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for idx in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                        if idx == i - 1:
+                            continue
+                        d = pos[idx] - p
+                        if d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < min_dist * min_dist:
+                            return False
+        return True
 
-        pos[0] = 0.0
-        grid.setdefault(key(pos[0]), []).append(0)
-        good = True
-        for i in range(1, n_atoms):
-            placed = False
-            for _t in range(64):
-                d = rng.standard_normal(3)
-                d /= np.linalg.norm(d)
-                p = pos[i - 1] + step * d
-                if np.linalg.norm(p) > R_ball:
-                    continue
-                if ok(p, i):
-                    pos[i] = p
-                    grid.setdefault(key(p), []).append(i)
-                    placed = True
-                    break
-            if not placed:
-                good = False
-                break
-        if good:
-            radii = rng.uniform(radius_range[0], radius_range[1], size=n_atoms)
-            q = rng.uniform(charge_range[0], charge_range[1], size=n_atoms)
-            q -= q.mean()
-            return pos - pos.mean(axis=0), radii, q
-    raise RuntimeError("self-avoiding walk failed after %d restarts" % max_tries)
+    grid.setdefault(key(pos[0]), []).append(0)
+    csum = np.zeros(3)
+    i = 1
+    while i < n_atoms:
+        d = rng.standard_normal((n_cand, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        cand = pos[i - 1] + step * d
+        good = [j for j in range(n_cand) if ok(cand[j], i)]
+        if not good:
+            for _b in range(min(8, i - 1)):
+                i -= 1
+                grid[key(pos[i])].remove(i)
+            continue
+        cen = pos[:i].mean(axis=0)
+        dist = np.linalg.norm(cand[good] - cen, axis=1)
+        wgt = np.exp(-beta * (dist - dist.min()))
+        j = good[rng.choice(len(good), p=wgt / wgt.sum())]
+        pos[i] = cand[j]
+        grid.setdefault(key(cand[j]), []).append(i)
+        i += 1
+    radii = rng.uniform(radius_range[0], radius_range[1], size=n_atoms)
+    q = rng.uniform(charge_range[0], charge_range[1], size=n_atoms)
+    q -= q.mean()
+    return pos - pos.mean(axis=0), radii, q
 
 
 def batch_sizes(n_mol=64, lo=50, hi=3000, seed=SEED_BATCH):
