@@ -184,7 +184,8 @@ def run_ours(args):
     ctx.set_charges(z, q)
     N = ctx.N
     P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
-    tpt, bps, tune_ms = ctx.autotune(P)
+    variant, bps, tune_ms = ctx.autotune(P)
+    tpt, minb = ibim.ibim_f32_variants()[variant]
     opts = dict(precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=1000, start=0, certify=0)
     dp = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -300,7 +301,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
                                l2="256 MB buffer written between timed steps",
-                               f32_variant={"targets_per_thread": tpt, "ctas_per_sm": bps}),
+                               f32_variant={"index": variant, "targets_per_thread": tpt, "min_ctas_per_sm": minb,
+                                            "ctas_per_sm": bps}),
                 "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
                 "wall_s_timed": wall}
         line.update(extra)

@@ -129,6 +129,11 @@ ibim_status ibim_num_nodes(const ibim_ctx* ctx, int64_t* N);
 ibim_status ibim_get_nodes(const ibim_ctx* ctx, double* xstar, double* normal, double* w,
                            double* d, int32_t* ijk);
 
+/* Per-node Laplacian of the signed distance (twice the mean curvature of the
+ * level surface): 2/R on analytic spheres, second central differences of phi
+ * for ibim_build, 0 for caller-given nodes.  curv: host, N doubles. */
+ibim_status ibim_get_curvature(const ibim_ctx* ctx, double* curv);
+
 /* ----------------------------------------------------------- operator etc. */
 
 /*
@@ -207,22 +212,62 @@ ibim_status ibim_solve_host(ibim_ctx* ctx, const ibim_phys* phys, const ibim_sol
                             int64_t Nc, const double* z, const double* q, double* h_p,
                             ibim_solve_info* info);
 
+/* ---------------------------------------------------- learned warm start */
+
+/*
+ * A small per-node network that predicts the initial GMRES vector (not part
+ * of the paper's method, whose reference start is zero or Lambda^-1 g of
+ * Sec. 3.3).  Features of node i: with S1, S2 the weighted RMS of g1, g2 and
+ * L = S1/S2, (g1/S1, g2/S2, d/eps, clamp(H L,-10,10)/10, kappa L/(1+kappa L),
+ * ln(eps_E/eps_I)/5, (eps_I/eps_E)/(1+kappa L), 0), H from
+ * ibim_get_curvature.  Network 8 -> 64 -> 64 -> 2 (tanh), BF16 weights with
+ * FP32 arithmetic; output psi = S1 o0, psin = S2 o1.  Trained on solutions
+ * the method computed (ibim_wsnet_add_example) by Adam on sampled nodes with
+ * loss sum (w_i/mean w) |o - t|^2 / batch, t = (psi/S1, psin/S2).
+ * Parameters (IBIM_WS_NPARAMS floats, FP32 master copy): W1[64][8], b1[64],
+ * W2[64][64], b2[64], W3[2][64], b3[2].  Use: ibim_wsnet_predict into a
+ * device vector, then ibim_solve with start = 3.
+ */
+#define IBIM_WS_NPARAMS 4866
+typedef struct ibim_wsnet ibim_wsnet;
+ibim_status ibim_wsnet_create(uint64_t seed, void* stream, ibim_wsnet** out);
+ibim_status ibim_wsnet_get_params(const ibim_wsnet* net, float* h_params);
+ibim_status ibim_wsnet_set_params(ibim_wsnet* net, const float* h_params);  /* resets Adam */
+/* features (host N x 8 floats, may be NULL) and scales (host S1, S2, mean w; may be NULL) */
+ibim_status ibim_wsnet_features(ibim_wsnet* net, ibim_ctx* ctx, const ibim_phys* phys, float* h_feat,
+                                double* h_scales);
+/* appends every node of ctx with the solution d_p (device 2N) as training examples */
+ibim_status ibim_wsnet_add_example(ibim_wsnet* net, ibim_ctx* ctx, const ibim_phys* phys, const double* d_p);
+ibim_status ibim_wsnet_num_examples(const ibim_wsnet* net, int64_t* count);
+/* loss and gradient (host IBIM_WS_NPARAMS floats) over examples [first, first + count) */
+ibim_status ibim_wsnet_gradient(ibim_wsnet* net, int64_t first, int64_t count, double* loss, float* h_grad);
+ibim_status ibim_wsnet_train(ibim_wsnet* net, int steps, int batch_nodes, double lr, double* last_loss);
+ibim_status ibim_wsnet_predict(ibim_wsnet* net, ibim_ctx* ctx, const ibim_phys* phys, double* d_p0);
+void ibim_wsnet_destroy(ibim_wsnet* net);
+
 /* ---------------------------------------------------------------- tuning */
 
 /*
- * Autotuner of the FP32 pair-sum kernel (not part of the paper's method):
- * times every variant (2 or 4 targets per thread; the occupancy-limited
- * number of CTAs per SM or half of it) on this context's geometry with CUDA
- * events, keeps the fastest for this context and caches it for contexts built
- * later in the process with N in the same power-of-two bucket.  Outputs may be
- * NULL.  Synchronises; call it outside any stream capture.
+ * FP32 pair-kernel variants (a GPU tuning device, not part of the paper's
+ * method).  The library compiles a small table of variants, each with a fixed
+ * number of targets per thread and a register budget (minimum CTAs per SM);
+ * ibim_f32_variant_info describes entry v of [0, ibim_f32_variant_count()).
  */
-ibim_status ibim_autotune(ibim_ctx* ctx, const ibim_phys* phys, int* targets_per_thread, int* ctas_per_sm,
-                          double* best_ms);
+int ibim_f32_variant_count(void);
+ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm);
 
-/* Manual choice of the FP32 pair-kernel variant: targets_per_thread 2 or 4,
- * ctas_per_sm >= 1 (clamped to the occupancy limit) or 0 for the limit. */
-ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int targets_per_thread, int ctas_per_sm);
+/*
+ * Autotuner: times every variant on this context's geometry with CUDA events,
+ * keeps the fastest for this context and caches it for contexts built later
+ * in the process with N in the same power-of-two bucket.  Returns the chosen
+ * variant, its resident CTAs per SM and its time per application (outputs
+ * may be NULL).  Synchronises; call it outside any stream capture.
+ */
+ibim_status ibim_autotune(ibim_ctx* ctx, const ibim_phys* phys, int* variant, int* ctas_per_sm, double* best_ms);
+
+/* Manual choice of the FP32 variant and of the CTAs per SM of its persistent
+ * grid (0 = the occupancy limit; larger values are clamped to it). */
+ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int variant, int ctas_per_sm);
 
 /* ------------------------------------------------- allocation-free variant */
 
@@ -253,6 +298,23 @@ ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int targets_per_thread, int ctas
 #define IBIM_NOALLOC_MAX_NODES 131072
 ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, const double* d_normal, const double* d_w,
                                 const ibim_phys* phys, const double* d_in, double* d_out, void* stream);
+
+/*
+ * Batched solve of several molecules (contexts with their own geometry and
+ * charges, one device): every molecule runs its own restarted GMRES (FP64
+ * CGS2 Arnoldi, device Givens) and all molecules still iterating advance one
+ * Arnoldi step per round; the operator applications of a round run as ONE
+ * persistent FP32 pair-sum launch over a device-built list of the active
+ * molecules' (target tile, source tile) steps, and a round is one CUDA graph
+ * replay.  Molecules drop out of the list as they converge.
+ *   nmol in [1, 1024]; phys: nmol entries (kappa etc. per molecule); opts must
+ *   ask for IBIM_F32C, start 0, certify 0; d_p: nmol device pointers, 2 N_m
+ *   doubles each (solutions out); infos: nmol entries.
+ * The call synchronises the contexts' streams.  Returns IBIM_ERR_NOT_CONVERGED
+ * (infos filled) when any molecule stopped at maxit above tol.
+ */
+ibim_status ibim_solve_batch(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts* opts,
+                             double* const* d_p, ibim_solve_info* infos);
 
 /* ----------------------------------------------------------- diagnostics */
 

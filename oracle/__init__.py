@@ -7,3 +7,4 @@ compiled with gcc by ``oracle.build``).
 """
 from .oracle import *  # noqa: F401,F403
 from .closed_forms import *  # noqa: F401,F403
+from . import warmstart_ref  # noqa: F401,E402

@@ -296,7 +296,7 @@ int64_t orc_ls_cavity(const orc_grid *g, double *phi, double eps, uint8_t *label
  * gradients, unit normals, projections and cosine weights.  Returns the
  * count; arrays are written when cap >= count. */
 int64_t orc_ls_band(const orc_grid *g, const double *phi, double eps, int64_t cap, double *xs, double *nrm,
-                    double *w, double *dist, int32_t *ijk)
+                    double *w, double *dist, int32_t *ijk, double *curv)
 {
     const double h = g->h;
     int64_t n = 0;
@@ -322,6 +322,16 @@ int64_t orc_ls_band(const orc_grid *g, const double *phi, double eps, int64_t ca
                     }
                     w[n] = (1.0 + cos(M_PI * p / eps)) / (2.0 * eps) * h * h * h;
                     dist[n] = p;
+                    /* twice the mean curvature: Laplacian of phi by central differences */
+                    double lap = 0.0;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        int64_t lo_[3] = {i, j, k}, hi_[3] = {i, j, k};
+                        lo_[ax] = clampi(lo_[ax] - 1, g->n[ax]);
+                        hi_[ax] = clampi(hi_[ax] + 1, g->n[ax]);
+                        lap += (phi[idx(g, hi_[0], hi_[1], hi_[2])] - 2.0 * p + phi[idx(g, lo_[0], lo_[1], lo_[2])]) /
+                               (h * h);
+                    }
+                    curv[n] = lap;
                     ijk[3 * n] = (int32_t)gi;
                     ijk[3 * n + 1] = (int32_t)gj;
                     ijk[3 * n + 2] = (int32_t)gk;

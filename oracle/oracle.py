@@ -205,7 +205,8 @@ def sphere_nodes(R, centre=(0.0, 0.0, 0.0), h=0.25, eps=0.75, origin=(0.0, 0.0, 
     n2 = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), n, _d(xs), _d(nrm), _d(w),
                             _d(d), ijk.ctypes.data_as(_I32))
     assert n2 == n
-    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk}
+    # twice the mean curvature of the sphere at the projections: 2/R
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": np.full(n, 2.0 / R)}
 
 
 def gmres(xs, nrm, w, phys, g, x0=None, tol=1e-8, restart=100, maxit=500):
@@ -243,7 +244,7 @@ def _ls_lib():
         L.orc_ls_cavity.restype = ctypes.c_int64
         L.orc_ls_cavity.argtypes = [G, _D, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
         L.orc_ls_band.restype = ctypes.c_int64
-        L.orc_ls_band.argtypes = [G, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D, _I32]
+        L.orc_ls_band.argtypes = [G, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D, _I32, _D]
         L.orc_ls_ses.restype = ctypes.c_int64
         L.orc_ls_ses.argtypes = [G, ctypes.c_int64, _D, _D, ctypes.c_double, ctypes.c_double, _D]
         L._ls_ready = True
@@ -302,14 +303,16 @@ def ls_band(g, phi, eps):
     """Band nodes of a level-set grid (Sec. 3.2): dict of xs, nrm, w, d, ijk (grid order)."""
     phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
     L = _ls_lib()
-    n = L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), 0, None, None, None, None, None)
+    n = L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), 0, None, None, None, None, None, None)
     xs = np.empty((n, 3))
     nrm = np.empty((n, 3))
     w = np.empty(n)
     d = np.empty(n)
     ijk = np.empty((n, 3), dtype=np.int32)
-    L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), n, _d(xs), _d(nrm), _d(w), _d(d), ijk.ctypes.data_as(_I32))
-    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk}
+    curv = np.empty(n)
+    L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), n, _d(xs), _d(nrm), _d(w), _d(d), ijk.ctypes.data_as(_I32),
+                  _d(curv))
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": curv}
 
 
 def ses_nodes(z, r, probe=1.4, h=0.5, eps=1.0):

@@ -1,0 +1,479 @@
+// Batched IBIM solves: many molecules with uneven narrowband sizes advance
+// their GMRES iterations in lock-step, and every round's operator
+// applications for all still-active molecules run as ONE persistent launch.
+//
+// Round (captured once into a CUDA graph and replayed):
+//   batch_plan_kernel   active molecules (GMRES not done) and the prefix sums
+//                       of their (target tile x source tile) step counts;
+//                       steps per CTA for the persistent grid
+//   batch_pack_kernel   each active molecule's FP32 source payload from its
+//                       current Krylov vector, and y = Lambda p (diagonal)
+//   batch_pair_kernel   stream-K over the concatenated step space; each step
+//                       looks up its molecule, stages that molecule's source
+//                       tile with a bulk async copy and evaluates it with the
+//                       same arithmetic as the single-molecule kernel; tile
+//                       sums are added to the molecule's output in FP64
+//                       (atomic adds: the few CTAs sharing a target tile)
+//   per molecule        CGS2 orthogonalisation, normalisation and Givens
+//                       (the single-molecule kernels, skipped once done)
+// Molecules that converge drop out of the plan, so later rounds only spend
+// time on the molecules still iterating.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gmres_internal.cuh"
+#include "pair_f32_core.cuh"
+
+namespace ibim {
+
+constexpr int kMaxBatch = 1024;
+constexpr int kBTpt = 2;
+constexpr int kBTTile = kF32Threads * kBTpt;
+
+struct BatchMol {
+    const float4* pos;
+    const float4* nrm;
+    const float4* frames;
+    float4* src;
+    const double* w;
+    double* V;
+    double* x;
+    double* t;
+    GmState* st;
+    int64_t N, n_ttiles, n_stiles;
+    F32Consts k;
+    double lambda1, lambda2;
+    Geo64 g64;
+};
+
+struct BatchPlan {
+    int nactive;
+    int pad;
+    int64_t total;
+    int64_t per_cta;
+    int mol[kMaxBatch];
+    int64_t off[kMaxBatch + 1];
+};
+
+// mode 0: Arnoldi round (active = GMRES not done; in = V_k, out = V_{k+1});
+// mode 1: residual round (active = want[m]; in = x, out = t).
+__device__ __forceinline__ const double* batch_in(const BatchMol& M, int mode)
+{
+    return mode == 0 ? M.V + (int64_t)M.st->k * 2 * M.N : M.x;
+}
+__device__ __forceinline__ double* batch_out(const BatchMol& M, int mode)
+{
+    return mode == 0 ? M.V + (int64_t)(M.st->k + 1) * 2 * M.N : M.t;
+}
+
+__global__ void batch_plan_kernel(const BatchMol* __restrict__ mols, int nmol, int mode, const int* __restrict__ want,
+                                  int grid, BatchPlan* __restrict__ plan)
+{
+    if (threadIdx.x != 0) return;
+    int a = 0;
+    int64_t total = 0;
+    for (int m = 0; m < nmol; ++m) {
+        const bool active = (mode == 0) ? (mols[m].st->done == 0) : (want[m] != 0);
+        if (!active) continue;
+        plan->mol[a] = m;
+        plan->off[a] = total;
+        total += mols[m].n_ttiles * mols[m].n_stiles;
+        ++a;
+    }
+    plan->off[a] = total;
+    plan->nactive = a;
+    plan->total = total;
+    plan->per_cta = total > 0 ? (total + grid - 1) / grid : 1;
+}
+
+__global__ void batch_pack_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode)
+{
+    const int a = blockIdx.y;
+    if (a >= plan->nactive) return;
+    const BatchMol& M = mols[plan->mol[a]];
+    const double* p = batch_in(M, mode);
+    double* y = batch_out(M, mode);
+    const int64_t N = M.N;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const float4 q = M.pos[j];
+        const float4 n = M.nrm[j];
+        const double wj = M.w[j];
+        const double pj = p[j], pn = p[N + j];
+        M.src[2 * j] = make_float4(q.x, q.y, q.z, (float)(wj * pj));
+        M.src[2 * j + 1] = make_float4(n.x, n.y, n.z, (float)(wj * pn));
+        y[j] = M.lambda1 * pj;
+        y[N + j] = M.lambda2 * pn;
+    }
+}
+
+__global__ void __launch_bounds__(kF32Threads)
+    batch_pair_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode,
+                      unsigned* __restrict__ err)
+{
+    constexpr int TPT = kBTpt;
+    constexpr int CPT = kF32STile / kChunk;
+    __shared__ __align__(128) float4 sbuf[kF32Stages][2 * kF32STile];
+    __shared__ __align__(128) float4 sfrm[kF32Stages][2 * CPT];
+    __shared__ __align__(8) uint64_t bars[kF32Stages];
+    __shared__ int abort_flag;
+    __shared__ int s_nact;
+    __shared__ int s_mol[kMaxBatch];
+    __shared__ int64_t s_off[kMaxBatch + 1];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int64_t total = plan->total;
+    const int64_t per_cta = plan->per_cta;
+    const int64_t s0 = (int64_t)blockIdx.x * per_cta;
+    const int64_t s1 = (s0 + per_cta < total) ? s0 + per_cta : total;
+    if (s0 >= s1) return;
+    const int nact = plan->nactive;
+    for (int q = tid; q < nact; q += blockDim.x) s_mol[q] = plan->mol[q];
+    for (int q = tid; q <= nact; q += blockDim.x) s_off[q] = plan->off[q];
+    if (tid == 0) {
+        s_nact = nact;
+        for (int q = 0; q < kF32Stages; ++q) ptx::mbar_init(&bars[q], 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    // active index of step u: s_off[a] <= u < s_off[a + 1]
+    auto locate = [&](int64_t u) {
+        int lo = 0, hi = s_nact - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    auto issue = [&](int64_t u) {
+        const int a = locate(u);
+        const BatchMol& M = mols[s_mol[a]];
+        const int64_t st = (u - s_off[a]) % M.n_stiles;
+        const int64_t j0 = st * kF32STile;
+        const int64_t cnt = (M.N - j0 < kF32STile) ? M.N - j0 : kF32STile;
+        const int stage = (int)((u - s0) % kF32Stages);
+        const uint32_t bytes = (uint32_t)(cnt * 2 * sizeof(float4));
+        const int64_t nch = (cnt + kChunk - 1) / kChunk;
+        const uint32_t fbytes = (uint32_t)(nch * 2 * sizeof(float4));
+        ptx::mbar_arrive_expect_tx(&bars[stage], bytes + fbytes);
+        ptx::bulk_g2s(&sbuf[stage][0], M.src + 2 * j0, bytes, &bars[stage]);
+        ptx::bulk_g2s(&sfrm[stage][0], M.frames + 2 * (j0 / kChunk), fbytes, &bars[stage]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
+
+    int a = locate(s0);
+    const BatchMol* M = &mols[s_mol[a]];
+    int64_t v = s0 - s_off[a];
+    int64_t t = v / M->n_stiles;
+    int64_t st = v % M->n_stiles;
+    F32Consts k = M->k;
+    float3 xi[TPT], ni[TPT];
+    float4 bh[TPT];
+    float3 bl[TPT];
+    int64_t gi[TPT];
+    double D1[TPT], D2[TPT];
+
+    auto load_targets = [&]() {
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t blk0 = t * kBTTile + q * kF32Threads + warp * 32;
+            const int64_t i = blk0 + (tid & 31);
+            gi[q] = (i < M->N) ? i : 0;
+            if (i < M->N) {
+                const float4 p4 = M->pos[i];
+                const float4 n4 = M->nrm[i];
+                xi[q] = make_float3(p4.x, p4.y, p4.z);
+                ni[q] = make_float3(n4.x, n4.y, n4.z);
+            } else {
+                xi[q] = make_float3(1.0e6f, 1.0e6f, 1.0e6f);
+                ni[q] = make_float3(0.0f, 0.0f, 1.0f);
+            }
+            if (blk0 < M->N) {
+                bh[q] = M->frames[2 * (blk0 / kChunk)];
+                const float4 l = M->frames[2 * (blk0 / kChunk) + 1];
+                bl[q] = make_float3(l.x, l.y, l.z);
+            } else {
+                bh[q] = make_float4(0.0f, 0.0f, 0.0f, __builtin_huge_valf());
+                bl[q] = make_float3(0.0f, 0.0f, 0.0f);
+            }
+            D1[q] = 0.0;
+            D2[q] = 0.0;
+        }
+    };
+    auto flush = [&]() {
+        double* y = batch_out(*M, mode);
+        const int64_t N = M->N;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t i = t * kBTTile + q * kF32Threads + tid;
+            if (i < N) {
+                atomicAdd(y + i, kInv4Pi * D1[q]);
+                atomicAdd(y + N + i, kInv4Pi * D2[q]);
+            }
+        }
+    };
+    load_targets();
+
+    for (int64_t u = s0; u < s1; ++u) {
+        const int stage = (int)((u - s0) % kF32Stages);
+        const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
+        if (!ptx::mbar_wait_bounded(&bars[stage], parity, kWaitLimitNs)) {
+            abort_flag = 1;
+            atomicOr(err, kDevErrTimeout);
+        }
+        __syncthreads();
+        if (abort_flag) return;
+
+        const int64_t j0 = st * kF32STile;
+        const int cnt = (int)((M->N - j0 < kF32STile) ? M->N - j0 : kF32STile);
+        float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+        tile_sums<TPT>(xi, ni, bh, bl, true, &sbuf[stage][0], &sfrm[stage][0], cnt, k, S1, C1, S2, C2, M->g64, gi,
+                       j0);
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            D1[q] += (double)S1[q] - (double)C1[q];
+            D2[q] += (double)S2[q] - (double)C2[q];
+        }
+        __syncthreads();
+        if (tid == 0 && u + kF32Stages < s1) {
+            ptx::fence_proxy_async_smem();
+            issue(u + kF32Stages);
+        }
+        // advance to step u + 1
+        const bool tile_ends = (st + 1 == M->n_stiles);
+        if (tile_ends || u + 1 == s1) flush();
+        if (u + 1 == s1) break;
+        if (!tile_ends) {
+            ++st;
+        } else {
+            st = 0;
+            if (t + 1 < M->n_ttiles) {
+                ++t;
+            } else {
+                ++a;
+                M = &mols[s_mol[a]];
+                k = M->k;
+                t = 0;
+            }
+            load_targets();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+struct BatchRun {
+    int nmol = 0;
+    BatchMol* d_mols = nullptr;
+    BatchPlan* d_plan = nullptr;
+    int* d_want = nullptr;
+    cudaStream_t bs = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+    int pack_blocks = 0;
+    ~BatchRun()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaFree(d_mols);
+        cudaFree(d_plan);
+        cudaFree(d_want);
+        if (bs) cudaStreamDestroy(bs);
+    }
+};
+
+}  // namespace
+
+static ibim_status batch_operator(ibim_ctx* c0, BatchRun& R, int mode)
+{
+    batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, R.grid, R.d_plan);
+    batch_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
+    batch_pair_kernel<<<R.grid, kF32Threads, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+    count_launch(c0, 3);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts& o,
+                        double* const* d_p, ibim_solve_info* infos)
+{
+    const int m = std::min(o.restart, kMaxRestart);
+    BatchRun R;
+    R.nmol = nmol;
+    IBIM_CUDA(cudaStreamCreateWithFlags(&R.bs, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> user(nmol);
+    std::vector<BatchMol> h(nmol);
+    std::vector<double> gnorm(nmol, 0.0);
+    int64_t maxN = 0;
+    int sms = ctxs[0]->num_sms;
+    // order every molecule's queued work before the batch stream
+    cudaEvent_t ev;
+    IBIM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    for (int i = 0; i < nmol; ++i) {
+        IBIM_CUDA(cudaEventRecord(ev, ctxs[i]->stream));
+        IBIM_CUDA(cudaStreamWaitEvent(R.bs, ev, 0));
+    }
+    for (int i = 0; i < nmol; ++i) {
+        user[i] = ctxs[i]->stream;
+        ctxs[i]->stream = R.bs;
+    }
+    struct Restore {
+        int n;
+        ibim_ctx* const* c;
+        std::vector<cudaStream_t>* u;
+        cudaStream_t bs;
+        cudaEvent_t ev;
+        ~Restore()
+        {
+            cudaEventRecord(ev, bs);
+            for (int i = 0; i < n; ++i) {
+                c[i]->stream = (*u)[i];
+                cudaStreamWaitEvent(c[i]->stream, ev, 0);
+            }
+            cudaEventDestroy(ev);
+        }
+    } restore{nmol, ctxs, &user, R.bs, ev};
+    for (int i = 0; i < nmol; ++i) {
+        ibim_ctx* c = ctxs[i];
+        IBIM_TRY(gm_alloc(c, m));
+        IBIM_TRY(ensure_operator_workspaces(c));
+        IBIM_TRY(gm_init(c, phys[i], m, &gnorm[i]));
+        const PairConsts pk = make_consts(phys[i]);
+        BatchMol& b = h[i];
+        b.pos = c->d_pos32;
+        b.nrm = c->d_nrm32;
+        b.frames = c->d_frames;
+        b.src = (float4*)c->d_src;
+        b.w = c->d_geo64 + 6 * c->N;
+        b.V = c->gm->V;
+        b.x = c->gm->x;
+        b.t = c->gm->t;
+        b.st = c->gm->st;
+        b.N = c->N;
+        b.n_ttiles = (c->N + kBTTile - 1) / kBTTile;
+        b.n_stiles = (c->N + kF32STile - 1) / kF32STile;
+        b.k = f32_consts(pk);
+        b.lambda1 = pk.lambda1;
+        b.lambda2 = pk.lambda2;
+        b.g64 = Geo64{c->d_geo64, c->d_geo64 + 3 * c->N, 1, c->N};
+        maxN = std::max(maxN, c->N);
+    }
+    IBIM_CUDA(cudaMalloc((void**)&R.d_mols, sizeof(BatchMol) * nmol));
+    IBIM_CUDA(cudaMalloc((void**)&R.d_plan, sizeof(BatchPlan)));
+    IBIM_CUDA(cudaMalloc((void**)&R.d_want, sizeof(int) * nmol));
+    IBIM_CUDA(cudaMemcpyAsync(R.d_mols, h.data(), sizeof(BatchMol) * nmol, cudaMemcpyHostToDevice, R.bs));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_pair_kernel, kF32Threads, 0);
+    if (occ < 1) occ = 1;
+    R.grid = occ * sms;
+    R.pack_blocks = (int)std::min<int64_t>(256, (maxN + 255) / 256);
+
+    std::vector<int> iters(nmol, 0), cycles(nmol, 0), conv(nmol, 0), finished(nmol, 0);
+    std::vector<double> beta(nmol, 0.0);
+    std::vector<char> x_zero(nmol, 1);
+    std::vector<int> want(nmol, 0);
+    for (int i = 0; i < nmol; ++i)
+        if (gnorm[i] == 0.0) finished[i] = conv[i] = 1;
+
+    for (int cycle_guard = 0; cycle_guard < 1000; ++cycle_guard) {
+        // residuals of the molecules that have an iterate
+        int nres = 0;
+        for (int i = 0; i < nmol; ++i) {
+            want[i] = (!finished[i] && !x_zero[i]) ? 1 : 0;
+            nres += want[i];
+        }
+        if (nres > 0) {
+            for (int i = 0; i < nmol; ++i) infos[i].matvecs_f32 += want[i];
+            IBIM_CUDA(cudaMemcpyAsync(R.d_want, want.data(), sizeof(int) * nmol, cudaMemcpyHostToDevice, R.bs));
+            IBIM_TRY(batch_operator(ctxs[0], R, 1));
+        }
+        int nactive = 0;
+        for (int i = 0; i < nmol; ++i) {
+            if (finished[i]) continue;
+            const int kmax = std::max(0, std::min(m, o.maxit - iters[i]));
+            IBIM_TRY(gm_cycle_begin(ctxs[i], x_zero[i] != 0, o.tol * gnorm[i], kmax));
+            IBIM_TRY(gm_fetch_state(ctxs[i]));
+        }
+        IBIM_CUDA(cudaStreamSynchronize(R.bs));
+        for (int i = 0; i < nmol; ++i) {
+            if (finished[i]) continue;
+            x_zero[i] = 0;
+            beta[i] = ctxs[i]->gm->h_st->resid;
+            const int kmax = std::max(0, std::min(m, o.maxit - iters[i]));
+            if (beta[i] <= o.tol * gnorm[i]) {
+                finished[i] = conv[i] = 1;
+            } else if (kmax <= 0) {
+                finished[i] = 1;
+            } else {
+                ++nactive;
+            }
+        }
+        if (nactive == 0) break;
+        // one graph per solve: plan + pack + batched pairs + every molecule's orthogonalisation
+        if (R.exec == nullptr) {
+            cudaGraph_t graph = nullptr;
+            const int64_t before = ctxs[0]->timing.total_launches;
+            IBIM_CUDA(cudaStreamBeginCapture(R.bs, cudaStreamCaptureModeThreadLocal));
+            ibim_status s = batch_operator(ctxs[0], R, 0);
+            for (int i = 0; i < nmol && s == IBIM_OK; ++i) s = gm_ortho(ctxs[i]);
+            cudaError_t e = cudaStreamEndCapture(R.bs, &graph);
+            ctxs[0]->timing.total_launches = before;
+            for (int i = 1; i < nmol; ++i) ctxs[i]->timing.total_launches -= 9;
+            if (s != IBIM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "capture of the batched round", __FILE__, __LINE__);
+            e = cudaGraphInstantiate(&R.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate (batch)", __FILE__, __LINE__);
+        }
+        for (int round = 0; round <= kMaxRestart + 2; ++round) {
+            IBIM_CUDA(cudaGraphLaunch(R.exec, R.bs));
+            count_launch(ctxs[0], 3 + 9 * nmol);
+            if (round % 2 == 1 || round == kMaxRestart + 2) {
+                for (int i = 0; i < nmol; ++i) IBIM_TRY(gm_fetch_state(ctxs[i]));
+                IBIM_CUDA(cudaStreamSynchronize(R.bs));
+                bool all = true;
+                for (int i = 0; i < nmol; ++i) all = all && (ctxs[i]->gm->h_st->done != 0);
+                if (all) break;
+            }
+        }
+        for (int i = 0; i < nmol; ++i) IBIM_TRY(gm_fetch_state(ctxs[i]));
+        IBIM_CUDA(cudaStreamSynchronize(R.bs));
+        for (int i = 0; i < nmol; ++i) {
+            if (finished[i]) continue;
+            const int steps = ctxs[i]->gm->h_st->k;
+            iters[i] += steps;
+            cycles[i] += 1;
+            infos[i].matvecs_f32 += steps;
+            if (steps > 0) IBIM_TRY(gm_cycle_end(ctxs[i]));
+        }
+    }
+    for (int i = 0; i < nmol; ++i) {
+        ibim_ctx* c = ctxs[i];
+        infos[i].iters = iters[i];
+        infos[i].cycles = cycles[i];
+        infos[i].converged = conv[i];
+        infos[i].relres = gnorm[i] > 0.0 ? beta[i] / gnorm[i] : 0.0;
+        IBIM_CUDA(cudaMemcpyAsync(d_p[i], c->gm->x, sizeof(double) * 2 * c->N, cudaMemcpyDeviceToDevice, R.bs));
+        double gpol = 0.0, area = 0.0;
+        IBIM_TRY(energy_launch(c, phys[i], c->gm->x, nullptr, &gpol));
+        IBIM_TRY(area_launch(c, &area));
+        infos[i].gpol = gpol;
+        infos[i].gpol_kcal = gpol * kKcalPerE2A;
+        infos[i].area = area;
+    }
+    return IBIM_OK;
+}
+
+}  // namespace ibim

@@ -43,6 +43,7 @@ ibim_status ensure(ibim_ctx* c, void** buf, size_t* have, size_t need)
     }
     IBIM_CUDA(cudaMalloc(buf, need));
     *have = need;
+    ++c->ws_generation;
     return IBIM_OK;
 }
 
@@ -136,11 +137,33 @@ ibim_status timing_collect(ibim_ctx* c)
     return IBIM_OK;
 }
 
+// Source payload and partial-sum buffers large enough for both precisions
+// and every FP32 variant, so operator applications never reallocate them.
+ibim_status ensure_operator_workspaces(ibim_ctx* c)
+{
+    if (c->ws_sized) return IBIM_OK;
+    const int64_t N = c->N;
+    IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)N * 8 * sizeof(double)));
+    const PairSchedule s64 = make_schedule(N, kF64TTile, N, kF64STile, f64_grid_cap(c));
+    size_t need = (size_t)s64.grid * s64.max_segs * 2 * kF64TTile * sizeof(double);
+    const int keep = c->f32_variant;
+    for (int v = 0; v < f32_variant_count(); ++v) {
+        c->f32_variant = v;
+        const PairSchedule s = f32_schedule(c);
+        need = std::max(need, (size_t)s.grid * s.max_segs * 2 * f32_ttile(c) * sizeof(double));
+    }
+    c->f32_variant = keep;
+    IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, need));
+    c->ws_sized = true;
+    return IBIM_OK;
+}
+
 // --------------------------------------------------------------- operator
 ibim_status apply_operator(ibim_ctx* c, const PairConsts& k, int precision, VecRef in, OutRef out,
                            const int* d_skip)
 {
     const int64_t N = c->N;
+    IBIM_TRY(ensure_operator_workspaces(c));
     if (precision == IBIM_F32C) {
         const PairSchedule s = f32_schedule(c);
         IBIM_TRY(f32_pack(c, in, d_skip));
@@ -208,12 +231,11 @@ void ibim_destroy(ibim_ctx* c)
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
     cudaFree(c->d_geo64);
     cudaFree(c->d_dist);
+    cudaFree(c->d_curv);
     cudaFree(c->d_ijk);
     cudaFree(c->d_pos32);
     cudaFree(c->d_nrm32);
-    cudaFree(c->d_tb32_2);
-    cudaFree(c->d_tb32_4);
-    cudaFree(c->d_sb32);
+    cudaFree(c->d_frames);
     cudaFree(c->d_z);
     cudaFree(c->d_q);
     cudaFree(c->d_src);
@@ -240,6 +262,7 @@ ibim_status ibim_build_sphere(double R, const double* centre, const double* orig
     ibim_ctx* c = nullptr;
     IBIM_TRY(ctx_new(stream, &c));
     c->h = h;
+    c->band_eps = band_eps;
     for (int a = 0; a < 3; ++a) c->centroid[a] = centre[a];
     ibim_status s = build_sphere_nodes(c, R, centre, o, h, band_eps);
     if (s == IBIM_OK) s = finish_geometry(c);
@@ -271,6 +294,7 @@ ibim_status ibim_build(const double* xyz, const double* radii, const double* cha
     ibim_ctx* c = nullptr;
     IBIM_TRY(ctx_new(stream, &c));
     c->h = h;
+    c->band_eps = band_eps;
     for (int a = 0; a < 3; ++a) c->centroid[a] = cen[a] / (double)Na;
     ibim_status s = build_levelset(c, Na, xyz, radii, probe, h, band_eps);
     if (s == IBIM_OK) s = finish_geometry(c);
@@ -334,6 +358,8 @@ ibim_status ibim_build_from_nodes(int64_t N, const double* xstar, const double* 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_geo64, geo.data(), sizeof(double) * 7 * N, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_dist, 0, sizeof(double) * N, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_curv, 0, sizeof(double) * N, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_ijk, ijk.data(), sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -374,6 +400,15 @@ ibim_status ibim_set_charges(ibim_ctx* c, int64_t Nc, const double* z, const dou
     IBIM_CUDA(cudaMemcpyAsync(c->d_z, z, sizeof(double) * 3 * Nc, cudaMemcpyHostToDevice, c->stream));
     IBIM_CUDA(cudaMemcpyAsync(c->d_q, q, sizeof(double) * Nc, cudaMemcpyHostToDevice, c->stream));
     c->Nc = Nc;
+    return IBIM_OK;
+}
+
+ibim_status ibim_get_curvature(const ibim_ctx* cc, double* curv)
+{
+    if (cc == nullptr || curv == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
+    ibim_ctx* c = const_cast<ibim_ctx*>(cc);
+    IBIM_CUDA(cudaMemcpyAsync(curv, c->d_curv, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
     return IBIM_OK;
 }
 
@@ -470,6 +505,33 @@ ibim_status ibim_solve(ibim_ctx* c, const ibim_phys* phys, const ibim_solve_opts
     ibim_status s2 = check_device_error(c);
     if (s2 != IBIM_OK) return s2;
     if (s == IBIM_ERR_NOT_CONVERGED) return fail(IBIM_ERR_NOT_CONVERGED, "GMRES reached maxit above tol");
+    return IBIM_OK;
+}
+
+ibim_status ibim_solve_batch(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts* o,
+                             double* const* d_p, ibim_solve_info* infos)
+{
+    if (nmol < 1 || nmol > 1024 || ctxs == nullptr || phys == nullptr || o == nullptr || d_p == nullptr ||
+        infos == nullptr)
+        return fail(IBIM_ERR_ARG, "need 1 <= nmol <= 1024 and non-NULL arrays");
+    if (o->precision != IBIM_F32C || o->start != 0 || o->certify != 0)
+        return fail(IBIM_ERR_ARG, "the batched solve runs the FP32 operator from a zero start without certification");
+    if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
+        return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
+    for (int i = 0; i < nmol; ++i) {
+        if (ctxs[i] == nullptr || d_p[i] == nullptr) return fail(IBIM_ERR_ARG, "NULL context or output");
+        IBIM_TRY(check_phys(&phys[i]));
+        if (ctxs[i]->Nc <= 0) return fail(IBIM_ERR_STATE, "a context has no charges");
+        if (ctxs[i]->device != ctxs[0]->device) return fail(IBIM_ERR_ARG, "contexts on different devices");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(IBIM_ERR_ARG, "a context appears twice in the batch");
+        memset(&infos[i], 0, sizeof(infos[i]));
+    }
+    ibim_status s = batch_solve(nmol, ctxs, phys, *o, d_p, infos);
+    if (s != IBIM_OK) return s;
+    for (int i = 0; i < nmol; ++i) IBIM_TRY(check_device_error(ctxs[i]));
+    for (int i = 0; i < nmol; ++i)
+        if (!infos[i].converged) return fail(IBIM_ERR_NOT_CONVERGED, "a molecule reached maxit above tol");
     return IBIM_OK;
 }
 

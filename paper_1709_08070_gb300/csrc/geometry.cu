@@ -57,7 +57,13 @@ __device__ __forceinline__ bool sphere_node(const SphereBox& B, uint64_t code, d
 
 constexpr int kCompactBlock = 1024;
 
-__global__ void sphere_count_kernel(SphereBox B, uint64_t ncodes, int* __restrict__ counts)
+__global__ void fill_value_kernel(double* __restrict__ a, int64_t n, double v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) sphere_count_kernel(SphereBox B, uint64_t ncodes, int* __restrict__ counts)
 {
     const uint64_t code = (uint64_t)blockIdx.x * kCompactBlock + threadIdx.x;
     double x[3], n[3], d;
@@ -96,7 +102,7 @@ __global__ void scan_counts_kernel(int* __restrict__ counts, int64_t nblocks, in
     }
 }
 
-__global__ void sphere_write_kernel(SphereBox B, uint64_t ncodes, const int* __restrict__ offsets, int64_t N,
+__global__ void __launch_bounds__(kCompactBlock) sphere_write_kernel(SphereBox B, uint64_t ncodes, const int* __restrict__ offsets, int64_t N,
                                     double* __restrict__ geo, double* __restrict__ dist,
                                     int32_t* __restrict__ ijk_out)
 {
@@ -167,7 +173,10 @@ ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, cons
     e = cudaMalloc((void**)&c->d_geo64, sizeof(double) * 7 * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dist, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ijk, sizeof(int32_t) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
     if (e == cudaSuccess) {
+        fill_value_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->d_curv, N, 2.0 / R);
+        count_launch(c);
         sphere_write_kernel<<<(unsigned)nblocks, kCompactBlock, 0, c->stream>>>(B, ncodes, d_counts, N, c->d_geo64,
                                                                                 c->d_dist, c->d_ijk);
         count_launch(c);
@@ -201,7 +210,7 @@ ibim_status finish_geometry(ibim_ctx* c)
         c->d_geo64, N, c->centroid[0], c->centroid[1], c->centroid[2], c->d_pos32, c->d_nrm32);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
-    IBIM_TRY(f32_tile_bounds(c));
+    IBIM_TRY(f32_chunk_frames(c));  // overwrites d_pos32 with chunk-frame positions
     apply_cached_tuning(c);
     IBIM_CUDA(cudaStreamSynchronize(c->stream));
     return IBIM_OK;

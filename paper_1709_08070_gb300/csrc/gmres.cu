@@ -22,50 +22,9 @@
 
 #include <vector>
 
-#include "ibim_internal.cuh"
+#include "gmres_internal.cuh"
 
 namespace ibim {
-
-constexpr int kMaxRestart = 128;
-constexpr int kVecThreads = 256;
-
-struct GmState {
-    int k;       // current Arnoldi step within the cycle
-    int done;    // stop expanding (converged, cycle full or breakdown)
-    int conv;    // residual estimate below target
-    int kmax;    // steps allowed in this cycle
-    int m;       // restart length (row stride of H)
-    int pad;
-    double target;     // absolute residual target of the cycle
-    double resid;      // |e_{k}| after the last rotation
-    double hn;         // ||w|| of the current step
-    double coef[kMaxRestart + 1];  // Gram-Schmidt coefficients of the current pass
-    double hcol[kMaxRestart + 1];  // accumulated column k of H
-    double cs[kMaxRestart], sn[kMaxRestart];
-    double e[kMaxRestart + 1];
-    double y[kMaxRestart];
-    double H[(kMaxRestart + 1) * kMaxRestart];  // row-major, row stride m
-};
-
-struct GmresWork {
-    int m = 0;
-    int64_t len = 0;
-    double* V = nullptr;       // (m + 1) x len
-    double* x = nullptr;       // len: current iterate (solution accumulator)
-    double* r = nullptr;       // len: residual / scratch
-    double* t = nullptr;       // len: operator output scratch
-    double* g = nullptr;       // len: right-hand side
-    double* part = nullptr;    // per-block partial sums ((m + 1) x nblk)
-    int nblk = 0;
-    GmState* st = nullptr;     // device state
-    GmState* h_st = nullptr;   // pinned host mirror (small fields only are read)
-    cudaStream_t gs = nullptr; // capture-capable stream owned by the solver
-    cudaEvent_t ev = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int graph_prec = 0;
-    PairConsts graph_k;
-    bool graph_valid = false;
-};
 
 // ------------------------------------------------------------ vector kernels
 
@@ -309,7 +268,7 @@ void gmres_free(ibim_ctx* c)
     c->gm = nullptr;
 }
 
-static ibim_status gmres_alloc(ibim_ctx* c, int m)
+ibim_status gm_alloc(ibim_ctx* c, int m)
 {
     const int64_t len = 2 * c->N;
     if (c->gm && c->gm->m >= m && c->gm->len == len) return IBIM_OK;
@@ -333,15 +292,10 @@ static ibim_status gmres_alloc(ibim_ctx* c, int m)
     return IBIM_OK;
 }
 
-// One Arnoldi step (see the file comment), all launches on c->stream.
-static ibim_status arnoldi_step(ibim_ctx* c, const PairConsts& k, int precision)
+ibim_status gm_ortho(ibim_ctx* c)
 {
     GmresWork* w = c->gm;
     const int64_t len = w->len;
-    const int* skip = &w->st->done;
-    VecRef in{w->V, &w->st->k, len, 0};
-    OutRef out{w->V, &w->st->k, len, 1};
-    IBIM_TRY(apply_operator(c, k, precision, in, out, skip));
     for (int pass = 0; pass < 2; ++pass) {
         gs_dots_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st, w->part);
         gs_reduce_kernel<<<1, 128, 0, c->stream>>>(w->part, w->nblk, w->st, pass);
@@ -352,6 +306,64 @@ static ibim_status arnoldi_step(ibim_ctx* c, const PairConsts& k, int precision)
     givens_kernel<<<1, 1, 0, c->stream>>>(w->st);
     count_launch(c, 9);
     IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+// One Arnoldi step (see the file comment), all launches on c->stream.
+static ibim_status arnoldi_step(ibim_ctx* c, const PairConsts& k, int precision)
+{
+    GmresWork* w = c->gm;
+    const int64_t len = w->len;
+    const int* skip = &w->st->done;
+    VecRef in{w->V, &w->st->k, len, 0};
+    OutRef out{w->V, &w->st->k, len, 1};
+    IBIM_TRY(apply_operator(c, k, precision, in, out, skip));
+    return gm_ortho(c);
+}
+
+ibim_status gm_cycle_begin(ibim_ctx* c, bool x_zero, double target, int kmax)
+{
+    GmresWork* w = c->gm;
+    const int64_t len = w->len;
+    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->g, x_zero ? nullptr : w->t, w->r, len, w->part);
+    cycle_begin_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, target, kmax);
+    cycle_begin_scale_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->r, w->V, len, w->st);
+    count_launch(c, 3);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+ibim_status gm_cycle_end(ibim_ctx* c)
+{
+    GmresWork* w = c->gm;
+    trisolve_kernel<<<1, 1, 0, c->stream>>>(w->st);
+    xupdate_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->x, w->V, w->len, w->st);
+    count_launch(c, 2);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+ibim_status gm_fetch_state(ibim_ctx* c)
+{
+    IBIM_CUDA(cudaMemcpyAsync(c->gm->h_st, c->gm->st, 64, cudaMemcpyDeviceToHost, c->stream));
+    return IBIM_OK;
+}
+
+ibim_status gm_init(ibim_ctx* c, const ibim_phys& p, int m, double* gnorm)
+{
+    GmresWork* w = c->gm;
+    GmState init;
+    memset(&init, 0, sizeof(init));
+    init.m = m;
+    IBIM_CUDA(cudaMemcpyAsync(w->st, &init, sizeof(GmState), cudaMemcpyHostToDevice, c->stream));
+    IBIM_TRY(rhs_launch(c, p.eps_in, w->g));
+    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->g, nullptr, w->r, w->len, w->part);
+    cycle_begin_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, 0.0, 0);
+    count_launch(c, 2);
+    IBIM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * w->len, c->stream));
+    IBIM_CUDA(cudaMemcpyAsync(w->h_st, w->st, 64, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    *gnorm = w->h_st->resid;
     return IBIM_OK;
 }
 
@@ -377,23 +389,18 @@ static ibim_status begin_cycle(ibim_ctx* c, const PairConsts& k, int prec_out, b
 static ibim_status capture_step(ibim_ctx* c, const PairConsts& k, int precision)
 {
     GmresWork* w = c->gm;
-    if (w->graph_valid && w->graph_prec == precision && memcmp(&w->graph_k, &k, sizeof(k)) == 0) return IBIM_OK;
+    // Every workspace the step (or a later operator application of either
+    // precision) touches is sized for both precisions before capture, so that
+    // no later call reallocates a buffer the graph holds a pointer to.
+    IBIM_TRY(ensure_operator_workspaces(c));
+    if (w->graph_valid && w->graph_prec == precision && memcmp(&w->graph_k, &k, sizeof(k)) == 0 &&
+        w->graph_generation == c->ws_generation)
+        return IBIM_OK;
     if (w->exec) {
         cudaGraphExecDestroy(w->exec);
         w->exec = nullptr;
     }
     w->graph_valid = false;
-    // make sure every workspace the step touches exists before capture
-    if (precision == IBIM_F32C) {
-        IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 2 * sizeof(float4)));
-        const PairSchedule s = f32_schedule(c);
-        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes,
-                        (size_t)s.grid * s.max_segs * 2 * f32_ttile(c) * sizeof(double)));
-    } else {
-        IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)c->N * 8 * sizeof(double)));
-        const PairSchedule s = make_schedule(c->N, kF64TTile, c->N, kF64STile, f64_grid_cap(c));
-        IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, (size_t)s.grid * s.max_segs * 2 * kF64TTile * sizeof(double)));
-    }
     cudaGraph_t graph = nullptr;
     IBIM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const int64_t launches_before = c->timing.total_launches;
@@ -411,6 +418,7 @@ static ibim_status capture_step(ibim_ctx* c, const PairConsts& k, int precision)
     w->graph_valid = true;
     w->graph_prec = precision;
     w->graph_k = k;
+    w->graph_generation = c->ws_generation;
     return IBIM_OK;
 }
 
@@ -424,6 +432,10 @@ static ibim_status run_cycle(ibim_ctx* c, const PairConsts& k, int precision, bo
     for (;;) {
         for (int q = 0; q < per_poll; ++q) {
             if (use_graph) {
+                if (!w->graph_valid || w->graph_generation != c->ws_generation) {
+                    set_error("captured GMRES step is stale (workspace reallocated)");
+                    return IBIM_ERR_STATE;
+                }
                 IBIM_CUDA(cudaGraphLaunch(w->exec, c->stream));
                 count_launch(c, 12);  // kernels in one captured step
             } else {
@@ -448,7 +460,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
                         ibim_solve_info* info)
 {
     const int m = std::min(o.restart, kMaxRestart);
-    IBIM_TRY(gmres_alloc(c, m));
+    IBIM_TRY(gm_alloc(c, m));
     GmresWork* w = c->gm;
     const int64_t len = w->len, N = c->N;
     const PairConsts k = make_consts(p);

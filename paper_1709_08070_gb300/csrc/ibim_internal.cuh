@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/ibim.h"
@@ -92,26 +93,26 @@ struct ibim_ctx {
     cudaStream_t stream = nullptr;
     int64_t N = 0;
     double h = 0.0;
+    double band_eps = 0.0;  // band half-width eps (0 for caller-given nodes)
     double centroid[3] = {0, 0, 0};
     // FP64 geometry, SoA: x*, y*, z*, nx, ny, nz, w (7 arrays of N)
     double* d_geo64 = nullptr;
     double* d_dist = nullptr;     // signed distance per node (0 for caller nodes)
+    double* d_curv = nullptr;     // Laplacian of the distance (twice the mean curvature) per node
     int32_t* d_ijk = nullptr;     // grid coordinates (N x 3) or -1
-    // FP32 geometry: float4 (x* - centroid, w) and float4 (n, 0)
+    // FP32 geometry: float4 (x* relative to its 32-node chunk centre, w),
+    // float4 (n, 0), and per chunk two float4 (centre hi + radius, centre lo)
     float4* d_pos32 = nullptr;
     float4* d_nrm32 = nullptr;
-    // bounding spheres (centre, radius) of FP32 target tiles (for 2 and 4
-    // targets per thread) and of source tiles
-    float4* d_tb32_2 = nullptr;
-    float4* d_tb32_4 = nullptr;
-    float4* d_sb32 = nullptr;
+    float4* d_frames = nullptr;
     // level-set grid of contexts built from atoms (kept for inspection)
     double* d_phi = nullptr;
     int64_t ls_lo[3] = {0, 0, 0};
     int64_t ls_n[3] = {0, 0, 0};
     int64_t ls_cavity_nodes = 0;
-    // FP32 pair-kernel variant: targets per thread and CTAs per SM (0 = occupancy limit)
-    int f32_tpt = 2;
+    // FP32 pair-kernel variant (index into the compiled table) and CTAs per SM
+    // (0 = occupancy limit)
+    int f32_variant = 0;
     int f32_bps = 0;
     int tuned = 0;
     // charges
@@ -130,11 +131,16 @@ struct ibim_ctx {
     size_t io_bytes = 0;
     ibim::GmresWork* gm = nullptr;
     ibim::Timing timing;
+    // incremented whenever a workspace is reallocated: CUDA graphs captured
+    // with the old pointers must be re-captured
+    uint64_t ws_generation = 0;
+    bool ws_sized = false;  // operator workspaces already at their final size
 };
 
 namespace ibim {
 
 ibim_status ensure(ibim_ctx* c, void** buf, size_t* have, size_t need);
+ibim_status ensure_operator_workspaces(ibim_ctx* c);
 // Bracket one pair-sum launch with timing events (no-ops when timing is off).
 ibim_status timing_begin(ibim_ctx* c);
 ibim_status timing_end(ibim_ctx* c, int64_t interactions);
@@ -171,9 +177,11 @@ ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, V
                       const int* d_skip);
 int f32_grid_cap(ibim_ctx* c);
 int f32_ttile(const ibim_ctx* c);
-int f32_max_bps(int tpt);
+int f32_max_bps(int variant);
+int f32_variant_count();
+void f32_variant_info(int v, int* tpt, int* minb);
 PairSchedule f32_schedule(ibim_ctx* c);
-ibim_status f32_tile_bounds(ibim_ctx* c);
+ibim_status f32_chunk_frames(ibim_ctx* c);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,
                          OutRef out, const int* d_skip);
 // FP64 path pieces (pair_f64.cu)
@@ -202,5 +210,7 @@ void apply_cached_tuning(ibim_ctx* c);      // tune.cu
 ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& o, double* d_p,
                         ibim_solve_info* info);
 void gmres_free(ibim_ctx* c);
+ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts& o,
+                        double* const* d_p, ibim_solve_info* infos);
 
 }  // namespace ibim

@@ -242,7 +242,7 @@ __host__ __device__ __forceinline__ uint32_t ls_compact1by2(uint64_t v)
     return (uint32_t)v;
 }
 
-constexpr int kBandBlock = 1024;
+constexpr int kBandBlock = 256;  // band_write_kernel needs ~94 registers per thread
 
 __device__ __forceinline__ bool band_node(const LsGrid& g, const double* __restrict__ phi, double eps, uint64_t code,
                                           int64_t* idout)
@@ -254,7 +254,7 @@ __device__ __forceinline__ bool band_node(const LsGrid& g, const double* __restr
     return fabs(phi[id]) < eps;
 }
 
-__global__ void band_count_kernel(LsGrid g, const double* __restrict__ phi, double eps, uint64_t ncodes,
+__global__ void __launch_bounds__(kBandBlock) band_count_kernel(LsGrid g, const double* __restrict__ phi, double eps, uint64_t ncodes,
                                   int* __restrict__ counts)
 {
     const uint64_t code = (uint64_t)blockIdx.x * kBandBlock + threadIdx.x;
@@ -292,9 +292,9 @@ __global__ void band_scan_kernel(int* __restrict__ counts, int64_t nblocks, int6
     }
 }
 
-__global__ void band_write_kernel(LsGrid g, const double* __restrict__ phi, double eps, uint64_t ncodes,
+__global__ void __launch_bounds__(kBandBlock) band_write_kernel(LsGrid g, const double* __restrict__ phi, double eps, uint64_t ncodes,
                                   const int* __restrict__ offsets, int64_t N, double* __restrict__ geo,
-                                  double* __restrict__ dist, int32_t* __restrict__ ijk)
+                                  double* __restrict__ dist, int32_t* __restrict__ ijk, double* __restrict__ curv)
 {
     __shared__ int warp_tot[kBandBlock / 32];
     const uint64_t code = (uint64_t)blockIdx.x * kBandBlock + threadIdx.x;
@@ -326,6 +326,15 @@ __global__ void band_write_kernel(LsGrid g, const double* __restrict__ phi, doub
     }
     geo[6 * N + jn] = (1.0 + cos(kPi * p / eps)) / (2.0 * eps) * g.h * g.h * g.h;
     dist[jn] = p;
+    // Laplacian of phi by second central differences (twice the mean curvature)
+    double lap = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        int64_t im[3] = {i, j, k}, ip[3] = {i, j, k};
+        im[ax] = clamp_i(im[ax] - 1, g.n[ax]);
+        ip[ax] = clamp_i(ip[ax] + 1, g.n[ax]);
+        lap += (phi[ls_idx(g, ip[0], ip[1], ip[2])] - 2.0 * p + phi[ls_idx(g, im[0], im[1], im[2])]) / (g.h * g.h);
+    }
+    curv[jn] = lap;
 }
 
 // ------------------------------------------------------------------ driver
@@ -517,9 +526,11 @@ ibim_status build_levelset(ibim_ctx* c, int64_t Na, const double* z, const doubl
             e = cudaMalloc((void**)&c->d_geo64, sizeof(double) * 7 * N);
             if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dist, sizeof(double) * N);
             if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ijk, sizeof(int32_t) * 3 * N);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
             if (e == cudaSuccess) {
                 band_write_kernel<<<(unsigned)nblocks, kBandBlock, 0, c->stream>>>(g, d_phi, eps, ncodes, d_counts, N,
-                                                                                   c->d_geo64, c->d_dist, c->d_ijk);
+                                                                                   c->d_geo64, c->d_dist, c->d_ijk,
+                                                                                   c->d_curv);
                 count_launch(c);
                 e = cudaGetLastError();
             }

@@ -19,7 +19,7 @@ PairSchedule make_schedule(int64_t n_targets, int ttile, int64_t n_sources, int 
 int f32_occupancy_per_sm();
 cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
                                 const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
-                                cudaStream_t stream);
+                                cudaStream_t stream, const double* xs_aos, const double* nrm_aos);
 cudaError_t launch_fixup_raw(const double* part, const PairSchedule& s, int64_t N, const PairConsts& k,
                              const double* d_in, double* d_out, cudaStream_t stream);
 
@@ -151,7 +151,7 @@ extern "C" ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, con
     noalloc_pack_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(d_xstar, d_normal, d_w, d_in, N, cen, tpos,
                                                                      tnrm, src);
     IBIM_CUDA(cudaGetLastError());
-    IBIM_CUDA(launch_pair_f32_raw(tpos, tnrm, src, N, s, k, part, err, st));
+    IBIM_CUDA(launch_pair_f32_raw(tpos, tnrm, src, N, s, k, part, err, st, d_xstar, d_normal));
     IBIM_CUDA(launch_fixup_raw(part, s, N, k, d_in, d_out, st));
     unsigned h_err = 0;
     IBIM_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

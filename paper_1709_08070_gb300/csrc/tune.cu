@@ -12,7 +12,7 @@ namespace ibim {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<int, std::pair<int, int>> g_tune_cache;  // bucket -> (tpt, bps)
+std::map<int, std::pair<int, int>> g_tune_cache;  // bucket -> (variant, CTAs per SM)
 
 int size_bucket(int64_t N)
 {
@@ -33,7 +33,7 @@ void apply_cached_tuning(ibim_ctx* c)
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(size_bucket(c->N));
     if (it != g_tune_cache.end()) {
-        c->f32_tpt = it->second.first;
+        c->f32_variant = it->second.first;
         c->f32_bps = it->second.second;
         c->tuned = 1;
     }
@@ -43,7 +43,22 @@ void apply_cached_tuning(ibim_ctx* c)
 
 using namespace ibim;
 
-extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* tpt_out, int* bps_out,
+extern "C" int ibim_f32_variant_count(void) { return f32_variant_count(); }
+
+extern "C" ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm)
+{
+    if (v < 0 || v >= f32_variant_count()) {
+        set_error("variant index out of range");
+        return IBIM_ERR_ARG;
+    }
+    int t = 0, m = 0;
+    f32_variant_info(v, &t, &m);
+    if (targets_per_thread) *targets_per_thread = t;
+    if (min_ctas_per_sm) *min_ctas_per_sm = m;
+    return IBIM_OK;
+}
+
+extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* variant_out, int* ctas_per_sm_out,
                                      double* best_ms)
 {
     if (c == nullptr) {
@@ -60,14 +75,10 @@ extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* tp
     IBIM_CUDA(cudaGetLastError());
     const PairConsts k = make_consts(*phys);
 
-    std::vector<std::pair<int, int>> cand;
-    for (int tpt : {2, 4}) {
-        const int occ = f32_max_bps(tpt);
-        cand.push_back({tpt, occ});
-        if (occ > 1) cand.push_back({tpt, occ / 2 > 0 ? occ / 2 : 1});
-    }
-    // Each repetition costs about N^2 / 5e11 s; keep the whole search short.
-    const double est_ms = (double)N * (double)N / 5e8;
+    std::vector<std::pair<int, int>> cand;  // (variant, CTAs per SM; 0 = occupancy limit)
+    for (int v = 0; v < f32_variant_count(); ++v) cand.push_back({v, 0});
+    // Each repetition costs about N^2 / 6e11 s; keep the whole search short.
+    const double est_ms = (double)N * (double)N / 6e8;
     const int reps = est_ms > 200.0 ? 1 : 2;
     cudaEvent_t e0, e1;
     IBIM_CUDA(cudaEventCreate(&e0));
@@ -75,10 +86,10 @@ extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* tp
     const bool timing_was = c->timing.enabled;
     c->timing.enabled = false;
     double best = 1e300;
-    std::pair<int, int> pick{c->f32_tpt, c->f32_bps};
+    std::pair<int, int> pick{c->f32_variant, c->f32_bps};
     ibim_status st = IBIM_OK;
     for (const auto& v : cand) {
-        c->f32_tpt = v.first;
+        c->f32_variant = v.first;
         c->f32_bps = v.second;
         st = apply_operator(c, k, IBIM_F32C, VecRef{in, nullptr, 0, 0}, OutRef{out, nullptr, 0, 0}, nullptr);
         if (st != IBIM_OK) break;
@@ -98,7 +109,7 @@ extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* tp
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->timing.enabled = timing_was;
-    c->f32_tpt = pick.first;
+    c->f32_variant = pick.first;
     c->f32_bps = pick.second;
     if (st != IBIM_OK) return st;
     c->tuned = 1;
@@ -106,19 +117,19 @@ extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* tp
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[size_bucket(N)] = pick;
     }
-    if (tpt_out) *tpt_out = pick.first;
-    if (bps_out) *bps_out = pick.second;
+    if (variant_out) *variant_out = pick.first;
+    if (ctas_per_sm_out) *ctas_per_sm_out = f32_max_bps(pick.first);
     if (best_ms) *best_ms = best;
     return IBIM_OK;
 }
 
-extern "C" ibim_status ibim_set_f32_variant(ibim_ctx* c, int tpt, int bps)
+extern "C" ibim_status ibim_set_f32_variant(ibim_ctx* c, int variant, int ctas_per_sm)
 {
-    if (c == nullptr || (tpt != 2 && tpt != 4) || bps < 0) {
-        set_error("need a context, targets_per_thread 2 or 4 and ctas_per_sm >= 0");
+    if (c == nullptr || variant < 0 || variant >= f32_variant_count() || ctas_per_sm < 0) {
+        set_error("need a context, a variant index in [0, ibim_f32_variant_count()) and ctas_per_sm >= 0");
         return IBIM_ERR_ARG;
     }
-    c->f32_tpt = tpt;
-    c->f32_bps = bps;
+    c->f32_variant = variant;
+    c->f32_bps = ctas_per_sm;
     return IBIM_OK;
 }

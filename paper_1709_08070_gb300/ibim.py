@@ -16,15 +16,17 @@ from . import build as _build
 __all__ = [
     "IbimError", "Phys", "SolveOpts", "SolveInfo", "lib", "library_path",
     "ibim_build", "ibim_get_levelset", "ibim_build_sphere", "ibim_build_from_nodes", "ibim_set_charges", "ibim_num_nodes", "ibim_get_nodes",
-    "ibim_matvec", "ibim_matvec_host", "ibim_rhs", "ibim_energy", "ibim_area", "ibim_solve", "ibim_solve_host",
+    "ibim_matvec", "ibim_matvec_host", "ibim_rhs", "ibim_energy", "ibim_area", "ibim_solve", "ibim_solve_host", "ibim_solve_batch",
     "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
-    "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant",
-    "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A",
+    "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
+    "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
+    "ibim_get_curvature",
 ]
 
 IBIM_F64 = 64
 IBIM_F32C = 32
 IBIM_NOALLOC_MAX_NODES = 131072
+IBIM_WS_NPARAMS = 4866
 KCAL_PER_E2_A = 4.0 * np.pi * 332.0637
 
 _STATUS = {0: "IBIM_OK", 1: "IBIM_ERR_ARG", 2: "IBIM_ERR_EMPTY_BAND", 3: "IBIM_ERR_NONFINITE",
@@ -80,8 +82,21 @@ _SIGS = {
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
+    "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
     "ibim_get_levelset": [_V, _I64P, _I64P, _D],
+    "ibim_solve_batch": [ctypes.c_int, ctypes.POINTER(_V), ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts),
+                         ctypes.POINTER(_V), ctypes.POINTER(SolveInfo)],
+    "ibim_get_curvature": [_V, _D],
+    "ibim_wsnet_create": [ctypes.c_uint64, _V, _CTXP],
+    "ibim_wsnet_get_params": [_V, ctypes.POINTER(ctypes.c_float)],
+    "ibim_wsnet_set_params": [_V, ctypes.POINTER(ctypes.c_float)],
+    "ibim_wsnet_features": [_V, _V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_float), _D],
+    "ibim_wsnet_add_example": [_V, _V, ctypes.POINTER(Phys), _V],
+    "ibim_wsnet_num_examples": [_V, _I64P],
+    "ibim_wsnet_gradient": [_V, ctypes.c_int64, ctypes.c_int64, _D, ctypes.POINTER(ctypes.c_float)],
+    "ibim_wsnet_train": [_V, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D],
+    "ibim_wsnet_predict": [_V, _V, ctypes.POINTER(Phys), _V],
 }
 
 _lib = None
@@ -105,6 +120,10 @@ def lib():
             f.restype = ctypes.c_int
         L.ibim_last_error.restype = ctypes.c_char_p
         L.ibim_last_error.argtypes = []
+        L.ibim_f32_variant_count.restype = ctypes.c_int
+        L.ibim_f32_variant_count.argtypes = []
+        L.ibim_wsnet_destroy.restype = None
+        L.ibim_wsnet_destroy.argtypes = [_V]
         L.ibim_destroy.restype = None
         L.ibim_destroy.argtypes = [_V]
         _lib = L
@@ -261,6 +280,20 @@ def ibim_solve(ctx, phys, d_p, allow_not_converged=False, **opts):
     return info.as_dict()
 
 
+def ibim_solve_batch(ctxs, physs, d_ps, allow_not_converged=False, **opts):
+    """Batched FP32 solve of several contexts; returns a list of info dicts."""
+    n = len(ctxs)
+    arr_c = (_V * n)(*[c.handle if isinstance(c, Context) else c for c in ctxs])
+    arr_p = (Phys * n)(*[_phys(p) for p in physs])
+    arr_d = (_V * n)(*[_dptr(d) for d in d_ps])
+    infos = (SolveInfo * n)()
+    o = _opts(**opts)
+    st = lib().ibim_solve_batch(n, arr_c, arr_p, ctypes.byref(o), arr_d, infos)
+    if not (allow_not_converged and st == 5):
+        _check(st)
+    return [infos[i].as_dict() for i in range(n)]
+
+
 def ibim_solve_host(ctx, phys, z, q, h_p=None, allow_not_converged=False, **opts):
     p = _phys(phys)
     o = _opts(**opts)
@@ -301,8 +334,19 @@ def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=Non
                                      _dptr(d_in), _dptr(d_out), _stream(stream)))
 
 
+def ibim_f32_variants():
+    """[(targets_per_thread, min_ctas_per_sm)] of the compiled FP32 variants."""
+    out = []
+    for v in range(lib().ibim_f32_variant_count()):
+        t = ctypes.c_int(0)
+        m = ctypes.c_int(0)
+        _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m)))
+        out.append((t.value, m.value))
+    return out
+
+
 def ibim_autotune(ctx, phys):
-    """Pick the fastest FP32 pair-kernel variant; returns (targets_per_thread, ctas_per_sm, ms)."""
+    """Pick the fastest FP32 pair-kernel variant; returns (variant, ctas_per_sm, ms)."""
     p = _phys(phys)
     t = ctypes.c_int(0)
     b = ctypes.c_int(0)
@@ -311,8 +355,82 @@ def ibim_autotune(ctx, phys):
     return t.value, b.value, ms.value
 
 
-def ibim_set_f32_variant(ctx, targets_per_thread, ctas_per_sm=0):
-    _check(lib().ibim_set_f32_variant(ctx, int(targets_per_thread), int(ctas_per_sm)))
+def ibim_set_f32_variant(ctx, variant, ctas_per_sm=0):
+    _check(lib().ibim_set_f32_variant(ctx, int(variant), int(ctas_per_sm)))
+
+
+def ibim_get_curvature(ctx):
+    out = np.empty(ibim_num_nodes(ctx))
+    _check(lib().ibim_get_curvature(ctx, out.ctypes.data_as(_D)))
+    return out
+
+
+def _h(c):
+    return c.handle if isinstance(c, Context) else c
+
+
+class WarmStartNet:
+    """Owning wrapper of an ibim_wsnet (learned GMRES start, see include/ibim.h)."""
+
+    def __init__(self, seed=0, stream=None):
+        h = _V()
+        _check(lib().ibim_wsnet_create(int(seed), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def params(self):
+        out = np.empty(IBIM_WS_NPARAMS, dtype=np.float32)
+        _check(lib().ibim_wsnet_get_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == IBIM_WS_NPARAMS
+        _check(lib().ibim_wsnet_set_params(self.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def features(self, ctx, phys):
+        N = ibim_num_nodes(_h(ctx))
+        f = np.empty((N, 8), dtype=np.float32)
+        sc = np.empty(3)
+        p = _phys(phys)
+        _check(lib().ibim_wsnet_features(self.handle, _h(ctx), ctypes.byref(p),
+                                         f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), sc.ctypes.data_as(_D)))
+        return f, sc
+
+    def add_example(self, ctx, phys, d_p):
+        p = _phys(phys)
+        _check(lib().ibim_wsnet_add_example(self.handle, _h(ctx), ctypes.byref(p), _dptr(d_p)))
+
+    def num_examples(self):
+        n = ctypes.c_int64(0)
+        _check(lib().ibim_wsnet_num_examples(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def gradient(self, first, count):
+        g = np.empty(IBIM_WS_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(lib().ibim_wsnet_gradient(self.handle, int(first), int(count), ctypes.byref(loss),
+                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def train(self, steps, batch_nodes=8192, lr=1e-3):
+        loss = ctypes.c_double(0.0)
+        _check(lib().ibim_wsnet_train(self.handle, int(steps), int(batch_nodes), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, ctx, phys, d_p0):
+        p = _phys(phys)
+        _check(lib().ibim_wsnet_predict(self.handle, _h(ctx), ctypes.byref(p), _dptr(d_p0)))
+
+    def close(self):
+        if self.handle:
+            lib().ibim_wsnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ibim_destroy(ctx):
@@ -375,8 +493,8 @@ class Context:
     def autotune(self, phys):
         return ibim_autotune(self.handle, phys)
 
-    def set_f32_variant(self, targets_per_thread, ctas_per_sm=0):
-        ibim_set_f32_variant(self.handle, targets_per_thread, ctas_per_sm)
+    def set_f32_variant(self, variant, ctas_per_sm=0):
+        ibim_set_f32_variant(self.handle, variant, ctas_per_sm)
 
     def timing_enable(self, enable=True):
         ibim_timing_enable(self.handle, enable)

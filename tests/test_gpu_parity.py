@@ -244,3 +244,26 @@ def test_solve_reports_not_converged():
     info = ctx.solve(P, dp, precision=F64, tol=1e-14, restart=2, maxit=2, allow_not_converged=True)
     assert info["iters"] == 2 and not info["converged"]
     ctx.close()
+
+
+def test_kirkwood_fp32_all_rows_against_fp64():
+    """All 2N rows of the FP32 operator against the FP64 operator (itself
+    checked against the oracle above) on the 80k-node sphere, whose lattice
+    symmetry puts many pairs within rounding of the tube boundary: the FP32
+    path must decide those ties as FP64 does (no row may stand out)."""
+    ctx = ibim.Context.sphere(KIRK["R"], h=KIRK["h"], band_eps=KIRK["k"] * KIRK["h"])
+    N = ctx.N
+    for kappa in (0.1257, 0.0):
+        P, _ = _phys(2.0, 80.0, kappa, KIRK["h"])
+        p = _dev(inputs.random_vector(2 * N, seed=1))
+        y64 = torch.empty_like(p)
+        y32 = torch.empty_like(p)
+        ctx.matvec(P, p, y64, precision=F64)
+        ctx.matvec(P, p, y32, precision=F32)
+        a, b = y64.cpu().numpy(), y32.cpu().numpy()
+        r = _both_blocks(b, a, N)
+        worst = np.max(np.abs(b - a)) / np.max(np.abs(a))
+        print("kirkwood all rows kappa=%g: rel %.2e %.2e %.2e, worst row %.2e" % (kappa, *r, worst))
+        assert max(r) < 1e-6, r
+        assert worst < 1e-5, worst
+    ctx.close()

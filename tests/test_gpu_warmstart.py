@@ -1,0 +1,113 @@
+"""Learned warm start: GPU features and gradients against the FP64 reference,
+and what the trained network gains over the zero start on held-out molecules."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import warmstart_ref as ws
+from paper_1709_08070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1709_08070_gb300 import ibim  # noqa: E402
+
+
+def _perm(gpu_ijk, orc_ijk):
+    key = {tuple(v): i for i, v in enumerate(orc_ijk)}
+    return np.array([key[tuple(v)] for v in gpu_ijk])
+
+
+def _setup(seed=5):
+    R, h = 3.0, 0.25
+    ctx = ibim.Context.sphere(R, h=h, band_eps=2 * h)
+    z, q = inputs.kirkwood_charges(n=4, ball_radius=2.0, seed=seed)
+    ctx.set_charges(z, q)
+    g = oracle.sphere_nodes(R, h=h, eps=2 * h)
+    perm = _perm(ctx.nodes()["ijk"], g["ijk"])
+    return ctx, g, z, q, perm, R, h
+
+
+def test_features_match_reference():
+    ctx, g, z, q, perm, R, h = _setup()
+    for kappa in (0.0, 0.1257):
+        P = ibim.Phys(2.0, 80.0, kappa, h, 0)
+        net = ibim.WarmStartNet(seed=1)
+        f, sc = net.features(ctx, P)
+        go = oracle.rhs(g["xs"], g["nrm"], z, q, 2.0)
+        Fo, (S1, S2, mw) = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, kappa)
+        assert sc[0] == pytest.approx(S1, rel=1e-10) and sc[1] == pytest.approx(S2, rel=1e-10)
+        np.testing.assert_allclose(f, Fo[perm], rtol=2e-6, atol=2e-6)
+        net.close()
+    ctx.close()
+
+
+def test_gradient_matches_reference():
+    ctx, g, z, q, perm, R, h = _setup()
+    P = ibim.Phys(2.0, 80.0, 0.1257, h, 0)
+    N = ctx.N
+    params = (0.3 * inputs.random_vector(ws.NPARAMS, seed=12)).astype(np.float32)
+    p_orc = inputs.random_vector(2 * N, seed=13, scale=1e-2)
+    p_gpu = np.concatenate([p_orc[:N][perm], p_orc[N:][perm]])
+    net = ibim.WarmStartNet(seed=2)
+    net.set_params(params)
+    net.add_example(ctx, P, torch.from_numpy(p_gpu).cuda())
+    assert net.num_examples() == N
+    loss_g, grad_g = net.gradient(0, N)
+    go = oracle.rhs(g["xs"], g["nrm"], z, q, 2.0)
+    Fo, sc = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, 0.1257)
+    To, wto = ws.targets(p_orc, g["w"], sc)
+    loss_o, grad_o = ws.loss_and_grad(ws.bf16_round(params), Fo, To, wto)
+    assert loss_g == pytest.approx(loss_o, rel=1e-4)
+    err = np.linalg.norm(grad_g - grad_o) / np.linalg.norm(grad_o)
+    print("warm-start gradient: loss %.6e vs %.6e, grad rel err %.2e" % (loss_g, loss_o, err))
+    assert err < 1e-3
+    net.close()
+    ctx.close()
+
+
+def _molecule(kind, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "sphere":
+        R = float(rng.uniform(3.0, 6.0))
+        ctx = ibim.Context.sphere(R, h=0.5, band_eps=1.0)
+        z, q = inputs.kirkwood_charges(n=int(rng.integers(2, 8)), ball_radius=0.7 * R, seed=seed)
+        ctx.set_charges(z, q)
+    else:
+        z, r, q = inputs.globule_atoms(int(rng.integers(20, 60)), seed=seed)
+        ctx = ibim.Context.molecule(z, r, q, probe=1.4, h=0.5)
+    P = ibim.Phys(float(rng.choice([1.0, 2.0, 4.0])), 80.0, float(rng.uniform(0.0, 0.2)), 0.5, 0)
+    return ctx, P
+
+
+def test_trained_start_saves_gmres_iterations():
+    net = ibim.WarmStartNet(seed=7)
+    train = [_molecule("sphere" if s % 2 else "globule", 1000 + s) for s in range(12)]
+    for ctx, P in train:
+        d = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
+        info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=400)
+        assert info["converged"]
+        net.add_example(ctx, P, d)
+        ctx.close()
+    loss0 = net.train(1, batch_nodes=4096, lr=1e-3)
+    loss = net.train(1500, batch_nodes=4096, lr=2e-3)
+    print("warm-start training loss %.3e -> %.3e" % (loss0, loss))
+    assert loss < 0.5 * loss0
+    saved = []
+    for s in range(4):
+        ctx, P = _molecule("sphere" if s % 2 else "globule", 5000 + s)
+        d0 = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
+        i0 = ctx.solve(P, d0, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=400, start=0)
+        d1 = torch.empty_like(d0)
+        net.predict(ctx, P, d1)
+        i1 = ctx.solve(P, d1, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=400, start=3)
+        assert i0["converged"] and i1["converged"]
+        assert abs(i1["gpol"] - i0["gpol"]) <= 1e-4 * abs(i0["gpol"])
+        saved.append(i0["iters"] - i1["iters"])
+        print("held-out N=%d iters zero %d learned %d" % (ctx.N, i0["iters"], i1["iters"]))
+        ctx.close()
+    assert sum(saved) > 0 and min(saved) >= 0, saved
+    net.close()
