@@ -33,13 +33,14 @@ if ROOT not in sys.path:
 
 WORKLOAD = {"workload": "kirkwood_sphere", "R": 20.0, "h": 0.5, "band_k": 2, "tau_k": 1.0, "n_charges": 50,
             "charge_ball": 16.0, "eps_in": 2.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64}
-# FP32-pipe (FFMA/FMUL/FADD) instructions per interaction of the pair kernel's
-# far-field formula, counted from its source: pair geometry (r, |r|^2, s_x, s_y,
-# c) 15, rho and the two exponential arguments 3, kernel scalars (E x, 1-E, g,
-# 3-B, 1/rho^2, 1/rho^3, the two theta terms) 9, the four kernel products fused
-# into the two running sums 13.  The chunked compensation adds 0.5 per pair;
-# the two MUFU operations (rsqrt, ex2) run on the XU pipe and are not counted.
-F32_OPS_PER_INTERACTION = 40
+# FP32-pipe operations (FMA/MUL/ADD lanes) per interaction of the pair
+# kernel's far-field formula, counted from its source (pair_far2, two sources
+# per packed instruction): r 3, |r|^2 3, s_x 3, r.(a m) 3, n.(a m) 3, rho and
+# the two exponent arguments 3, E x, E - 1, g, 3 - B 5, rho^-3 1, the two
+# theta terms 2, the four kernel products fused into the two sums 10.  The
+# three MUFU operations (rsqrt, rcp, ex2) run on the XU pipe and are not
+# counted; the per-chunk frame offsets and compensation add about 0.5.
+F32_OPS_PER_INTERACTION = 36
 FP32_LANES_PER_SM = 128
 METRIC = "IBIM matvec interactions/s"
 
@@ -312,6 +313,39 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """Operator applications only (the workload's tuned FP32 pair kernel), for
+    profiler captures: warm-up + steps matvecs, one short JSON line."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    W = WORKLOAD
+    h = W["h"]
+    ctx = ibim.Context.sphere(W["R"], h=h, band_eps=W["band_k"] * h)
+    N = ctx.N
+    P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
+    if args.variant is not None:
+        ctx.set_f32_variant(args.variant, args.ctas_per_sm)
+        variant, bps = args.variant, args.ctas_per_sm
+    else:
+        variant, bps, _ = ctx.autotune(P)
+    x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.matvec(P, x, y, precision=ibim.IBIM_F32C)
+    torch.cuda.synchronize()
+    ctx.timing_enable(True)
+    ctx.timing_reset()
+    for _ in range(args.steps):
+        ctx.matvec(P, x, y, precision=ibim.IBIM_F32C)
+    torch.cuda.synchronize()
+    tim = ctx.timing()
+    ctx.close()
+    print(json.dumps({"mode": "profile", "N": N, "variant": variant, "ctas_per_sm": bps,
+                      "pair_ms": tim["pair_ms"] / max(1, tim["pair_launches"])}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,6 +355,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="operator applications only (for profiler captures); prints no bench line")
+    ap.add_argument("--variant", type=int, default=None, help="with --profile: FP32 kernel variant (no autotune)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -328,6 +366,8 @@ def main():
     __graft_entry__.build()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     else:
         run_ours(args)
 

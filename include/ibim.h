@@ -83,7 +83,8 @@ typedef struct {
  * (ceil((k1+4)/k0) steps, dt = k0 h, k0 = 1/2, k1 = band_eps/h), band
  * {|phi| < band_eps} with WENO5 normals, projections x* = x - phi n and
  * weights delta_eps(phi) h^3.  Grid: nodes h * (integer coordinates) covering
- * the atoms' extent plus probe + band_eps + 8h.  Nodes are in Morton order.
+ * the atoms' extent plus probe + band_eps + 8h.  Node order: compact aligned
+ * blocks of 32 nodes by recursive coordinate bisection of x* (ties by index).
  *   xyz: Na x 3 host centres (A); radii: Na host (> 0); charges: Na host or
  *   NULL (when given they become the context's charges at the centres);
  *   probe >= 0 (rho0), h > 0, band_eps > 0 (eps).
@@ -101,8 +102,9 @@ ibim_status ibim_get_levelset(const ibim_ctx* ctx, int64_t* lo, int64_t* n, doub
  * Narrowband of an analytic sphere (signed distance d(x) = |x - c| - R),
  * Sec. 2.2 and Sec. 3.2 with J = 1.  Grid U_h = origin + h Z^3; nodes with
  * |d| < band_eps are kept, x* = c + R (x - c)/|x - c|, n = (x - c)/|x - c|,
- * w = delta_eps(d) h^3 (cosine weight).  Nodes are stored in Morton order of
- * their grid coordinates (use ibim_get_nodes for the coordinates).
+ * w = delta_eps(d) h^3 (cosine weight).  Node order: compact aligned blocks of
+ * 32 nodes by recursive coordinate bisection of x* (use ibim_get_nodes for the
+ * grid coordinates of each node).
  *   R > 0, h > 0, band_eps > 0; centre/origin: host double[3] (origin may be NULL = 0).
  * Errors: IBIM_ERR_ARG, IBIM_ERR_EMPTY_BAND, IBIM_ERR_CUDA.
  */
@@ -112,7 +114,10 @@ ibim_status ibim_build_sphere(double R, const double* centre, const double* orig
 /*
  * Context from caller-given nodes (host arrays, copied): x* (N x 3, row-major),
  * unit normals (N x 3), weights w (N).  h is informational (> 0).  Nodes keep
- * the caller's order.  Errors: IBIM_ERR_ARG (N <= 0, NULL), IBIM_ERR_NONFINITE.
+ * the caller's order; the FP32 operator is fastest when every aligned block of
+ * 32 consecutive nodes is spatially compact (its far-field path is taken per
+ * pair of blocks whose bounding spheres are apart).
+ * Errors: IBIM_ERR_ARG (N <= 0, NULL), IBIM_ERR_NONFINITE.
  */
 ibim_status ibim_build_from_nodes(int64_t N, const double* xstar, const double* normal,
                                   const double* w, double h, void* stream, ibim_ctx** out);

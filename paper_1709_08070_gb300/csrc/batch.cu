@@ -43,6 +43,7 @@ struct BatchMol {
     double* t;
     GmState* st;
     int64_t N, n_ttiles, n_stiles;
+    int64_t sperm;  // source-tile visiting stride (see make_schedule)
     F32Consts k;
     double lambda1, lambda2;
     Geo64 g64;
@@ -96,15 +97,30 @@ __global__ void batch_pack_kernel(const BatchMol* __restrict__ mols, const Batch
     const double* p = batch_in(M, mode);
     double* y = batch_out(M, mode);
     const int64_t N = M.N;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const float4 q = M.pos[j];
-        const float4 n = M.nrm[j];
-        const double wj = M.w[j];
-        const double pj = p[j], pn = p[N + j];
-        M.src[2 * j] = make_float4(q.x, q.y, q.z, (float)(wj * pj));
-        M.src[2 * j + 1] = make_float4(n.x, n.y, n.z, (float)(wj * pn));
-        y[j] = M.lambda1 * pj;
-        y[N + j] = M.lambda2 * pn;
+    const int64_t n_pairs = padded_nodes(N) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pr < n_pairs;
+         pr += (int64_t)gridDim.x * blockDim.x) {
+        float4 q[2], n[2];
+        float av[2], bv[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t j = 2 * pr + e;
+            if (j < N) {
+                q[e] = M.pos[j];
+                n[e] = M.nrm[j];
+                const double wj = M.w[j];
+                const double pj = p[j], pn = p[N + j];
+                av[e] = (float)(wj * pj);
+                bv[e] = (float)(wj * pn);
+                y[j] = M.lambda1 * pj;
+                y[N + j] = M.lambda2 * pn;
+            } else {
+                q[e] = pad_source_pos();
+                n[e] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+                av[e] = bv[e] = 0.0f;
+            }
+        }
+        write_source_pair(M.src + kPairF4 * pr, q[0], q[1], n[0], n[1], av[0], av[1], bv[0], bv[1]);
     }
 }
 
@@ -113,17 +129,17 @@ __global__ void __launch_bounds__(kF32Threads)
                       unsigned* __restrict__ err)
 {
     constexpr int TPT = kBTpt;
-    constexpr int CPT = kF32STile / kChunk;
-    __shared__ __align__(128) float4 sbuf[kF32Stages][2 * kF32STile];
-    __shared__ __align__(128) float4 sfrm[kF32Stages][2 * CPT];
-    __shared__ __align__(8) uint64_t bars[kF32Stages];
-    __shared__ int abort_flag;
+    constexpr int NW = kF32Threads / 32;
+    __shared__ __align__(128) SourceStage stg[kF32Stages];
+    __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
+    __shared__ __align__(8) StagePipe pipe;
     __shared__ int s_nact;
     __shared__ int s_mol[kMaxBatch];
     __shared__ int64_t s_off[kMaxBatch + 1];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
+    const int lane = tid & 31;
     const int64_t total = plan->total;
     const int64_t per_cta = plan->per_cta;
     const int64_t s0 = (int64_t)blockIdx.x * per_cta;
@@ -134,9 +150,7 @@ __global__ void __launch_bounds__(kF32Threads)
     for (int q = tid; q <= nact; q += blockDim.x) s_off[q] = plan->off[q];
     if (tid == 0) {
         s_nact = nact;
-        for (int q = 0; q < kF32Stages; ++q) ptx::mbar_init(&bars[q], 1);
-        ptx::fence_mbar_init();
-        abort_flag = 0;
+        pipe_init(pipe, NW);
     }
     __syncthreads();
 
@@ -153,16 +167,10 @@ __global__ void __launch_bounds__(kF32Threads)
     auto issue = [&](int64_t u) {
         const int a = locate(u);
         const BatchMol& M = mols[s_mol[a]];
-        const int64_t st = (u - s_off[a]) % M.n_stiles;
-        const int64_t j0 = st * kF32STile;
-        const int64_t cnt = (M.N - j0 < kF32STile) ? M.N - j0 : kF32STile;
+        const int64_t st = (((u - s_off[a]) % M.n_stiles) * M.sperm) % M.n_stiles;
         const int stage = (int)((u - s0) % kF32Stages);
-        const uint32_t bytes = (uint32_t)(cnt * 2 * sizeof(float4));
-        const int64_t nch = (cnt + kChunk - 1) / kChunk;
-        const uint32_t fbytes = (uint32_t)(nch * 2 * sizeof(float4));
-        ptx::mbar_arrive_expect_tx(&bars[stage], bytes + fbytes);
-        ptx::bulk_g2s(&sbuf[stage][0], M.src + 2 * j0, bytes, &bars[stage]);
-        ptx::bulk_g2s(&sfrm[stage][0], M.frames + 2 * (j0 / kChunk), fbytes, &bars[stage]);
+        pipe_issue(pipe, stg[stage], stage, M.src + st * (kF32STile / 2) * kPairF4,
+                   M.frames + st * 2 * kChunksPerTile);
     };
     if (tid == 0)
         for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
@@ -173,45 +181,39 @@ __global__ void __launch_bounds__(kF32Threads)
     int64_t t = v / M->n_stiles;
     int64_t st = v % M->n_stiles;
     F32Consts k = M->k;
-    float3 xi[TPT], ni[TPT];
-    float4 bh[TPT];
-    float3 bl[TPT];
-    int64_t gi[TPT];
+    Targets<TPT> T;
+    int64_t gi0 = 0;
+    bool idle = false;
     double D1[TPT], D2[TPT];
 
     auto load_targets = [&]() {
+        gi0 = t * kBTTile + tid;
+        idle = t * kBTTile + warp * 32 >= M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t blk0 = t * kBTTile + q * kF32Threads + warp * 32;
-            const int64_t i = blk0 + (tid & 31);
-            gi[q] = (i < M->N) ? i : 0;
-            if (i < M->N) {
-                const float4 p4 = M->pos[i];
-                const float4 n4 = M->nrm[i];
-                xi[q] = make_float3(p4.x, p4.y, p4.z);
-                ni[q] = make_float3(n4.x, n4.y, n4.z);
-            } else {
-                xi[q] = make_float3(1.0e6f, 1.0e6f, 1.0e6f);
-                ni[q] = make_float3(0.0f, 0.0f, 1.0f);
-            }
-            if (blk0 < M->N) {
-                bh[q] = M->frames[2 * (blk0 / kChunk)];
-                const float4 l = M->frames[2 * (blk0 / kChunk) + 1];
-                bl[q] = make_float3(l.x, l.y, l.z);
-            } else {
-                bh[q] = make_float4(0.0f, 0.0f, 0.0f, __builtin_huge_valf());
-                bl[q] = make_float3(0.0f, 0.0f, 0.0f);
-            }
+            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const float4 p4 = M->pos[i];
+            const float4 n4 = M->nrm[i];
+            T.x[q] = make_float3(p4.x, p4.y, p4.z);
+            T.nx[q] = f2(n4.x);
+            T.ny[q] = f2(n4.y);
+            T.nz[q] = f2(n4.z);
             D1[q] = 0.0;
             D2[q] = 0.0;
         }
+        __syncwarp();
+        if (lane < 2 * TPT) {
+            const int64_t blk0 = t * kBTTile + (int64_t)(lane >> 1) * kF32Threads + warp * 32;
+            tfrm[warp][lane] = M->frames[2 * (blk0 / kChunk) + (lane & 1)];
+        }
+        __syncwarp();
     };
     auto flush = [&]() {
         double* y = batch_out(*M, mode);
         const int64_t N = M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = t * kBTTile + q * kF32Threads + tid;
+            const int64_t i = gi0 + (int64_t)q * kF32Threads;
             if (i < N) {
                 atomicAdd(y + i, kInv4Pi * D1[q]);
                 atomicAdd(y + N + i, kInv4Pi * D2[q]);
@@ -223,29 +225,37 @@ __global__ void __launch_bounds__(kF32Threads)
     for (int64_t u = s0; u < s1; ++u) {
         const int stage = (int)((u - s0) % kF32Stages);
         const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
-        if (!ptx::mbar_wait_bounded(&bars[stage], parity, kWaitLimitNs)) {
-            abort_flag = 1;
-            atomicOr(err, kDevErrTimeout);
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+            if (lane == 0) atomicOr(err, kDevErrTimeout);
+            return;
         }
-        __syncthreads();
-        if (abort_flag) return;
-
-        const int64_t j0 = st * kF32STile;
-        const int cnt = (int)((M->N - j0 < kF32STile) ? M->N - j0 : kF32STile);
         float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
-        tile_sums<TPT>(xi, ni, bh, bl, true, &sbuf[stage][0], &sfrm[stage][0], cnt, k, S1, C1, S2, C2, M->g64, gi,
-                       j0);
+        if (!idle)
+            tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, M->g64, gi0,
+                           ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
             D2[q] += (double)S2[q] - (double)C2[q];
         }
-        __syncthreads();
-        if (tid == 0 && u + kF32Stages < s1) {
-            ptx::fence_proxy_async_smem();
-            issue(u + kF32Stages);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+        if (warp == 0) {
+            bool ok = true;
+            if (lane == 0 && u > s0 && u - 1 + kF32Stages < s1) {
+                const int64_t w = u - 1 - s0;
+                ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(w % kF32Stages)], (uint32_t)((w / kF32Stages) & 1),
+                                            kWaitLimitNs);
+                if (ok) {
+                    ptx::fence_proxy_async_smem();
+                    issue(u - 1 + kF32Stages);
+                } else {
+                    atomicOr(err, kDevErrTimeout);
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
         }
         // advance to step u + 1
         const bool tile_ends = (st + 1 == M->n_stiles);
@@ -361,6 +371,7 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
         b.N = c->N;
         b.n_ttiles = (c->N + kBTTile - 1) / kBTTile;
         b.n_stiles = (c->N + kF32STile - 1) / kF32STile;
+        b.sperm = make_schedule(c->N, kBTTile, c->N, kF32STile, 1).sperm;
         b.k = f32_consts(pk);
         b.lambda1 = pk.lambda1;
         b.lambda2 = pk.lambda2;

@@ -93,6 +93,25 @@ PairSchedule make_schedule(int64_t n_targets, int ttile, int64_t n_sources, int 
     s.per_cta = (s.total + g - 1) / g;
     s.grid = (int)((s.total + s.per_cta - 1) / s.per_cta);
     s.max_segs = (int)((s.per_cta + s.n_stiles - 1) / s.n_stiles + 1);
+    // Rows visit their source tiles with a stride near n_stiles / golden ratio
+    // (coprime to n_stiles, so a permutation): the few expensive near-field
+    // tiles, which sit together around the diagonal, are then spread evenly
+    // over the CTAs that share a row instead of landing on one of them.
+    s.sperm = 1;
+    if (s.n_stiles > 2) {
+        int64_t m = (int64_t)llround(0.6180339887498949 * (double)s.n_stiles);
+        if (m < 1) m = 1;
+        auto gcd = [](int64_t a, int64_t b) {
+            while (b != 0) {
+                const int64_t r = a % b;
+                a = b;
+                b = r;
+            }
+            return a;
+        };
+        while (gcd(m, s.n_stiles) != 1) ++m;
+        s.sperm = m % s.n_stiles;
+    }
     return s;
 }
 
@@ -143,7 +162,8 @@ ibim_status ensure_operator_workspaces(ibim_ctx* c)
 {
     if (c->ws_sized) return IBIM_OK;
     const int64_t N = c->N;
-    IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)N * 8 * sizeof(double)));
+    IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes,
+                    std::max((size_t)N * 8 * sizeof(double), (size_t)padded_nodes(N) * 2 * sizeof(float4))));
     const PairSchedule s64 = make_schedule(N, kF64TTile, N, kF64STile, f64_grid_cap(c));
     size_t need = (size_t)s64.grid * s64.max_segs * 2 * kF64TTile * sizeof(double);
     const int keep = c->f32_variant;
@@ -265,7 +285,7 @@ ibim_status ibim_build_sphere(double R, const double* centre, const double* orig
     c->band_eps = band_eps;
     for (int a = 0; a < 3; ++a) c->centroid[a] = centre[a];
     ibim_status s = build_sphere_nodes(c, R, centre, o, h, band_eps);
-    if (s == IBIM_OK) s = finish_geometry(c);
+    if (s == IBIM_OK) s = finish_geometry(c, true);
     if (s != IBIM_OK) {
         std::string msg = g_err;
         ibim_destroy(c);
@@ -297,7 +317,7 @@ ibim_status ibim_build(const double* xyz, const double* radii, const double* cha
     c->band_eps = band_eps;
     for (int a = 0; a < 3; ++a) c->centroid[a] = cen[a] / (double)Na;
     ibim_status s = build_levelset(c, Na, xyz, radii, probe, h, band_eps);
-    if (s == IBIM_OK) s = finish_geometry(c);
+    if (s == IBIM_OK) s = finish_geometry(c, true);
     if (s == IBIM_OK && charges != nullptr) s = ibim_set_charges(c, Na, xyz, charges);
     if (s != IBIM_OK) {
         std::string msg = g_err;
@@ -370,7 +390,7 @@ ibim_status ibim_build_from_nodes(int64_t N, const double* xstar, const double* 
         g_err = msg;
         return s;
     }
-    ibim_status s = finish_geometry(c);
+    ibim_status s = finish_geometry(c, false);
     if (s != IBIM_OK) {
         std::string msg = g_err;
         ibim_destroy(c);

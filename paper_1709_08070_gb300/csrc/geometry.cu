@@ -2,10 +2,12 @@
 // {|d| < eps} over the Cartesian grid, closest-point projection
 // x* = x - d grad d, unit normals and weights w = J delta_eps(d) h^3 (J = 1,
 // cosine weight).  Grid nodes are enumerated in Morton (Z-curve) order of
-// their box-local coordinates, so consecutive nodes are close in space; the
-// compaction keeps that order (block counts, one scan, ordered writes).
+// their box-local coordinates; the compaction keeps that order (block counts,
+// one scan, ordered writes), and finish_geometry then reorders the nodes of
+// built geometries into compact 32-node blocks by coordinate bisection.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ibim_internal.cuh"
@@ -189,25 +191,146 @@ ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, cons
     return IBIM_OK;
 }
 
-// FP32 copies of the geometry, positions relative to the centroid.
-__global__ void pack_geometry_f32_kernel(const double* __restrict__ geo, int64_t N, double c0, double c1,
-                                         double c2, float4* __restrict__ pos, float4* __restrict__ nrm)
+// FP32 copies of the geometry over the padded node range (positions relative
+// to the centroid; the chunk-frame pass replaces them), placeholder normals
+// past N.
+__global__ void pack_geometry_f32_kernel(const double* __restrict__ geo, int64_t N, int64_t n_pad, double c0,
+                                         double c1, double c2, float4* __restrict__ pos, float4* __restrict__ nrm)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+    if (j >= n_pad) return;
+    if (j >= N) {
+        pos[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        nrm[j] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+        return;
+    }
     pos[j] = make_float4((float)(geo[j] - c0), (float)(geo[N + j] - c1), (float)(geo[2 * N + j] - c2),
                          (float)geo[6 * N + j]);
     nrm[j] = make_float4((float)geo[3 * N + j], (float)geo[4 * N + j], (float)geo[5 * N + j], 0.0f);
 }
 
-ibim_status finish_geometry(ibim_ctx* c)
+// out[i] = in[perm[i]] for `fields` interleaved-by-field arrays of N values
+// (field f of node j at in[f * N + j]).
+template <typename T>
+__global__ void gather_fields_kernel(const T* __restrict__ in, const int64_t* __restrict__ perm, int64_t N,
+                                     int fields, T* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t j = perm[i];
+    for (int f = 0; f < fields; ++f) out[f * N + i] = in[f * N + j];
+}
+
+// out[3 i + a] = in[3 perm[i] + a] (node-major triples).
+__global__ void gather_triples_kernel(const int32_t* __restrict__ in, const int64_t* __restrict__ perm, int64_t N,
+                                      int32_t* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t j = perm[i];
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = in[3 * j + a];
+}
+
+namespace {
+
+// Recursive coordinate bisection of x* into aligned blocks of kRcbLeaf nodes:
+// each range is split across the longest side of its bounding box, the left
+// part holding a multiple of kRcbLeaf nodes (ties broken by node index, so the
+// order is a deterministic function of the coordinates).
+constexpr int64_t kRcbLeaf = 32;
+
+void rcb_split(const std::vector<double>& xs, int64_t N, std::vector<int64_t>& perm, int64_t lo, int64_t hi)
+{
+    const int64_t n = hi - lo;
+    if (n <= kRcbLeaf) return;
+    double mn[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, mx[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int64_t q = lo; q < hi; ++q)
+        for (int a = 0; a < 3; ++a) {
+            const double v = xs[a * N + perm[q]];
+            mn[a] = std::min(mn[a], v);
+            mx[a] = std::max(mx[a], v);
+        }
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+        if (mx[a] - mn[a] > mx[ax] - mn[ax]) ax = a;
+    const int64_t half = std::max<int64_t>(1, (int64_t)llround((double)n / (2.0 * kRcbLeaf)));
+    const int64_t k = lo + kRcbLeaf * half;
+    const double* key = xs.data() + ax * N;
+    std::nth_element(perm.begin() + lo, perm.begin() + k, perm.begin() + hi, [key](int64_t a, int64_t b) {
+        return key[a] < key[b] || (key[a] == key[b] && a < b);
+    });
+    rcb_split(xs, N, perm, lo, k);
+    rcb_split(xs, N, perm, k, hi);
+}
+
+}  // namespace
+
+// Reorders the nodes of a built geometry (every per-node array) into compact
+// aligned 32-node blocks: the blocks are the pair kernels' chunks, whose
+// bounding spheres decide the near/far split, so a block that straddles two
+// distant pieces of the band would send whole rows down the near path.
+static ibim_status compact_order(ibim_ctx* c)
 {
     const int64_t N = c->N;
-    IBIM_CUDA(cudaMalloc((void**)&c->d_pos32, sizeof(float4) * N));
-    IBIM_CUDA(cudaMalloc((void**)&c->d_nrm32, sizeof(float4) * N));
+    if (N <= kRcbLeaf) return IBIM_OK;
+    std::vector<double> xs(3 * (size_t)N);
+    IBIM_CUDA(cudaMemcpyAsync(xs.data(), c->d_geo64, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> perm(N);
+    for (int64_t i = 0; i < N; ++i) perm[i] = i;
+    rcb_split(xs, N, perm, 0, N);
+
+    int64_t* d_perm = nullptr;
+    double* geo = nullptr;
+    double* dist = nullptr;
+    double* curv = nullptr;
+    int32_t* ijk = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_perm, sizeof(int64_t) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&geo, sizeof(double) * 7 * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dist, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&curv, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ijk, sizeof(int32_t) * 3 * N);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_perm, perm.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        const unsigned nb = (unsigned)((N + 255) / 256);
+        gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_geo64, d_perm, N, 7, geo);
+        gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_dist, d_perm, N, 1, dist);
+        gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_curv, d_perm, N, 1, curv);
+        gather_triples_kernel<<<nb, 256, 0, c->stream>>>(c->d_ijk, d_perm, N, ijk);
+        count_launch(c, 4);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_perm);
+    if (e != cudaSuccess) {
+        cudaFree(geo);
+        cudaFree(dist);
+        cudaFree(curv);
+        cudaFree(ijk);
+        return cuda_fail(e, "compact node order", __FILE__, __LINE__);
+    }
+    std::swap(c->d_geo64, geo);
+    std::swap(c->d_dist, dist);
+    std::swap(c->d_curv, curv);
+    std::swap(c->d_ijk, ijk);
+    cudaFree(geo);
+    cudaFree(dist);
+    cudaFree(curv);
+    cudaFree(ijk);
+    return IBIM_OK;
+}
+
+ibim_status finish_geometry(ibim_ctx* c, bool reorder)
+{
+    if (reorder) IBIM_TRY(compact_order(c));
+    const int64_t N = c->N;
+    const int64_t n_pad = padded_nodes(N);
+    IBIM_CUDA(cudaMalloc((void**)&c->d_pos32, sizeof(float4) * n_pad));
+    IBIM_CUDA(cudaMalloc((void**)&c->d_nrm32, sizeof(float4) * n_pad));
     const int bs = 256;
-    pack_geometry_f32_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
-        c->d_geo64, N, c->centroid[0], c->centroid[1], c->centroid[2], c->d_pos32, c->d_nrm32);
+    pack_geometry_f32_kernel<<<(unsigned)((n_pad + bs - 1) / bs), bs, 0, c->stream>>>(
+        c->d_geo64, N, n_pad, c->centroid[0], c->centroid[1], c->centroid[2], c->d_pos32, c->d_nrm32);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_TRY(f32_chunk_frames(c));  // overwrites d_pos32 with chunk-frame positions

@@ -35,13 +35,21 @@ ibim_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 enum : unsigned { kDevErrTimeout = 1u, kDevErrBounds = 2u };
 
 // Pair-kernel tiling of the FP32 path: kF32Threads threads per CTA, each
-// thread owns kF32Tpt targets, sources stream through shared memory in tiles
-// of kF32STile nodes (two float4 per node).
+// thread owns TPT targets (kF32Tpt on the allocation-free path), sources
+// stream through kF32Stages shared-memory stages in tiles of kF32STile nodes
+// (32 bytes per node).
 constexpr int kF32Threads = 128;
-constexpr int kF32Tpt = 4;
+constexpr int kF32Tpt = 2;
 constexpr int kF32TTile = kF32Threads * kF32Tpt;
 constexpr int kF32STile = 256;
-constexpr int kF32Stages = 2;
+constexpr int kF32Stages = 4;
+constexpr int kF32MaxTpt = 4;
+// FP32 node arrays (targets, payload, chunk frames) are padded to a multiple
+// of kPadNodes placeholder-filled nodes: every source tile and every target
+// tile (at most kF32Threads * kF32MaxTpt nodes) then lies inside the arrays.
+constexpr int kPadNodes = 512;
+static_assert(kPadNodes % kF32STile == 0 && kPadNodes % (kF32Threads * kF32MaxTpt) == 0, "padding");
+__host__ __device__ inline int64_t padded_nodes(int64_t N) { return (N + kPadNodes - 1) / kPadNodes * kPadNodes; }
 // FP64 path: one target per thread, 128 threads, 128 sources per tile.
 constexpr int kF64Threads = 128;
 constexpr int kF64TTile = kF64Threads;
@@ -55,6 +63,7 @@ struct PairSchedule {
     int64_t per_cta;    // steps per CTA (last CTA may get fewer)
     int grid;           // CTAs launched (persistent, a multiple of the SM count when possible)
     int max_segs;       // partial slots per CTA
+    int64_t sperm;      // source-tile stride: position p of a row visits tile (p * sperm) mod n_stiles
 };
 
 // Physical constants of one operator application, in the form the kernels use.
@@ -200,7 +209,9 @@ ibim_status area_launch(ibim_ctx* c, double* area_host);
 // Geometry (geometry.cu)
 ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, const double* origin,
                                double h, double eps);
-ibim_status finish_geometry(ibim_ctx* c);  // FP32 packing relative to c->centroid
+// FP32 packing relative to c->centroid and chunk frames; `reorder` first puts
+// the nodes into compact aligned 32-node blocks (built geometries only).
+ibim_status finish_geometry(ibim_ctx* c, bool reorder);
 // Level-set SES (levelset.cu)
 ibim_status build_levelset(ibim_ctx* c, int64_t Na, const double* z, const double* r, double probe, double h,
                            double eps);

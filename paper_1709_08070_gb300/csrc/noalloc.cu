@@ -11,7 +11,7 @@
 // loads the library, from load until process exit.
 #include <mutex>
 
-#include "ibim_internal.cuh"
+#include "pair_f32_core.cuh"
 
 namespace ibim {
 
@@ -31,6 +31,7 @@ constexpr int kMaxSegs = 2;     // partial slots per CTA (enough once the grid h
 constexpr size_t kHeadBytes = 256;  // error word + centroid
 constexpr size_t kPosBytes = sizeof(float4) * (size_t)kMaxNodes;
 constexpr size_t kSrcBytes = 2 * sizeof(float4) * (size_t)kMaxNodes;
+static_assert(kMaxNodes % kPadNodes == 0, "the padded node range must fit the static arrays");
 constexpr size_t kPartDoubles = (size_t)kMaxCtas * kMaxSegs * 2 * kF32TTile;
 constexpr size_t kScratchBytes = kHeadBytes + 2 * kPosBytes + kSrcBytes + kPartDoubles * sizeof(double);
 
@@ -80,22 +81,37 @@ __global__ void noalloc_centroid_kernel(const double* __restrict__ xs, int64_t N
     if (threadIdx.x < 3) cen[threadIdx.x] = red[threadIdx.x][0] / (double)N;
 }
 
-// FP32 target geometry and source payload from the caller's FP64 arrays.
+// FP32 target geometry and source payload from the caller's FP64 arrays,
+// over the padded node range (one thread per node pair; placeholders past N).
 __global__ void noalloc_pack_kernel(const double* __restrict__ xs, const double* __restrict__ nrm,
                                     const double* __restrict__ w, const double* __restrict__ p, int64_t N,
-                                    const double* __restrict__ cen, float4* __restrict__ tpos,
+                                    int64_t n_pairs, const double* __restrict__ cen, float4* __restrict__ tpos,
                                     float4* __restrict__ tnrm, float4* __restrict__ src)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    const float x = (float)(xs[3 * j] - cen[0]), y = (float)(xs[3 * j + 1] - cen[1]),
-                z = (float)(xs[3 * j + 2] - cen[2]);
-    const float n0 = (float)nrm[3 * j], n1 = (float)nrm[3 * j + 1], n2 = (float)nrm[3 * j + 2];
-    const double wj = w[j];
-    tpos[j] = make_float4(x, y, z, (float)wj);
-    tnrm[j] = make_float4(n0, n1, n2, 0.0f);
-    src[2 * j] = make_float4(x, y, z, (float)(wj * p[j]));
-    src[2 * j + 1] = make_float4(n0, n1, n2, (float)(wj * p[N + j]));
+    const int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= n_pairs) return;
+    float4 y[2], m[2];
+    float a[2], b[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int64_t j = 2 * pr + e;
+        if (j < N) {
+            y[e] = make_float4((float)(xs[3 * j] - cen[0]), (float)(xs[3 * j + 1] - cen[1]),
+                               (float)(xs[3 * j + 2] - cen[2]), 0.0f);
+            m[e] = make_float4((float)nrm[3 * j], (float)nrm[3 * j + 1], (float)nrm[3 * j + 2], 0.0f);
+            const double wj = w[j];
+            a[e] = (float)(wj * p[j]);
+            b[e] = (float)(wj * p[N + j]);
+            tpos[j] = y[e];
+        } else {
+            y[e] = pad_source_pos();
+            m[e] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+            a[e] = b[e] = 0.0f;
+            tpos[j] = pad_target_pos();
+        }
+        tnrm[j] = m[e];
+    }
+    write_source_pair(src + kPairF4 * pr, y[0], y[1], m[0], m[1], a[0], a[1], b[0], b[1]);
 }
 
 }  // namespace
@@ -148,8 +164,9 @@ extern "C" ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, con
     noalloc_centroid_kernel<<<1, 1024, 0, st>>>(d_xstar, N, cen);
     IBIM_CUDA(cudaGetLastError());
     const int bs = 256;
-    noalloc_pack_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(d_xstar, d_normal, d_w, d_in, N, cen, tpos,
-                                                                     tnrm, src);
+    const int64_t n_pairs = padded_nodes(N) / 2;
+    noalloc_pack_kernel<<<(unsigned)((n_pairs + bs - 1) / bs), bs, 0, st>>>(d_xstar, d_normal, d_w, d_in, N,
+                                                                           n_pairs, cen, tpos, tnrm, src);
     IBIM_CUDA(cudaGetLastError());
     IBIM_CUDA(launch_pair_f32_raw(tpos, tnrm, src, N, s, k, part, err, st, d_xstar, d_normal));
     IBIM_CUDA(launch_fixup_raw(part, s, N, k, d_in, d_out, st));

@@ -14,9 +14,11 @@
 // Schedule: persistent CTAs walk a stream-K range of (target tile, source
 // tile) steps.  Source tiles (kF32STile nodes, 32 B each, plus the frames of
 // their 32-node chunks) are brought into shared memory by bulk async copies
-// with an mbarrier per stage (double buffered).  Each thread owns TPT
-// targets; the 32 lanes of a warp hold one aligned 32-node block per target
-// slot.
+// through kF32Stages stages with a full and an empty mbarrier each; warps
+// consume and release stages independently (no CTA-wide barrier in the step
+// loop) and thread 0 refills a stage once every warp has released it.  Each
+// thread owns TPT targets; the 32 lanes of a warp hold one aligned 32-node
+// block per target slot.
 //
 // Chunk frames: every aligned block of 32 consecutive (Morton-ordered) nodes
 // has a centre C stored as two floats (hi + lo) and a radius; node
@@ -29,16 +31,18 @@
 // Near/far split per (warp, chunk): when the two blocks' bounding spheres are
 // at least `far_dist` apart (>= 2 tau and >= 1.5 A), no pair can lie in the
 // regularisation tube (tube rule 0) and the cancellation in g is harmless, so
-// the chunk runs a branch-free loop with no tube masks.  Otherwise every pair
-// gets the tube test and, when any lane of the warp has x < 0.5, g from its
-// Taylor series (from the exponential series).  The decision is warp-uniform.
+// the chunk runs a branch-free loop with no tube masks on packed float2
+// operands, one lane per source of a payload pair (the FP32 pipe then does
+// two interactions per issued instruction).  Otherwise every pair gets the
+// tube test and, when any lane of the warp has x < 0.5, g from its Taylor
+// series (from the exponential series).  The decision is warp-uniform.
 //
 // Accumulation: per target the two sums run in FP32 over one 32-source chunk
-// (fused into the FMAs), each chunk sum is Kahan-added into a compensated FP32
-// pair (s, c), and at the end of each source tile the compensated value s - c
-// is added to FP64 accumulators.  Every CTA writes one FP64 partial per target
-// tile it touched; the fixup kernel adds the partials, scales by 1/(4 pi) and
-// adds the diagonal Lambda p.
+// (fused into the FMAs, even and odd sources apart), each chunk sum is
+// Kahan-added into a compensated FP32 pair (s, c), and at the end of each
+// source tile the compensated value s - c is added to FP64 accumulators.
+// Every CTA writes one FP64 partial per target tile it touched; the fixup
+// kernel adds the partials, scales by 1/(4 pi) and adds the diagonal Lambda p.
 #include "pair_f32_core.cuh"
 
 namespace ibim {
@@ -51,111 +55,105 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
                     Geo64 g64)
 {
     constexpr int TTILE = kF32Threads * TPT;
-    constexpr int CPT = kF32STile / kChunk;  // chunks per source tile
+    constexpr int NW = kF32Threads / 32;
     if (skip != nullptr && *skip) return;
-    __shared__ __align__(128) float4 sbuf[kF32Stages][2 * kF32STile];
-    __shared__ __align__(128) float4 sfrm[kF32Stages][2 * CPT];
-    __shared__ __align__(8) uint64_t bars[kF32Stages];
-    __shared__ int abort_flag;
+    __shared__ __align__(128) SourceStage stg[kF32Stages];
+    __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
+    __shared__ __align__(8) StagePipe pipe;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
+    const int lane = tid & 31;
     const int64_t s0 = (int64_t)blockIdx.x * s.per_cta;
     const int64_t s1 = (s0 + s.per_cta < s.total) ? s0 + s.per_cta : s.total;
     if (s0 >= s1) return;
     const bool have_frames = frames != nullptr;
 
-    if (tid == 0) {
-        for (int q = 0; q < kF32Stages; ++q) ptx::mbar_init(&bars[q], 1);
-        ptx::fence_mbar_init();
-        abort_flag = 0;
-    }
+    if (tid == 0) pipe_init(pipe, NW);
     __syncthreads();
 
     auto issue = [&](int64_t u) {
-        const int64_t st = u % s.n_stiles;
-        const int64_t j0 = st * kF32STile;
-        const int64_t cnt = (N - j0 < kF32STile) ? N - j0 : kF32STile;
+        const int64_t st = ((u % s.n_stiles) * s.sperm) % s.n_stiles;
         const int stage = (int)((u - s0) % kF32Stages);
-        const uint32_t bytes = (uint32_t)(cnt * 2 * sizeof(float4));
-        const int64_t nch = (cnt + kChunk - 1) / kChunk;
-        const uint32_t fbytes = have_frames ? (uint32_t)(nch * 2 * sizeof(float4)) : 0u;
-        ptx::mbar_arrive_expect_tx(&bars[stage], bytes + fbytes);
-        ptx::bulk_g2s(&sbuf[stage][0], src + 2 * j0, bytes, &bars[stage]);
-        if (have_frames) ptx::bulk_g2s(&sfrm[stage][0], frames + 2 * (j0 / kChunk), fbytes, &bars[stage]);
+        pipe_issue(pipe, stg[stage], stage, src + st * (kF32STile / 2) * kPairF4,
+                   have_frames ? frames + st * 2 * kChunksPerTile : nullptr);
     };
     if (tid == 0)
         for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
 
     const int64_t t_first = s0 / s.n_stiles;
     int64_t t = t_first;
-    float3 xi[TPT], ni[TPT];
-    float4 bh[TPT];  // target block centre (hi) and radius
-    float3 bl[TPT];  // target block centre (lo)
-    int64_t gi[TPT];  // target node indices
+    Targets<TPT> T;
+    int64_t gi0 = 0;  // node index of the thread's slot-0 target (slot q adds q * kF32Threads)
+    bool idle = false;  // every block of the warp lies past N
     double D1[TPT], D2[TPT];
 
+    // Targets and target-block frames of tile `tile` (arrays padded, so every
+    // index below is in range; placeholder targets give discarded sums).
     auto load_targets = [&](int64_t tile) {
+        gi0 = tile * TTILE + tid;
+        idle = tile * TTILE + warp * 32 >= N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t blk0 = tile * TTILE + q * kF32Threads + warp * 32;  // first node of the warp's block
-            const int64_t i = blk0 + (tid & 31);
-            gi[q] = (i < N) ? i : 0;
-            if (i < N) {
-                const float4 a = tpos[i];
-                const float4 b = tnrm[i];
-                xi[q] = make_float3(a.x, a.y, a.z);
-                ni[q] = make_float3(b.x, b.y, b.z);
-            } else {  // padding target far from every node; its sums are discarded
-                xi[q] = make_float3(1.0e6f, 1.0e6f, 1.0e6f);
-                ni[q] = make_float3(0.0f, 0.0f, 1.0f);
-            }
-            if (have_frames && blk0 < N) {
-                bh[q] = frames[2 * (blk0 / kChunk)];
-                const float4 l = frames[2 * (blk0 / kChunk) + 1];
-                bl[q] = make_float3(l.x, l.y, l.z);
-            } else {
-                bh[q] = make_float4(0.0f, 0.0f, 0.0f, __builtin_huge_valf());
-                bl[q] = make_float3(0.0f, 0.0f, 0.0f);
-            }
+            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const float4 a = tpos[i];
+            const float4 b = tnrm[i];
+            T.x[q] = make_float3(a.x, a.y, a.z);
+            T.nx[q] = f2(b.x);
+            T.ny[q] = f2(b.y);
+            T.nz[q] = f2(b.z);
             D1[q] = 0.0;
             D2[q] = 0.0;
         }
+        __syncwarp();
+        if (have_frames && lane < 2 * TPT) {
+            const int64_t blk0 = tile * TTILE + (int64_t)(lane >> 1) * kF32Threads + warp * 32;
+            tfrm[warp][lane] = frames[2 * (blk0 / kChunk) + (lane & 1)];
+        }
+        __syncwarp();
     };
     load_targets(t);
 
     for (int64_t u = s0; u < s1; ++u) {
         const int stage = (int)((u - s0) % kF32Stages);
         const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
-        if (!ptx::mbar_wait_bounded(&bars[stage], parity, kWaitLimitNs)) {
-            abort_flag = 1;
-            atomicOr(err, kDevErrTimeout);
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+            if (lane == 0) atomicOr(err, kDevErrTimeout);
+            return;
         }
-        __syncthreads();
-        if (abort_flag) return;
-
-        const int64_t st = u % s.n_stiles;
-        const int64_t j0 = st * kF32STile;
-        const int cnt = (int)((N - j0 < kF32STile) ? N - j0 : kF32STile);
-        const float4* sb = &sbuf[stage][0];
-
+        const int64_t sp = u % s.n_stiles;               // position in the row
+        const int64_t st = (sp * s.sperm) % s.n_stiles;  // source tile visited there
         float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
-
-        tile_sums<TPT>(xi, ni, bh, bl, have_frames, sb, &sfrm[stage][0], cnt, k, S1, C1, S2, C2, g64, gi, j0);
+        if (!idle)
+            tile_sums<TPT>(T, &tfrm[warp][0], have_frames, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64,
+                           gi0, st * kF32STile, N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
             D2[q] += (double)S2[q] - (double)C2[q];
         }
-        __syncthreads();  // every thread is done with this stage
-        if (tid == 0 && u + kF32Stages < s1) {
-            ptx::fence_proxy_async_smem();
-            issue(u + kF32Stages);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+        // thread 0 refills the stage of step u - 1 with step u - 1 + kF32Stages
+        if (warp == 0) {
+            bool ok = true;
+            if (lane == 0 && u > s0 && u - 1 + kF32Stages < s1) {
+                const int64_t v = u - 1 - s0;
+                ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(v % kF32Stages)], (uint32_t)((v / kF32Stages) & 1),
+                                            kWaitLimitNs);
+                if (ok) {
+                    ptx::fence_proxy_async_smem();
+                    issue(u - 1 + kF32Stages);
+                } else {
+                    atomicOr(err, kDevErrTimeout);
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
         }
 
-        if (st == s.n_stiles - 1 || u + 1 == s1) {
+        if (sp == s.n_stiles - 1 || u + 1 == s1) {
             const int seg = (int)(t - t_first);
             double* dst = part + ((int64_t)blockIdx.x * s.max_segs + seg) * 2 * TTILE;
 #pragma unroll
@@ -163,7 +161,7 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
                 dst[q * kF32Threads + tid] = D1[q];
                 dst[TTILE + q * kF32Threads + tid] = D2[q];
             }
-            if (st == s.n_stiles - 1 && u + 1 < s1) {
+            if (sp == s.n_stiles - 1 && u + 1 < s1) {
                 ++t;
                 load_targets(t);
             }
@@ -173,14 +171,21 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
 
 // Frames of the aligned 32-node chunks (FP64 centre split into hi + lo
 // floats, radius padded for rounding) and node coordinates relative to their
-// chunk centre.  One thread per chunk.
-__global__ void chunk_frames_kernel(const double* __restrict__ geo, int64_t N, float4* __restrict__ rel,
-                                    float4* __restrict__ frames)
+// chunk centre; chunks and nodes past N (up to the padded count) get a zero
+// frame and placeholder target positions.  One thread per chunk.
+__global__ void chunk_frames_kernel(const double* __restrict__ geo, int64_t N, int64_t n_chunks,
+                                    float4* __restrict__ rel, float4* __restrict__ frames)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
     const int64_t j0 = c * kChunk;
-    if (j0 >= N) return;
-    const int64_t j1 = (j0 + kChunk < N) ? j0 + kChunk : N;
+    const int64_t j1 = (j0 + kChunk < N) ? j0 + kChunk : (N > j0 ? N : j0);
+    for (int64_t j = j1; j < j0 + kChunk; ++j) rel[j] = pad_target_pos();
+    if (j1 == j0) {
+        frames[2 * c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        frames[2 * c + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
     double cx = 0.0, cy = 0.0, cz = 0.0;
     for (int64_t j = j0; j < j1; ++j) {
         cx += geo[j];
@@ -202,20 +207,34 @@ __global__ void chunk_frames_kernel(const double* __restrict__ geo, int64_t N, f
     frames[2 * c + 1] = make_float4((float)(cx - (double)hx), (float)(cy - (double)hy), (float)(cz - (double)hz), 0.0f);
 }
 
-// Source payload: node j -> float4 (position in its chunk frame, w psi), float4 (n, w psin).
+// Source payload of the padded node range, one thread per node pair:
+// positions in their chunk frame, a = w psi, b = w psin (placeholders past N).
 __global__ void pack_f32_kernel(const float4* __restrict__ pos, const float4* __restrict__ nrm,
-                                const double* __restrict__ w, VecRef in, int64_t N,
+                                const double* __restrict__ w, VecRef in, int64_t N, int64_t n_pairs,
                                 float4* __restrict__ src, const int* __restrict__ skip)
 {
     if (skip != nullptr && *skip) return;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+    const int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= n_pairs) return;
     const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
-    const float4 a = pos[j];
-    const float4 b = nrm[j];
-    const double wj = w[j];
-    src[2 * j] = make_float4(a.x, a.y, a.z, (float)(wj * p[j]));
-    src[2 * j + 1] = make_float4(b.x, b.y, b.z, (float)(wj * p[N + j]));
+    float4 y[2], m[2];
+    float a[2], b[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int64_t j = 2 * pr + e;
+        if (j < N) {
+            y[e] = pos[j];
+            m[e] = nrm[j];
+            const double wj = w[j];
+            a[e] = (float)(wj * p[j]);
+            b[e] = (float)(wj * p[N + j]);
+        } else {
+            y[e] = pad_source_pos();
+            m[e] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+            a[e] = b[e] = 0.0f;
+        }
+    }
+    write_source_pair(src + kPairF4 * pr, y[0], y[1], m[0], m[1], a[0], a[1], b[0], b[1]);
 }
 
 // y = Lambda p + (1/(4 pi)) sum of the partials of every CTA that touched the tile.
@@ -244,16 +263,40 @@ __global__ void fixup_kernel(const double* __restrict__ part, PairSchedule s, in
 }
 
 // Compiled variants: targets per thread x minimum CTAs per SM (register budget).
+struct PairArgs {
+    const float4* tpos;
+    const float4* tnrm;
+    const float4* src;
+    const float4* frames;
+    int64_t N;
+    PairSchedule s;
+    F32Consts k;
+    double* part;
+    unsigned* err;
+    const int* skip;
+    Geo64 g64;
+};
+
+template <int TPT, int MINB>
+static void launch_variant(const PairArgs& a, cudaStream_t stream)
+{
+    pair_f32_kernel<TPT, MINB><<<a.s.grid, kF32Threads, 0, stream>>>(a.tpos, a.tnrm, a.src, a.frames, a.N, a.s, a.k,
+                                                                      a.part, a.err, a.skip, a.g64);
+}
+
 struct F32Variant {
     int tpt, minb;
     const void* fn;
+    void (*launch)(const PairArgs&, cudaStream_t);
 };
+#define IBIM_F32_VARIANT(T, M) {T, M, (const void*)pair_f32_kernel<T, M>, launch_variant<T, M>}
 static const F32Variant kVariants[] = {
-    {2, 1, (const void*)pair_f32_kernel<2, 1>}, {2, 6, (const void*)pair_f32_kernel<2, 6>},
-    {2, 8, (const void*)pair_f32_kernel<2, 8>}, {4, 1, (const void*)pair_f32_kernel<4, 1>},
-    {4, 4, (const void*)pair_f32_kernel<4, 4>},
+    IBIM_F32_VARIANT(2, 1), IBIM_F32_VARIANT(2, 3), IBIM_F32_VARIANT(2, 4),
+    IBIM_F32_VARIANT(1, 4), IBIM_F32_VARIANT(1, 6), IBIM_F32_VARIANT(1, 8),
 };
+#undef IBIM_F32_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+static_assert(kF32Tpt <= kF32MaxTpt, "target tile");
 
 int f32_variant_count() { return kNumVariants; }
 void f32_variant_info(int v, int* tpt, int* minb)
@@ -287,10 +330,10 @@ PairSchedule f32_schedule(ibim_ctx* c)
 
 ibim_status f32_chunk_frames(ibim_ctx* c)
 {
-    const int64_t N = c->N;
-    const int64_t nch = (N + kChunk - 1) / kChunk;
+    const int64_t nch = padded_nodes(c->N) / kChunk;
     IBIM_CUDA(cudaMalloc((void**)&c->d_frames, sizeof(float4) * 2 * nch));
-    chunk_frames_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, c->stream>>>(c->d_geo64, N, c->d_pos32, c->d_frames);
+    chunk_frames_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, c->stream>>>(c->d_geo64, c->N, nch, c->d_pos32,
+                                                                               c->d_frames);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -299,11 +342,12 @@ ibim_status f32_chunk_frames(ibim_ctx* c)
 ibim_status f32_pack(ibim_ctx* c, VecRef in, const int* d_skip)
 {
     const int64_t N = c->N;
-    IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)N * 2 * sizeof(float4)));
+    const int64_t n_pairs = padded_nodes(N) / 2;
+    IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)n_pairs * kPairF4 * sizeof(float4)));
     const double* w = c->d_geo64 + 6 * N;
     const int bs = 256;
-    pack_f32_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
-        c->d_pos32, c->d_nrm32, w, in, N, (float4*)c->d_src, d_skip);
+    pack_f32_kernel<<<(unsigned)((n_pairs + bs - 1) / bs), bs, 0, c->stream>>>(
+        c->d_pos32, c->d_nrm32, w, in, N, n_pairs, (float4*)c->d_src, d_skip);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -314,31 +358,9 @@ ibim_status f32_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, c
     const int ttile = f32_ttile(c);
     const size_t need = (size_t)s.grid * s.max_segs * 2 * ttile * sizeof(double);
     IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, need));
-    const F32Consts kk = f32_consts(k);
-    const float4* srcp = (const float4*)c->d_src;
-    const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * c->N, 1, c->N};
-    switch (c->f32_variant) {
-    case 1:
-        pair_f32_kernel<2, 6><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                      s, kk, c->d_part, c->d_err, d_skip, g64);
-        break;
-    case 2:
-        pair_f32_kernel<2, 8><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                      s, kk, c->d_part, c->d_err, d_skip, g64);
-        break;
-    case 3:
-        pair_f32_kernel<4, 1><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                      s, kk, c->d_part, c->d_err, d_skip, g64);
-        break;
-    case 4:
-        pair_f32_kernel<4, 4><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                      s, kk, c->d_part, c->d_err, d_skip, g64);
-        break;
-    default:
-        pair_f32_kernel<2, 1><<<s.grid, kF32Threads, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                      s, kk, c->d_part, c->d_err, d_skip, g64);
-        break;
-    }
+    const PairArgs a{c->d_pos32, c->d_nrm32, (const float4*)c->d_src, c->d_frames, c->N, s, f32_consts(k),
+                     c->d_part, c->d_err, d_skip, Geo64{c->d_geo64, c->d_geo64 + 3 * c->N, 1, c->N}};
+    kVariants[c->f32_variant].launch(a, c->stream);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -361,16 +383,22 @@ ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, V
     return fixup_launch(c, k, s, f32_ttile(c), in, out, d_skip);
 }
 
-// Launchers on caller-supplied buffers (used by the allocation-free entry point).
-int f32_occupancy_per_sm() { return occupancy_of(0); }
+// Launchers on caller-supplied buffers (used by the allocation-free entry
+// point): variant (kF32Tpt, 1), no chunk frames (positions relative to one
+// common origin), arrays padded as above.
+int f32_occupancy_per_sm()
+{
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel<kF32Tpt, 1>, kF32Threads, 0);
+    return occ < 1 ? 1 : occ;
+}
 
 cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
                                 const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
                                 cudaStream_t stream, const double* xs_aos, const double* nrm_aos)
 {
-    const Geo64 g64{xs_aos, nrm_aos, 3, 1};
-    pair_f32_kernel<kF32Tpt, 1><<<s.grid, kF32Threads, 0, stream>>>(tpos, tnrm, src, nullptr, N, s, f32_consts(k),
-                                                                     part, err, nullptr, g64);
+    const PairArgs a{tpos, tnrm, src, nullptr, N, s, f32_consts(k), part, err, nullptr, Geo64{xs_aos, nrm_aos, 3, 1}};
+    launch_variant<kF32Tpt, 1>(a, stream);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
-// Pair arithmetic of the FP32 compensated operator, shared by the
-// single-molecule and batched pair-sum kernels.  See pair_f32.cu for the
-// formulas, the chunk frames, the near/far split and the accumulation.
+// Pair arithmetic, source payload and stage pipeline of the FP32 compensated
+// operator, shared by the single-molecule and batched pair-sum kernels.  See
+// pair_f32.cu for the formulas, the chunk frames, the near/far split and the
+// accumulation.
 #pragma once
 #include "ibim_internal.cuh"
 #include "ptx.cuh"
@@ -11,8 +12,8 @@ struct F32Consts {
     float th1, th2, omth1, omth2;
     float kappa, kl2e;        // kappa and -kappa log2(e)
     float tau2, four_tau2, k12t;
-    float far_dist;           // minimum bounding-sphere gap of a far step (A)
-    int rule0;                // tube rule 0 (far steps allowed)
+    float far_dist;           // minimum bounding-sphere gap of a far chunk (A)
+    int rule0;                // tube rule 0 (far chunks allowed)
     double tau2_d, four_tau2_d;  // the tube thresholds in FP64 (near-tie decisions)
 };
 
@@ -44,6 +45,39 @@ inline F32Consts f32_consts(const PairConsts& k)
     return c;
 }
 
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kChunk = 32;                        // chunk = frame block = compensation unit
+constexpr int kChunksPerTile = kF32STile / kChunk;
+constexpr int kPairsPerChunk = kChunk / 2;
+
+// ------------------------------------------------------------ source payload
+//
+// Sources are stored by pairs of consecutive nodes (2p, 2p + 1), 64 bytes a
+// pair, so that the far-field arithmetic runs on packed float2 operands (one
+// lane of the pair per source):
+//   [0] = (-y0.x, -y1.x, -y0.y, -y1.y)   minus the position in its chunk frame
+//   [1] = (-y0.z, -y1.z,  b0,    b1  )   b = w psin
+//   [2] = (a0 m0.x, a1 m1.x, a0 m0.y, a1 m1.y)   a = w psi, m the unit normal
+//   [3] = (a0 m0.z, a1 m1.z, 0, 0)
+// Node arrays are padded to a multiple of kPadNodes with placeholder nodes
+// (a = b = 0, far from every frame) so that every source tile is full.
+constexpr int kPairF4 = 4;
+constexpr float kPadCoord = 1.0e4f;  // placeholder source coordinate (targets use -kPadCoord)
+
+__device__ __forceinline__ void write_source_pair(float4* __restrict__ dst, float4 y0, float4 y1, float4 m0,
+                                                  float4 m1, float a0, float a1, float b0, float b1)
+{
+    dst[0] = make_float4(-y0.x, -y1.x, -y0.y, -y1.y);
+    dst[1] = make_float4(-y0.z, -y1.z, b0, b1);
+    dst[2] = make_float4(a0 * m0.x, a1 * m1.x, a0 * m0.y, a1 * m1.y);
+    dst[3] = make_float4(a0 * m0.z, a1 * m1.z, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ float4 pad_source_pos() { return make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f); }
+__device__ __forceinline__ float4 pad_target_pos() { return make_float4(-kPadCoord, -kPadCoord, -kPadCoord, 0.0f); }
+
+// ------------------------------------------------------------ arithmetic
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 {
     const float y = v - c;
@@ -67,42 +101,76 @@ __device__ __forceinline__ float g_series(float x)
     return p * x * x;
 }
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-constexpr int kChunk = 32;  // chunk = frame block = compensation unit
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// Far pair: no tube, exp-form g.  Accumulates into t1, t2.
-__device__ __forceinline__ void pair_far(const float3& xi, const float3& ni, const float4& y, const float4& m,
-                                         const F32Consts& k, float& t1, float& t2)
+// Packed constants of the far-field formula.
+struct FarConsts {
+    float2 kl2e, nkappa, neg1, neg3, th1, omth1, th2, omth2;
+};
+
+__device__ __forceinline__ FarConsts far_consts(const F32Consts& k)
 {
-    const float rx = xi.x - y.x, ry = xi.y - y.y, rz = xi.z - y.z;
-    const float rr = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float sx = fmaf(rx, ni.x, fmaf(ry, ni.y, rz * ni.z));
-    const float sy = fmaf(rx, m.x, fmaf(ry, m.y, rz * m.z));
-    const float cc = fmaf(ni.x, m.x, fmaf(ni.y, m.y, ni.z * m.z));
-    const float inv = ptx::rsqrt_approx(rr);
-    const float rho = rr * inv;
-    const float x = k.kappa * rho;
-    const float E = ptx::ex2_approx(rho * k.kl2e);
-    const float Ex = E * x;
-    const float f = 1.0f - E;
-    const float g = f - Ex;
-    const float hh = fmaf(3.0f, g, -Ex * x);
-    const float inv2 = inv * inv;
-    const float inv3 = inv2 * inv;
-    const float u1 = fmaf(k.th1, g, k.omth1);
-    const float u2 = fmaf(k.th2, g, k.omth2);
-    const float A1 = inv3 * y.w;
-    t1 = fmaf(sy * u1, A1, t1);
-    t1 = fmaf(-f, inv * m.w, t1);
-    const float w21 = fmaf(g, cc, -(hh * sx) * (sy * inv2));
-    t2 = fmaf(w21, A1, t2);
-    t2 = fmaf(sx * u2, inv3 * m.w, t2);
+    FarConsts c;
+    c.kl2e = f2(k.kl2e);
+    c.nkappa = f2(-k.kappa);
+    c.neg1 = f2(-1.0f);
+    c.neg3 = f2(-3.0f);
+    c.th1 = f2(k.th1);
+    c.omth1 = f2(k.omth1);
+    c.th2 = f2(k.th2);
+    c.omth2 = f2(k.omth2);
+    return c;
 }
 
-// All interactions of the warp's targets with one staged source tile (cnt
-// nodes at sb, chunk frames at sfrm).  xi/ni: targets in their block frame,
-// bh/bl: the target blocks' frames (radius in bh.w).  Adds the tile's sums
-// to the compensated pairs (S, C).
+// Far pairs: one target against the two sources of a payload pair, no tube,
+// exp-form g: 36 packed FP32 operations and three MUFU operations per source
+// (rsqrt, rcp and ex2 on the XU pipe, which has spare throughput here).
+// With xn = -kappa rho, En = E xn, fn = E - 1 = -(1 - E), g = -fn + En and
+// hn = E x^2 - 3 g = -(3 - B):
+//   t1 += rho^-3 u1 (r . a m) + fn rho^-1 b
+//   t2 += rho^-3 [g (n . a m) + s_x (u2 b + hn rho^-2 (r . a m))]
+// (u1 = 1 - th1 A = omth1 + th1 g, u2 likewise).
+__device__ __forceinline__ void pair_far2(float2 Xx, float2 Xy, float2 Xz, float2 nx, float2 ny, float2 nz,
+                                          const float4& A, const float4& B, const float4& C, const float4& D,
+                                          const FarConsts& c, float2& t1, float2& t2)
+{
+    const float2 rx = __fadd2_rn(Xx, make_float2(A.x, A.y));
+    const float2 ry = __fadd2_rn(Xy, make_float2(A.z, A.w));
+    const float2 rz = __fadd2_rn(Xz, make_float2(B.x, B.y));
+    const float2 b = make_float2(B.z, B.w);
+    const float2 mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w), mz = make_float2(D.x, D.y);
+    float2 rr = __fmul2_rn(rx, rx);
+    rr = __ffma2_rn(ry, ry, rr);
+    rr = __ffma2_rn(rz, rz, rr);
+    float2 sx = __fmul2_rn(rx, nx);
+    sx = __ffma2_rn(ry, ny, sx);
+    sx = __ffma2_rn(rz, nz, sx);
+    float2 sa = __fmul2_rn(rx, mx);
+    sa = __ffma2_rn(ry, my, sa);
+    sa = __ffma2_rn(rz, mz, sa);
+    float2 ca = __fmul2_rn(nx, mx);
+    ca = __ffma2_rn(ny, my, ca);
+    ca = __ffma2_rn(nz, mz, ca);
+    const float2 inv = make_float2(ptx::rsqrt_approx(rr.x), ptx::rsqrt_approx(rr.y));
+    const float2 rho = __fmul2_rn(rr, inv);
+    const float2 ea = __fmul2_rn(rho, c.kl2e);
+    const float2 xn = __fmul2_rn(rho, c.nkappa);
+    const float2 E = make_float2(ptx::ex2_approx(ea.x), ptx::ex2_approx(ea.y));
+    const float2 En = __fmul2_rn(E, xn);
+    const float2 fn = __fadd2_rn(E, c.neg1);
+    const float2 g = __ffma2_rn(fn, c.neg1, En);
+    const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));
+    const float2 inv2 = make_float2(ptx::rcp_approx(rr.x), ptx::rcp_approx(rr.y));
+    const float2 P = __fmul2_rn(inv2, inv);
+    const float2 u1 = __ffma2_rn(c.th1, g, c.omth1);
+    const float2 u2 = __ffma2_rn(c.th2, g, c.omth2);
+    t1 = __ffma2_rn(P, __fmul2_rn(u1, sa), t1);
+    t1 = __ffma2_rn(__fmul2_rn(fn, inv), b, t1);
+    const float2 v = __ffma2_rn(__fmul2_rn(hn, inv2), sa, __fmul2_rn(u2, b));
+    const float2 w = __ffma2_rn(sx, v, __fmul2_rn(g, ca));
+    t2 = __ffma2_rn(P, w, t2);
+}
+
 // Tube test of one pair in FP64 from the FP64 coordinates of target i and
 // source j (the oracle's definition): used when the FP32 test is within
 // rounding of a threshold, so that near-ties are decided as in FP64.
@@ -122,103 +190,193 @@ static __device__ __noinline__ bool tube_f64(const Geo64& g, int64_t i, int64_t 
 // FP32 tube test defers to tube_f64.
 constexpr float kTieBand = 1e-5f;
 
+// Near pairs: TPT targets against the two sources of a payload pair, scalar,
+// with the tube test (FP64 re-decision of near-ties) and the series form of
+// g when any lane of the warp has kappa rho < 0.5.
 template <int TPT>
-__device__ __forceinline__ void tile_sums(const float3 (&xi)[TPT], const float3 (&ni)[TPT], const float4 (&bh)[TPT],
-                                          const float3 (&bl)[TPT], bool have_frames, const float4* sb,
-                                          const float4* sfrm, int cnt, const F32Consts& k, float (&S1)[TPT],
-                                          float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT], const Geo64& g64,
-                                          const int64_t (&gi)[TPT], int64_t j0)
+__device__ __forceinline__ void near_pair(const float3 (&X)[TPT], const float2 (&nx)[TPT], const float2 (&ny)[TPT],
+                                          const float2 (&nz)[TPT], const float4& A, const float4& B,
+                                          const float4& C, const float4& D, const F32Consts& k, float2 (&t1)[TPT],
+                                          float2 (&t2)[TPT], const Geo64& g64, int64_t gi0, int64_t j, int64_t N)
 {
-    for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-        const int c1 = (c0 + kChunk < cnt) ? c0 + kChunk : cnt;
+    const float yx[2] = {A.x, A.y}, yy[2] = {A.z, A.w}, yz[2] = {B.x, B.y}, bb[2] = {B.z, B.w};
+    const float mx[2] = {C.x, C.y}, my[2] = {C.z, C.w}, mz[2] = {D.x, D.y};
+    float rr[TPT][2], sx[TPT][2], sa[TPT][2], ca[TPT][2], inv[TPT][2], x[TPT][2], E[TPT][2];
+    bool tube[TPT][2];
+    bool need = false;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float rx = X[q].x + yx[e], ry = X[q].y + yy[e], rz = X[q].z + yz[e];
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            rr[q][e] = r2;
+            sx[q][e] = fmaf(rx, nx[q].x, fmaf(ry, ny[q].x, rz * nz[q].x));
+            sa[q][e] = fmaf(rx, mx[e], fmaf(ry, my[e], rz * mz[e]));
+            ca[q][e] = fmaf(nx[q].x, mx[e], fmaf(ny[q].x, my[e], nz[q].x * mz[e]));
+            const float rp2 = fmaf(-sx[q][e], sx[q][e], r2);
+            tube[q][e] = (rp2 < k.tau2) & (r2 < k.four_tau2);
+            const bool tie = (fabsf(rp2 - k.tau2) < kTieBand * k.tau2) |
+                             (fabsf(r2 - k.four_tau2) < kTieBand * k.four_tau2);
+            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            if (tie && g64.x != nullptr && i < N && j + e < N)
+                tube[q][e] = tube_f64(g64, i, j + e, k.tau2_d, k.four_tau2_d);
+            const float rrs = fmaxf(r2, 1.0e-30f);
+            inv[q][e] = ptx::rsqrt_approx(rrs);
+            const float rho = rrs * inv[q][e];
+            x[q][e] = k.kappa * rho;
+            E[q][e] = ptx::ex2_approx(rho * k.kl2e);
+            need |= (x[q][e] < 0.5f);
+        }
+    }
+    const bool series = __any_sync(0xffffffffu, need);
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float xe = x[q][e];
+            const float Ex = E[q][e] * xe;
+            float f = 1.0f - E[q][e];
+            float g = f - Ex;
+            if (series && xe < 0.5f) {
+                g = g_series(xe);
+                f = g + Ex;
+            }
+            const float hh = fmaf(3.0f, g, -Ex * xe);
+            const float iv = inv[q][e];
+            const float inv2 = iv * iv;
+            const float i3 = tube[q][e] ? 0.0f : inv2 * iv;
+            const float Q = tube[q][e] ? k.k12t : f * iv;
+            const float u1 = fmaf(k.th1, g, k.omth1);
+            const float u2 = fmaf(k.th2, g, k.omth2);
+            const float d1 = fmaf(i3 * u1, sa[q][e], -Q * bb[e]);
+            const float v = fmaf(u2, bb[e], -(hh * inv2) * sa[q][e]);
+            const float d2 = i3 * fmaf(g, ca[q][e], sx[q][e] * v);
+            if (e == 0) {
+                t1[q].x += d1;
+                t2[q].x += d2;
+            } else {
+                t1[q].y += d1;
+                t2[q].y += d2;
+            }
+        }
+    }
+}
+
+// Per-thread target slots: position in the target block's frame and the
+// normal, duplicated into both lanes of a float2 for the packed formula.
+template <int TPT>
+struct Targets {
+    float3 x[TPT];
+    float2 nx[TPT], ny[TPT], nz[TPT];
+};
+
+// All interactions of one thread's targets with one staged source tile
+// (kF32STile nodes as kF32STile / 2 payload pairs at sb, chunk frames at
+// sfrm).  tfrm: the frames of the warp's target blocks (2 float4 per slot).
+// Adds the tile's sums to the compensated pairs (S, C).
+template <int TPT>
+__device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* tfrm, bool have_frames,
+                                          const float4* sb, const float4* sfrm, const F32Consts& k,
+                                          float (&S1)[TPT], float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
+                                          const Geo64& g64, int64_t gi0, int64_t j0, int64_t N)
+{
+    const FarConsts fc = far_consts(k);
+#pragma unroll 1
+    for (int c = 0; c < kChunksPerTile; ++c) {
         // targets in the source chunk's frame; far test on the two bounding spheres
         float3 X[TPT];
         bool far = have_frames && k.rule0;
         if (have_frames) {
-            const float4 mh = sfrm[2 * (c0 / kChunk)];
-            const float4 ml = sfrm[2 * (c0 / kChunk) + 1];
+            const float4 mh = sfrm[2 * c];
+            const float4 ml = sfrm[2 * c + 1];
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
-                const float dx = (bh[q].x - mh.x) + (bl[q].x - ml.x);
-                const float dy = (bh[q].y - mh.y) + (bl[q].y - ml.y);
-                const float dz = (bh[q].z - mh.z) + (bl[q].z - ml.z);
-                X[q] = make_float3(xi[q].x + dx, xi[q].y + dy, xi[q].z + dz);
-                const float lim = k.far_dist + bh[q].w + mh.w;
+                const float4 th = tfrm[2 * q];
+                const float4 tl = tfrm[2 * q + 1];
+                const float dx = (th.x - mh.x) + (tl.x - ml.x);
+                const float dy = (th.y - mh.y) + (tl.y - ml.y);
+                const float dz = (th.z - mh.z) + (tl.z - ml.z);
+                X[q] = make_float3(T.x[q].x + dx, T.x[q].y + dy, T.x[q].z + dz);
+                const float lim = k.far_dist + th.w + mh.w;
                 far = far && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim);
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < TPT; ++q) X[q] = xi[q];
+            for (int q = 0; q < TPT; ++q) X[q] = T.x[q];
         }
-        float t1[TPT], t2[TPT];
+        float2 t1[TPT], t2[TPT];
 #pragma unroll
-        for (int q = 0; q < TPT; ++q) t1[q] = t2[q] = 0.0f;
+        for (int q = 0; q < TPT; ++q) t1[q] = t2[q] = make_float2(0.0f, 0.0f);
+        const float4* cb = sb + c * kPairsPerChunk * kPairF4;
         if (far) {
-#pragma unroll 4
-            for (int j = c0; j < c1; ++j) {
-                const float4 y = sb[2 * j];
-                const float4 m = sb[2 * j + 1];
+            float2 Xx[TPT], Xy[TPT], Xz[TPT];
 #pragma unroll
-                for (int q = 0; q < TPT; ++q) pair_far(X[q], ni[q], y, m, k, t1[q], t2[q]);
+            for (int q = 0; q < TPT; ++q) {
+                Xx[q] = f2(X[q].x);
+                Xy[q] = f2(X[q].y);
+                Xz[q] = f2(X[q].z);
+            }
+#pragma unroll 4
+            for (int p = 0; p < kPairsPerChunk; ++p) {
+                const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
+                const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
+#pragma unroll
+                for (int q = 0; q < TPT; ++q)
+                    pair_far2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, t1[q], t2[q]);
             }
         } else {
-            for (int j = c0; j < c1; ++j) {
-                const float4 y = sb[2 * j];
-                const float4 m = sb[2 * j + 1];
-                float rr[TPT], sx[TPT], sy[TPT], cc[TPT], inv[TPT], x[TPT], E[TPT];
-                bool tube[TPT];
-                bool need = false;
-#pragma unroll
-                for (int q = 0; q < TPT; ++q) {
-                    const float rx = X[q].x - y.x, ry = X[q].y - y.y, rz = X[q].z - y.z;
-                    rr[q] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    sx[q] = fmaf(rx, ni[q].x, fmaf(ry, ni[q].y, rz * ni[q].z));
-                    sy[q] = fmaf(rx, m.x, fmaf(ry, m.y, rz * m.z));
-                    cc[q] = fmaf(ni[q].x, m.x, fmaf(ni[q].y, m.y, ni[q].z * m.z));
-                    const float rp2 = fmaf(-sx[q], sx[q], rr[q]);
-                    tube[q] = (rp2 < k.tau2) & (rr[q] < k.four_tau2);
-                    const bool tie = (fabsf(rp2 - k.tau2) < kTieBand * k.tau2) |
-                                     (fabsf(rr[q] - k.four_tau2) < kTieBand * k.four_tau2);
-                    if (tie && g64.x != nullptr) tube[q] = tube_f64(g64, gi[q], j0 + j, k.tau2_d, k.four_tau2_d);
-                    const float rrs = fmaxf(rr[q], 1.0e-30f);
-                    inv[q] = ptx::rsqrt_approx(rrs);
-                    const float rho = rrs * inv[q];
-                    x[q] = k.kappa * rho;
-                    E[q] = ptx::ex2_approx(rho * k.kl2e);
-                    need |= (x[q] < 0.5f);
-                }
-                const bool series = __any_sync(0xffffffffu, need);
-#pragma unroll
-                for (int q = 0; q < TPT; ++q) {
-                    const float Ex = E[q] * x[q];
-                    float f = 1.0f - E[q];
-                    float g = f - Ex;
-                    if (series && x[q] < 0.5f) {
-                        g = g_series(x[q]);
-                        f = g + Ex;
-                    }
-                    const float hh = fmaf(3.0f, g, -Ex * x[q]);
-                    const float inv2 = inv[q] * inv[q];
-                    const float inv3 = inv2 * inv[q];
-                    const float u1 = fmaf(k.th1, g, k.omth1);
-                    const float u2 = fmaf(k.th2, g, k.omth2);
-                    const float i3 = tube[q] ? 0.0f : inv3;
-                    const float Q = tube[q] ? k.k12t : f * inv[q];
-                    const float A1 = i3 * y.w;
-                    t1[q] = fmaf(sy[q] * u1, A1, t1[q]);
-                    t1[q] = fmaf(-Q, m.w, t1[q]);
-                    const float w21 = fmaf(g, cc[q], -(hh * sx[q]) * (sy[q] * inv2));
-                    t2[q] = fmaf(w21, A1, t2[q]);
-                    t2[q] = fmaf(sx[q] * u2, i3 * m.w, t2[q]);
-                }
+            for (int p = 0; p < kPairsPerChunk; ++p) {
+                const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
+                const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
+                near_pair<TPT>(X, T.nx, T.ny, T.nz, A, B, C, D, k, t1, t2, g64, gi0,
+                               j0 + (int64_t)c * kChunk + 2 * p, N);
             }
         }
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            kahan_add(S1[q], C1[q], t1[q]);
-            kahan_add(S2[q], C2[q], t2[q]);
+            kahan_add(S1[q], C1[q], t1[q].x + t1[q].y);
+            kahan_add(S2[q], C2[q], t2[q].x + t2[q].y);
         }
     }
+}
+
+// ------------------------------------------------------------ stage pipeline
+//
+// kF32Stages shared-memory stages, each with a `full` barrier (one producer
+// arrival + the bulk-copy bytes) and an `empty` barrier (one arrival per
+// warp once it is done with the stage).  Warps consume stages independently;
+// thread 0 refills the stage of step u - 1 while at step u, so warps never
+// meet at a CTA-wide barrier inside the step loop.
+struct SourceStage {
+    float4 buf[kF32STile / 2 * kPairF4];
+    float4 frm[2 * kChunksPerTile];
+};
+constexpr uint32_t kStagePayloadBytes = kF32STile / 2 * kPairF4 * sizeof(float4);
+constexpr uint32_t kStageFrameBytes = 2 * kChunksPerTile * sizeof(float4);
+
+struct StagePipe {
+    uint64_t full[kF32Stages];
+    uint64_t empty[kF32Stages];
+};
+
+__device__ __forceinline__ void pipe_init(StagePipe& P, int nwarps)
+{
+    for (int q = 0; q < kF32Stages; ++q) {
+        ptx::mbar_init(&P.full[q], 1);
+        ptx::mbar_init(&P.empty[q], (uint32_t)nwarps);
+    }
+    ptx::fence_mbar_init();
+}
+
+// Stage a source tile (payload at src, frames at frm or none).
+__device__ __forceinline__ void pipe_issue(StagePipe& P, SourceStage& S, int stage, const float4* src,
+                                           const float4* frm)
+{
+    const uint32_t fbytes = frm != nullptr ? kStageFrameBytes : 0u;
+    ptx::mbar_arrive_expect_tx(&P.full[stage], kStagePayloadBytes + fbytes);
+    ptx::bulk_g2s(&S.buf[0], src, kStagePayloadBytes, &P.full[stage]);
+    if (frm != nullptr) ptx::bulk_g2s(&S.frm[0], frm, fbytes, &P.full[stage]);
 }
 
 }  // namespace ibim
