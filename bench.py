@@ -186,7 +186,7 @@ def run_ours(args):
     N = ctx.N
     P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
     variant, bps, tune_ms = ctx.autotune(P)
-    tpt, minb = ibim.ibim_f32_variants()[variant]
+    tpt, minb, nthr = ibim.ibim_f32_variants()[variant]
     opts = dict(precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=1000, start=0, certify=0)
     dp = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -206,11 +206,13 @@ def run_ours(args):
     barrier()
     clocks.start()
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("ibim_timed_steps")  # lets a profiler select exactly the timed launches
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
         infos.append(ctx.solve(P, dp, **opts))
         ev[i][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t_wall
     ck = clocks.stop()
@@ -303,7 +305,7 @@ def run_ours(args):
                 "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
                                l2="256 MB buffer written between timed steps",
                                f32_variant={"index": variant, "targets_per_thread": tpt, "min_ctas_per_sm": minb,
-                                            "ctas_per_sm": bps}),
+                                            "threads_per_cta": nthr, "ctas_per_sm": bps}),
                 "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
                 "wall_s_timed": wall}
         line.update(extra)

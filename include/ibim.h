@@ -255,11 +255,12 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
 /*
  * FP32 pair-kernel variants (a GPU tuning device, not part of the paper's
  * method).  The library compiles a small table of variants, each with a fixed
- * number of targets per thread and a register budget (minimum CTAs per SM);
- * ibim_f32_variant_info describes entry v of [0, ibim_f32_variant_count()).
+ * number of targets per thread, a register budget (minimum CTAs per SM) and
+ * a CTA size; ibim_f32_variant_info describes entry v of
+ * [0, ibim_f32_variant_count()) (outputs may be NULL).
  */
 int ibim_f32_variant_count(void);
-ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm);
+ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm, int* threads_per_cta);
 
 /*
  * Autotuner: times every variant on this context's geometry with CUDA events,

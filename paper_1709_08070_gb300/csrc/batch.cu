@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kF32Threads)
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
             tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, M->g64, gi0,
-                           ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
+                           kF32Threads, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];

@@ -34,21 +34,21 @@ ibim_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 // Device-side error word bits (written by bounded waits instead of trapping).
 enum : unsigned { kDevErrTimeout = 1u, kDevErrBounds = 2u };
 
-// Pair-kernel tiling of the FP32 path: kF32Threads threads per CTA, each
-// thread owns TPT targets (kF32Tpt on the allocation-free path), sources
-// stream through kF32Stages shared-memory stages in tiles of kF32STile nodes
-// (32 bytes per node).
+// Pair-kernel tiling of the FP32 path: a CTA of THREADS threads (a variant
+// parameter; kF32Threads on the batched and allocation-free paths), each
+// thread owning TPT targets, streams sources through kF32Stages shared-memory
+// stages in tiles of kF32STile nodes (32 bytes per node).
 constexpr int kF32Threads = 128;
 constexpr int kF32Tpt = 2;
 constexpr int kF32TTile = kF32Threads * kF32Tpt;
 constexpr int kF32STile = 256;
 constexpr int kF32Stages = 4;
-constexpr int kF32MaxTpt = 4;
+constexpr int kF32MaxTTile = 1024;  // largest target tile of any variant
 // FP32 node arrays (targets, payload, chunk frames) are padded to a multiple
 // of kPadNodes placeholder-filled nodes: every source tile and every target
-// tile (at most kF32Threads * kF32MaxTpt nodes) then lies inside the arrays.
-constexpr int kPadNodes = 512;
-static_assert(kPadNodes % kF32STile == 0 && kPadNodes % (kF32Threads * kF32MaxTpt) == 0, "padding");
+// tile then lies inside the arrays.
+constexpr int kPadNodes = 1024;
+static_assert(kPadNodes % kF32STile == 0 && kPadNodes % kF32MaxTTile == 0, "padding");
 __host__ __device__ inline int64_t padded_nodes(int64_t N) { return (N + kPadNodes - 1) / kPadNodes * kPadNodes; }
 // FP64 path: one target per thread, 128 threads, 128 sources per tile.
 constexpr int kF64Threads = 128;
@@ -188,7 +188,7 @@ int f32_grid_cap(ibim_ctx* c);
 int f32_ttile(const ibim_ctx* c);
 int f32_max_bps(int variant);
 int f32_variant_count();
-void f32_variant_info(int v, int* tpt, int* minb);
+void f32_variant_info(int v, int* tpt, int* minb, int* threads);
 PairSchedule f32_schedule(ibim_ctx* c);
 ibim_status f32_chunk_frames(ibim_ctx* c);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,

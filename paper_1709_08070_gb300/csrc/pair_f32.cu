@@ -47,15 +47,16 @@
 
 namespace ibim {
 
-template <int TPT, int MINB>
-__global__ void __launch_bounds__(kF32Threads, MINB)
+template <int TPT, int MINB, int THREADS>
+__global__ void __launch_bounds__(THREADS, MINB)
     pair_f32_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm,
                     const float4* __restrict__ src, const float4* __restrict__ frames, int64_t N, PairSchedule s,
                     F32Consts k, double* __restrict__ part, unsigned* __restrict__ err, const int* __restrict__ skip,
                     Geo64 g64)
 {
-    constexpr int TTILE = kF32Threads * TPT;
-    constexpr int NW = kF32Threads / 32;
+    constexpr int TTILE = THREADS * TPT;
+    constexpr int NW = THREADS / 32;
+    static_assert(TTILE <= kF32MaxTTile, "target tile");
     if (skip != nullptr && *skip) return;
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
     const int64_t t_first = s0 / s.n_stiles;
     int64_t t = t_first;
     Targets<TPT> T;
-    int64_t gi0 = 0;  // node index of the thread's slot-0 target (slot q adds q * kF32Threads)
+    int64_t gi0 = 0;  // node index of the thread's slot-0 target (slot q adds q * THREADS)
     bool idle = false;  // every block of the warp lies past N
     double D1[TPT], D2[TPT];
 
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
         idle = tile * TTILE + warp * 32 >= N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const int64_t i = gi0 + (int64_t)q * THREADS;
             const float4 a = tpos[i];
             const float4 b = tnrm[i];
             T.x[q] = make_float3(a.x, a.y, a.z);
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
         }
         __syncwarp();
         if (have_frames && lane < 2 * TPT) {
-            const int64_t blk0 = tile * TTILE + (int64_t)(lane >> 1) * kF32Threads + warp * 32;
+            const int64_t blk0 = tile * TTILE + (int64_t)(lane >> 1) * THREADS + warp * 32;
             tfrm[warp][lane] = frames[2 * (blk0 / kChunk) + (lane & 1)];
         }
         __syncwarp();
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
             tile_sums<TPT>(T, &tfrm[warp][0], have_frames, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64,
-                           gi0, st * kF32STile, N);
+                           gi0, THREADS, st * kF32STile, N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
@@ -158,8 +159,8 @@ __global__ void __launch_bounds__(kF32Threads, MINB)
             double* dst = part + ((int64_t)blockIdx.x * s.max_segs + seg) * 2 * TTILE;
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
-                dst[q * kF32Threads + tid] = D1[q];
-                dst[TTILE + q * kF32Threads + tid] = D2[q];
+                dst[q * THREADS + tid] = D1[q];
+                dst[TTILE + q * THREADS + tid] = D2[q];
             }
             if (sp == s.n_stiles - 1 && u + 1 < s1) {
                 ++t;
@@ -277,44 +278,45 @@ struct PairArgs {
     Geo64 g64;
 };
 
-template <int TPT, int MINB>
+template <int TPT, int MINB, int THREADS>
 static void launch_variant(const PairArgs& a, cudaStream_t stream)
 {
-    pair_f32_kernel<TPT, MINB><<<a.s.grid, kF32Threads, 0, stream>>>(a.tpos, a.tnrm, a.src, a.frames, a.N, a.s, a.k,
-                                                                      a.part, a.err, a.skip, a.g64);
+    pair_f32_kernel<TPT, MINB, THREADS><<<a.s.grid, THREADS, 0, stream>>>(a.tpos, a.tnrm, a.src, a.frames, a.N, a.s,
+                                                                          a.k, a.part, a.err, a.skip, a.g64);
 }
 
 struct F32Variant {
-    int tpt, minb;
+    int tpt, minb, threads;
     const void* fn;
     void (*launch)(const PairArgs&, cudaStream_t);
 };
-#define IBIM_F32_VARIANT(T, M) {T, M, (const void*)pair_f32_kernel<T, M>, launch_variant<T, M>}
+#define IBIM_F32_VARIANT(T, M, W) {T, M, W, (const void*)pair_f32_kernel<T, M, W>, launch_variant<T, M, W>}
 static const F32Variant kVariants[] = {
-    IBIM_F32_VARIANT(2, 1), IBIM_F32_VARIANT(2, 3), IBIM_F32_VARIANT(2, 4),
-    IBIM_F32_VARIANT(1, 4), IBIM_F32_VARIANT(1, 6), IBIM_F32_VARIANT(1, 8),
+    IBIM_F32_VARIANT(2, 1, 128), IBIM_F32_VARIANT(2, 3, 128), IBIM_F32_VARIANT(2, 4, 128),
+    IBIM_F32_VARIANT(1, 6, 128), IBIM_F32_VARIANT(2, 2, 256), IBIM_F32_VARIANT(2, 1, 512),
+    IBIM_F32_VARIANT(1, 1, 512),
 };
 #undef IBIM_F32_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
-static_assert(kF32Tpt <= kF32MaxTpt, "target tile");
 
 int f32_variant_count() { return kNumVariants; }
-void f32_variant_info(int v, int* tpt, int* minb)
+void f32_variant_info(int v, int* tpt, int* minb, int* threads)
 {
     *tpt = kVariants[v].tpt;
     *minb = kVariants[v].minb;
+    *threads = kVariants[v].threads;
 }
 
 static int occupancy_of(int v)
 {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kVariants[v].fn, kF32Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kVariants[v].fn, kVariants[v].threads, 0);
     return occ < 1 ? 1 : occ;
 }
 
 int f32_max_bps(int v) { return occupancy_of(v); }
 
-int f32_ttile(const ibim_ctx* c) { return kF32Threads * kVariants[c->f32_variant].tpt; }
+int f32_ttile(const ibim_ctx* c) { return kVariants[c->f32_variant].threads * kVariants[c->f32_variant].tpt; }
 
 int f32_grid_cap(ibim_ctx* c)
 {
@@ -389,7 +391,7 @@ ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, V
 int f32_occupancy_per_sm()
 {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel<kF32Tpt, 1>, kF32Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_f32_kernel<kF32Tpt, 1, kF32Threads>, kF32Threads, 0);
     return occ < 1 ? 1 : occ;
 }
 
@@ -398,7 +400,7 @@ cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const fl
                                 cudaStream_t stream, const double* xs_aos, const double* nrm_aos)
 {
     const PairArgs a{tpos, tnrm, src, nullptr, N, s, f32_consts(k), part, err, nullptr, Geo64{xs_aos, nrm_aos, 3, 1}};
-    launch_variant<kF32Tpt, 1>(a, stream);
+    launch_variant<kF32Tpt, 1, kF32Threads>(a, stream);
     return cudaGetLastError();
 }
 

@@ -197,7 +197,8 @@ template <int TPT>
 __device__ __forceinline__ void near_pair(const float3 (&X)[TPT], const float2 (&nx)[TPT], const float2 (&ny)[TPT],
                                           const float2 (&nz)[TPT], const float4& A, const float4& B,
                                           const float4& C, const float4& D, const F32Consts& k, float2 (&t1)[TPT],
-                                          float2 (&t2)[TPT], const Geo64& g64, int64_t gi0, int64_t j, int64_t N)
+                                          float2 (&t2)[TPT], const Geo64& g64, int64_t gi0, int qstride, int64_t j,
+                                          int64_t N)
 {
     const float yx[2] = {A.x, A.y}, yy[2] = {A.z, A.w}, yz[2] = {B.x, B.y}, bb[2] = {B.z, B.w};
     const float mx[2] = {C.x, C.y}, my[2] = {C.z, C.w}, mz[2] = {D.x, D.y};
@@ -218,7 +219,7 @@ __device__ __forceinline__ void near_pair(const float3 (&X)[TPT], const float2 (
             tube[q][e] = (rp2 < k.tau2) & (r2 < k.four_tau2);
             const bool tie = (fabsf(rp2 - k.tau2) < kTieBand * k.tau2) |
                              (fabsf(r2 - k.four_tau2) < kTieBand * k.four_tau2);
-            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const int64_t i = gi0 + (int64_t)q * qstride;
             if (tie && g64.x != nullptr && i < N && j + e < N)
                 tube[q][e] = tube_f64(g64, i, j + e, k.tau2_d, k.four_tau2_d);
             const float rrs = fmaxf(r2, 1.0e-30f);
@@ -274,12 +275,13 @@ struct Targets {
 // All interactions of one thread's targets with one staged source tile
 // (kF32STile nodes as kF32STile / 2 payload pairs at sb, chunk frames at
 // sfrm).  tfrm: the frames of the warp's target blocks (2 float4 per slot).
-// Adds the tile's sums to the compensated pairs (S, C).
+// Adds the tile's sums to the compensated pairs (S, C).  gi0: node index of
+// the thread's slot-0 target, slot q adding q * qstride.
 template <int TPT>
 __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* tfrm, bool have_frames,
                                           const float4* sb, const float4* sfrm, const F32Consts& k,
                                           float (&S1)[TPT], float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
-                                          const Geo64& g64, int64_t gi0, int64_t j0, int64_t N)
+                                          const Geo64& g64, int64_t gi0, int qstride, int64_t j0, int64_t N)
 {
     const FarConsts fc = far_consts(k);
 #pragma unroll 1
@@ -329,7 +331,7 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
             for (int p = 0; p < kPairsPerChunk; ++p) {
                 const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
                 const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
-                near_pair<TPT>(X, T.nx, T.ny, T.nz, A, B, C, D, k, t1, t2, g64, gi0,
+                near_pair<TPT>(X, T.nx, T.ny, T.nz, A, B, C, D, k, t1, t2, g64, gi0, qstride,
                                j0 + (int64_t)c * kChunk + 2 * p, N);
             }
         }

@@ -82,7 +82,8 @@ _SIGS = {
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
-    "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
     "ibim_get_levelset": [_V, _I64P, _I64P, _D],
     "ibim_solve_batch": [ctypes.c_int, ctypes.POINTER(_V), ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts),
@@ -335,13 +336,14 @@ def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=Non
 
 
 def ibim_f32_variants():
-    """[(targets_per_thread, min_ctas_per_sm)] of the compiled FP32 variants."""
+    """[(targets_per_thread, min_ctas_per_sm, threads_per_cta)] of the compiled FP32 variants."""
     out = []
     for v in range(lib().ibim_f32_variant_count()):
         t = ctypes.c_int(0)
         m = ctypes.c_int(0)
-        _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m)))
-        out.append((t.value, m.value))
+        w = ctypes.c_int(0)
+        _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m), ctypes.byref(w)))
+        out.append((t.value, m.value, w.value))
     return out
 
 

@@ -267,3 +267,25 @@ def test_kirkwood_fp32_all_rows_against_fp64():
         assert max(r) < 1e-6, r
         assert worst < 1e-5, worst
     ctx.close()
+
+
+def test_every_fp32_variant_matches_fp64():
+    """Each compiled FP32 pair-kernel variant (targets per thread, register
+    budget, CTA size) and a reduced persistent grid give the same operator as
+    the FP64 path on a sphere with several target and source tiles."""
+    ctx = ibim.Context.sphere(6.0, h=0.25, band_eps=0.5)
+    N = ctx.N
+    P, _ = _phys(2.0, 80.0, 0.1257, 0.25)
+    p = _dev(inputs.random_vector(2 * N, seed=2))
+    y64 = torch.empty_like(p)
+    ctx.matvec(P, p, y64, precision=F64)
+    a = y64.cpu().numpy()
+    y32 = torch.empty_like(p)
+    for v, (tpt, minb, nthr) in enumerate(ibim.ibim_f32_variants()):
+        for bps in (0, 1):
+            ctx.set_f32_variant(v, bps)
+            ctx.matvec(P, p, y32, precision=F32)
+            torch.cuda.synchronize()
+            r = _both_blocks(y32.cpu().numpy(), a, N)
+            assert max(r) < 1e-6, (v, tpt, minb, nthr, bps, r)
+    ctx.close()
