@@ -42,6 +42,10 @@ WORKLOAD = {"workload": "kirkwood_sphere", "R": 20.0, "h": 0.5, "band_k": 2, "ta
 # counted; the per-chunk frame offsets and compensation add about 0.5.
 F32_OPS_PER_INTERACTION = 36
 FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this
+# workload, by variant (targets/thread, min CTAs/SM, threads/CTA), from the ncu
+# full-set capture summarised in profiles/pair_f32_kernel_kirkwood80k.md.
+NCU_TRAFFIC_BYTES = {(2, 1, 512): 5.681664e6}
 METRIC = "IBIM matvec interactions/s"
 
 
@@ -241,7 +245,7 @@ def run_ours(args):
     per_launch = tim["pair_interactions"] / max(1, tim["pair_launches"])
     achieved_ops = F32_OPS_PER_INTERACTION * per_launch / (avg_pair_ms * 1e-3)
     roofline = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": achieved_ops / peak_ops, "traffic": None,
+                "frac": achieved_ops / peak_ops, "traffic": NCU_TRAFFIC_BYTES.get((tpt, minb, nthr)),
                 "kernel": "pair_f32_kernel", "ops_per_interaction": F32_OPS_PER_INTERACTION,
                 "interactions_per_launch": per_launch, "avg_launch_ms": avg_pair_ms,
                 "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock, measured peaks file)" % (
@@ -315,6 +319,199 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------- other workloads
+# Opt-in (--workload): the synthetic protein, the batched globules and the
+# learned warm start.  Paper parameters: eps_I = 1, eps_E = 80, kappa = 0.1257,
+# h = 0.5, band 2h, tau = h, probe 1.4.
+
+PROTEIN = {"workload": "protein_globule", "atoms": 2000, "probe": 1.4, "h": 0.5, "band_k": 2, "tau_k": 1.0,
+           "eps_in": 1.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64}
+
+
+def _line(args, workload, value, ms, extra):
+    line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": workload}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def _globule(n_atoms, seed, h=0.5, probe=1.4):
+    from paper_1709_08070_gb300 import ibim, inputs
+    z, r, q = inputs.globule_atoms(int(n_atoms), seed=int(seed))
+    return ibim.Context.molecule(z, r, q, probe=probe, h=h)
+
+
+def run_protein(args):
+    """2000-atom globule, level-set SES: timed FP32 operator applications and
+    one certified FP32 solve to 1e-6 (the FP64 solve at this size is not run)."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    W = PROTEIN
+    t0 = time.perf_counter()
+    ctx = _globule(W["atoms"], inputs.SEED_PROTEIN, W["h"], W["probe"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    N = ctx.N
+    P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * W["h"], 0)
+    variant, bps, _ = ctx.autotune(P)
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.matvec(P, x, y)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ctx.matvec(P, x, y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    value = N * N * len(ms) / (sum(ms) * 1e-3)
+    d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=2000, certify=1)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    cfg = dict(W, N=N, l2="256 MB buffer written between timed applications", step="one FP32 operator application",
+               f32_variant={"index": variant, "ctas_per_sm": bps})
+    _line(args, cfg, value, float(np.mean(ms)), {
+        "clocks": ck, "geometry_build_s": build_s,
+        "solve_f32_certified": {"s": solve_s, "iters": info["iters"], "relres_f64": info["relres"],
+                                "converged": info["converged"], "gpol_kcal": info["gpol_kcal"],
+                                "area": info["area"], "matvecs_f32": info["matvecs_f32"],
+                                "matvecs_f64": info["matvecs_f64"]}})
+    ctx.close()
+
+
+def run_batched(args):
+    """64 globules (atoms log-uniform in [50, 3000], kappa ~ U[0, 0.2]) solved
+    together by ibim_solve_batch; the timed step is a bounded number of
+    lock-step GMRES rounds (--batch-rounds), value = sum over molecules of
+    operator applications x N_m^2 / time."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    n_atoms, kappas = inputs.batch_sizes(args.batch_mols)
+    t0 = time.perf_counter()
+    ctxs = [_globule(n, inputs.SEED_BATCH + 1 + m) for m, n in enumerate(n_atoms)]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Ns = [c.N for c in ctxs]
+    physs = [ibim.Phys(1.0, 80.0, float(k), 0.5, 0) for k in kappas]
+    # autotune once per size bucket (cached for the other molecules)
+    order = np.argsort(Ns)[::-1]
+    seen = set()
+    for i in order:
+        b = int(np.log2(Ns[i]))
+        if b not in seen:
+            ctxs[i].autotune(physs[i])
+            seen.add(b)
+    outs = [torch.empty(2 * n, dtype=torch.float64, device="cuda") for n in Ns]
+    opts = dict(precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=args.batch_rounds, allow_not_converged=True)
+    for _ in range(max(1, args.warmup - 2)):
+        ibim.ibim_solve_batch(ctxs, physs, outs, **dict(opts, maxit=2))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    infos = ibim.ibim_solve_batch(ctxs, physs, outs, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    inter = sum((i["matvecs_f32"] + i["matvecs_f64"]) * n * n for i, n in zip(infos, Ns))
+    cfg = {"workload": "batched_globules", "molecules": len(Ns), "atoms_min": int(n_atoms.min()),
+           "atoms_max": int(n_atoms.max()), "N_total": int(sum(Ns)), "N_max": int(max(Ns)),
+           "sum_N2": float(sum(n * n for n in Ns)), "kappa_range": [0.0, 0.2], "h": 0.5, "eps_in": 1.0,
+           "eps_out": 80.0, "rounds_cap": args.batch_rounds, "tol": 1e-6, "restart": 64,
+           "step": "ibim_solve_batch capped at rounds_cap lock-step GMRES rounds"}
+    _line(args, cfg, inter / (ms * 1e-3), ms, {
+        "clocks": ck, "geometry_build_s": build_s,
+        "batch": {"converged": int(sum(i["converged"] for i in infos)), "iters_max": int(max(i["iters"] for i in infos)),
+                  "iters_median": float(np.median([i["iters"] for i in infos])),
+                  "interactions": float(inter)}})
+    for c in ctxs:
+        c.close()
+
+
+def run_learned(args):
+    """Learned warm start: train the network on solutions of small globules,
+    then solve held-out larger globules from the zero start and from the
+    network's prediction (both FP32, certified to 1e-6 in FP64)."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    rng = np.random.default_rng(inputs.SEED_LEARNED)
+    net = ibim.WarmStartNet(seed=1)
+    t0 = time.perf_counter()
+    train_atoms = rng.integers(args.learn_train_lo, args.learn_train_hi + 1, size=args.learn_train)
+    for m, n in enumerate(train_atoms):
+        ctx = _globule(n, inputs.SEED_LEARNED + 100 + m)
+        P = ibim.Phys(1.0, 80.0, float(rng.uniform(0.0, 0.2)), 0.5, 0)
+        d = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
+        info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=2000)
+        if info["converged"]:
+            net.add_example(ctx, P, d)
+        ctx.close()
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss0 = net.train(1, batch_nodes=8192, lr=1e-3)
+    loss = net.train(args.learn_steps, batch_nodes=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    tests = []
+    for m in range(args.learn_test):
+        ctx = _globule(args.learn_test_atoms, inputs.SEED_LEARNED + 10000 + m)
+        P = ibim.Phys(1.0, 80.0, 0.1257, 0.5, 0)
+        d0 = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
+        res = {"N": ctx.N}
+        for name, start in (("zero", 0), ("learned", 3)):
+            if start == 3:
+                net.predict(ctx, P, d0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            info = ctx.solve(P, d0, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=2000, start=start,
+                             certify=1)
+            torch.cuda.synchronize()
+            res[name] = {"s": time.perf_counter() - t1, "iters": info["iters"], "relres_f64": info["relres"],
+                         "gpol_kcal": info["gpol_kcal"], "converged": info["converged"]}
+        tests.append(res)
+        ctx.close()
+    net.close()
+    z_it = sum(t["zero"]["iters"] for t in tests)
+    l_it = sum(t["learned"]["iters"] for t in tests)
+    z_s = sum(t["zero"]["s"] for t in tests)
+    l_s = sum(t["learned"]["s"] for t in tests)
+    cfg = {"workload": "learned_warm_start", "train_globules": int(args.learn_train),
+           "train_atoms": [int(args.learn_train_lo), int(args.learn_train_hi)], "train_steps": int(args.learn_steps),
+           "test_globules": int(args.learn_test), "test_atoms": int(args.learn_test_atoms), "h": 0.5,
+           "eps_in": 1.0, "eps_out": 80.0, "tol": 1e-6,
+           "step": "certified FP32 solve of a held-out globule from the learned start"}
+    line = {"metric": "GMRES iterations to 1e-6 (learned start vs zero start)", "value": l_it / max(1, len(tests)),
+            "unit": "iterations per solve", "n_gpus": 1, "steps": len(tests), "warmup": 0,
+            "ms_per_step": 1e3 * l_s / max(1, len(tests)), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 weights, f32+f64 solve", "data": "synthetic", "config": cfg,
+            "zero_start_iters_per_solve": z_it / max(1, len(tests)),
+            "iters_saved_frac": (z_it - l_it) / max(1, z_it), "time_saved_frac": (z_s - l_s) / max(1e-9, z_s),
+            "train": {"examples_s": gen_s, "train_s": train_s, "loss_first": loss0, "loss_last": loss},
+            "tests": tests}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args):
     """Operator applications only (the workload's tuned FP32 pair kernel), for
     profiler captures: warm-up + steps matvecs, one short JSON line."""
@@ -361,6 +558,16 @@ def main():
                     help="operator applications only (for profiler captures); prints no bench line")
     ap.add_argument("--variant", type=int, default=None, help="with --profile: FP32 kernel variant (no autotune)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
+    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein", "batched", "learned"],
+                    help="kirkwood (default, the headline line) or an opt-in workload")
+    ap.add_argument("--batch-mols", type=int, default=64)
+    ap.add_argument("--batch-rounds", type=int, default=12)
+    ap.add_argument("--learn-train", type=int, default=48)
+    ap.add_argument("--learn-train-lo", type=int, default=100)
+    ap.add_argument("--learn-train-hi", type=int, default=400)
+    ap.add_argument("--learn-steps", type=int, default=3000)
+    ap.add_argument("--learn-test", type=int, default=2)
+    ap.add_argument("--learn-test-atoms", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -370,6 +577,12 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.workload == "protein":
+        run_protein(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -54,57 +54,61 @@ def sphere_cloud(n, radius=10.0, jitter=0.0, seed=0, weight_range=(0.01, 0.06)):
     return xs[key], u[key], w[key]
 
 
-def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, beta=3.0, n_cand=16,
+def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, beta=100.0, n_cand=128,
                   radius_range=(1.2, 1.9), charge_range=(-0.8, 0.8)):
     """Seeded self-avoiding random-walk chain compacted into a globule:
     bond length `step` A, non-bonded distances >= `min_dist` A.  Each new bead
     is drawn from `n_cand` random bond directions that keep the chain
     self-avoiding, with probability proportional to exp(-beta * (distance to the
     chain's centre of mass - the smallest such distance)), which packs the
-    chain towards its centre; a walk with no admissible candidate backs up 8
-    beads.  Radii uniform in `radius_range`; partial charges uniform in
+    chain towards its centre (at the default beta almost always the most
+    central admissible candidate); a walk with no admissible candidate backs
+    up 8 beads.  Radii uniform in `radius_range`; partial charges uniform in
     `charge_range` shifted to a net charge of zero.
     Returns (centres (n,3) about their mean, radii, charges)."""
     rng = np.random.default_rng(seed)
-    cell = min_dist
+    cell = step + min_dist  # every bead that can clash with a candidate is in a neighbouring cell
     pos = np.zeros((n_atoms, 3))
     grid = {}
 
     def key(p):
         return (int(np.floor(p[0] / cell)), int(np.floor(p[1] / cell)), int(np.floor(p[2] / cell)))
 
-    def ok(p, i):
+    def near(p, i):
         k = key(p)
+        out = []
         for dx in (-1, 0, 1):
             for dy in (-1, 0, 1):
                 for dz in (-1, 0, 1):
-                    for idx in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
-                        if idx == i - 1:
-                            continue
-                        d = pos[idx] - p
-                        if d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < min_dist * min_dist:
-                            return False
-        return True
+                    out.extend(grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()))
+        return [j for j in out if j != i - 1]
 
     grid.setdefault(key(pos[0]), []).append(0)
-    csum = np.zeros(3)
+    csum = pos[0].copy()
     i = 1
     while i < n_atoms:
         d = rng.standard_normal((n_cand, 3))
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         cand = pos[i - 1] + step * d
-        good = [j for j in range(n_cand) if ok(cand[j], i)]
-        if not good:
+        nb = near(pos[i - 1], i)
+        if nb:
+            diff = cand[:, None, :] - pos[nb][None, :, :]
+            good = np.nonzero(((diff * diff).sum(axis=2) >= min_dist * min_dist).all(axis=1))[0]
+        else:
+            good = np.arange(n_cand)
+        if good.size == 0:
             for _b in range(min(8, i - 1)):
                 i -= 1
                 grid[key(pos[i])].remove(i)
+                csum -= pos[i]
             continue
-        cen = pos[:i].mean(axis=0)
+        cen = csum / i
         dist = np.linalg.norm(cand[good] - cen, axis=1)
         wgt = np.exp(-beta * (dist - dist.min()))
-        j = good[rng.choice(len(good), p=wgt / wgt.sum())]
+        j = good[rng.choice(good.size, p=wgt / wgt.sum())]
         pos[i] = cand[j]
         grid.setdefault(key(cand[j]), []).append(i)
+        csum += cand[j]
         i += 1
     radii = rng.uniform(radius_range[0], radius_range[1], size=n_atoms)
     q = rng.uniform(charge_range[0], charge_range[1], size=n_atoms)
