@@ -447,9 +447,10 @@ def run_batched(args):
 
 
 def run_learned(args):
-    """Learned warm start: train the network on solutions of small globules,
-    then solve held-out larger globules from the zero start and from the
-    network's prediction (both FP32, certified to 1e-6 in FP64)."""
+    """Learned warm start: solutions of globules of learn_train_lo..hi atoms
+    (batched FP32 solves, 64 molecules per batch) train the network; held-out
+    globules of learn_test_atoms atoms are then solved from the zero start and
+    from the network's prediction (FP32 GMRES, FP64-certified to 1e-6)."""
     import torch
 
     from paper_1709_08070_gb300 import ibim, inputs
@@ -458,14 +459,20 @@ def run_learned(args):
     net = ibim.WarmStartNet(seed=1)
     t0 = time.perf_counter()
     train_atoms = rng.integers(args.learn_train_lo, args.learn_train_hi + 1, size=args.learn_train)
-    for m, n in enumerate(train_atoms):
-        ctx = _globule(n, inputs.SEED_LEARNED + 100 + m)
-        P = ibim.Phys(1.0, 80.0, float(rng.uniform(0.0, 0.2)), 0.5, 0)
-        d = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
-        info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=2000)
-        if info["converged"]:
-            net.add_example(ctx, P, d)
-        ctx.close()
+    train_kappa = rng.uniform(0.0, 0.2, size=args.learn_train)
+    n_examples = 0
+    for b0 in range(0, args.learn_train, 64):
+        idx = range(b0, min(args.learn_train, b0 + 64))
+        ctxs = [_globule(train_atoms[m], inputs.SEED_LEARNED + 100 + m) for m in idx]
+        physs = [ibim.Phys(1.0, 80.0, float(train_kappa[m]), 0.5, 0) for m in idx]
+        outs = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in ctxs]
+        infos = ibim.ibim_solve_batch(ctxs, physs, outs, precision=ibim.IBIM_F32C, tol=1e-6, restart=64,
+                                      maxit=3000, allow_not_converged=True)
+        for c, P, d, info in zip(ctxs, physs, outs, infos):
+            if info["converged"]:
+                net.add_example(c, P, d)
+                n_examples += 1
+            c.close()
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -477,18 +484,21 @@ def run_learned(args):
     for m in range(args.learn_test):
         ctx = _globule(args.learn_test_atoms, inputs.SEED_LEARNED + 10000 + m)
         P = ibim.Phys(1.0, 80.0, 0.1257, 0.5, 0)
+        ctx.autotune(P)
         d0 = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
         res = {"N": ctx.N}
         for name, start in (("zero", 0), ("learned", 3)):
-            if start == 3:
-                net.predict(ctx, P, d0)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            info = ctx.solve(P, d0, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=2000, start=start,
+            if start == 3:
+                net.predict(ctx, P, d0)
+            info = ctx.solve(P, d0, precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=3000, start=start,
                              certify=1)
             torch.cuda.synchronize()
             res[name] = {"s": time.perf_counter() - t1, "iters": info["iters"], "relres_f64": info["relres"],
-                         "gpol_kcal": info["gpol_kcal"], "converged": info["converged"]}
+                         "gpol_kcal": info["gpol_kcal"], "converged": info["converged"],
+                         "matvecs_f64": info["matvecs_f64"]}
+        res["gpol_rel_diff"] = abs(res["learned"]["gpol_kcal"] - res["zero"]["gpol_kcal"]) / abs(res["zero"]["gpol_kcal"])
         tests.append(res)
         ctx.close()
     net.close()
@@ -496,11 +506,11 @@ def run_learned(args):
     l_it = sum(t["learned"]["iters"] for t in tests)
     z_s = sum(t["zero"]["s"] for t in tests)
     l_s = sum(t["learned"]["s"] for t in tests)
-    cfg = {"workload": "learned_warm_start", "train_globules": int(args.learn_train),
+    cfg = {"workload": "learned_warm_start", "train_globules": int(args.learn_train), "train_examples": n_examples,
            "train_atoms": [int(args.learn_train_lo), int(args.learn_train_hi)], "train_steps": int(args.learn_steps),
            "test_globules": int(args.learn_test), "test_atoms": int(args.learn_test_atoms), "h": 0.5,
            "eps_in": 1.0, "eps_out": 80.0, "tol": 1e-6,
-           "step": "certified FP32 solve of a held-out globule from the learned start"}
+           "step": "certified FP32 solve of a held-out globule from the learned start (prediction included)"}
     line = {"metric": "GMRES iterations to 1e-6 (learned start vs zero start)", "value": l_it / max(1, len(tests)),
             "unit": "iterations per solve", "n_gpus": 1, "steps": len(tests), "warmup": 0,
             "ms_per_step": 1e3 * l_s / max(1, len(tests)), "higher_is_better": False, "scaling": "weak",
@@ -562,12 +572,12 @@ def main():
                     help="kirkwood (default, the headline line) or an opt-in workload")
     ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--batch-rounds", type=int, default=12)
-    ap.add_argument("--learn-train", type=int, default=48)
+    ap.add_argument("--learn-train", type=int, default=256)
     ap.add_argument("--learn-train-lo", type=int, default=100)
-    ap.add_argument("--learn-train-hi", type=int, default=400)
-    ap.add_argument("--learn-steps", type=int, default=3000)
+    ap.add_argument("--learn-train-hi", type=int, default=1000)
+    ap.add_argument("--learn-steps", type=int, default=4000)
     ap.add_argument("--learn-test", type=int, default=2)
-    ap.add_argument("--learn-test-atoms", type=int, default=1000)
+    ap.add_argument("--learn-test-atoms", type=int, default=10000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -519,18 +519,29 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         IBIM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * len, c->stream));
         converged = true;
     }
+    // Restart residuals use the iteration's operator; with certification the
+    // residual is recomputed with the FP64 operator once the iteration's
+    // residual meets the inner target (or the iteration budget is spent), and
+    // a failed check restarts from that FP64 residual (iterative refinement).
+    bool check = false;
     while (!converged) {
         const int kmax = std::min(m, o.maxit - iters);
+        const int prec_r = (check || kmax <= 0) ? prec_out : prec_in;
         if (!x_zero) {
-            if (prec_out == IBIM_F32C) info->matvecs_f32 += 1;
+            if (prec_r == IBIM_F32C) info->matvecs_f32 += 1;
             else info->matvecs_f64 += 1;
         }
-        IBIM_TRY(begin_cycle(c, k, prec_out, x_zero, inner_target, std::max(kmax, 0), &beta));
+        IBIM_TRY(begin_cycle(c, k, prec_r, x_zero, inner_target, std::max(kmax, 0), &beta));
         x_zero = false;
-        if (beta <= target_abs) {
+        if (prec_r == prec_out && beta <= target_abs) {
             converged = true;
             break;
         }
+        if (prec_r != prec_out && beta <= inner_target) {
+            check = true;
+            continue;
+        }
+        check = false;
         if (kmax <= 0) break;
         if (use_graph) IBIM_TRY(capture_step(c, k, prec_in));
         int steps = 0, conv = 0;
