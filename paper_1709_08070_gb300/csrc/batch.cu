@@ -29,8 +29,13 @@
 namespace ibim {
 
 constexpr int kMaxBatch = 1024;
+// One 512-thread CTA per SM, two targets per thread (the fastest
+// single-molecule variant): warps coupled through the stage ring finish
+// together.
+constexpr int kBThreads = 512;
 constexpr int kBTpt = 2;
-constexpr int kBTTile = kF32Threads * kBTpt;
+constexpr int kBTTile = kBThreads * kBTpt;
+static_assert(kBTTile <= kF32MaxTTile, "target tile");
 
 struct BatchMol {
     const float4* pos;
@@ -124,12 +129,12 @@ __global__ void batch_pack_kernel(const BatchMol* __restrict__ mols, const Batch
     }
 }
 
-__global__ void __launch_bounds__(kF32Threads)
+__global__ void __launch_bounds__(kBThreads, 1)
     batch_pair_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode,
                       unsigned* __restrict__ err)
 {
     constexpr int TPT = kBTpt;
-    constexpr int NW = kF32Threads / 32;
+    constexpr int NW = kBThreads / 32;
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
     __shared__ __align__(8) StagePipe pipe;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kF32Threads)
         idle = t * kBTTile + warp * 32 >= M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const int64_t i = gi0 + (int64_t)q * kBThreads;
             const float4 p4 = M->pos[i];
             const float4 n4 = M->nrm[i];
             T.x[q] = make_float3(p4.x, p4.y, p4.z);
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kF32Threads)
         }
         __syncwarp();
         if (lane < 2 * TPT) {
-            const int64_t blk0 = t * kBTTile + (int64_t)(lane >> 1) * kF32Threads + warp * 32;
+            const int64_t blk0 = t * kBTTile + (int64_t)(lane >> 1) * kBThreads + warp * 32;
             tfrm[warp][lane] = M->frames[2 * (blk0 / kChunk) + (lane & 1)];
         }
         __syncwarp();
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(kF32Threads)
         const int64_t N = M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = gi0 + (int64_t)q * kF32Threads;
+            const int64_t i = gi0 + (int64_t)q * kBThreads;
             if (i < N) {
                 atomicAdd(y + i, kInv4Pi * D1[q]);
                 atomicAdd(y + N + i, kInv4Pi * D2[q]);
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kF32Threads)
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
             tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, M->g64, gi0,
-                           kF32Threads, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
+                           kBThreads, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
@@ -307,7 +312,7 @@ static ibim_status batch_operator(ibim_ctx* c0, BatchRun& R, int mode)
 {
     batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, R.grid, R.d_plan);
     batch_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
-    batch_pair_kernel<<<R.grid, kF32Threads, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+    batch_pair_kernel<<<R.grid, kBThreads, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
     count_launch(c0, 3);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -383,7 +388,7 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
     IBIM_CUDA(cudaMalloc((void**)&R.d_want, sizeof(int) * nmol));
     IBIM_CUDA(cudaMemcpyAsync(R.d_mols, h.data(), sizeof(BatchMol) * nmol, cudaMemcpyHostToDevice, R.bs));
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_pair_kernel, kF32Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_pair_kernel, kBThreads, 0);
     if (occ < 1) occ = 1;
     R.grid = occ * sms;
     R.pack_blocks = (int)std::min<int64_t>(256, (maxN + 255) / 256);

@@ -165,7 +165,8 @@ def test_born_solve_fp32_certified(born, start):
     d32 = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     i32 = ctx.solve(P, d32, precision=F32, tol=1e-6, restart=64, maxit=300, start=start, certify=1)
     assert i32["converged"] and i32["relres"] < 1e-6
-    assert i32["matvecs_f64"] >= 1
+    # restarts use the FP32 operator; the FP64 operator only checks convergence
+    assert 1 <= i32["matvecs_f64"] <= 2, i32
     assert abs(i32["gpol"] - i64["gpol"]) / abs(i64["gpol"]) < 1e-4
     # the certified residual is the oracle's residual of the returned vector
     x = d32.cpu().numpy()
@@ -288,4 +289,33 @@ def test_every_fp32_variant_matches_fp64():
             torch.cuda.synchronize()
             r = _both_blocks(y32.cpu().numpy(), a, N)
             assert max(r) < 1e-6, (v, tpt, minb, nthr, bps, r)
+    ctx.close()
+
+
+def _block_radii(xs):
+    nb = len(xs) // 32
+    b = xs[:nb * 32].reshape(nb, 32, 3)
+    return np.sqrt(((b - b.mean(axis=1, keepdims=True)) ** 2).sum(axis=2).max(axis=1))
+
+
+def test_built_geometries_have_compact_32_node_blocks():
+    """Built geometries are reordered into compact aligned 32-node blocks (the
+    pair kernels' chunks): on the 80k sphere no block is wider than a few grid
+    cells and on a level-set globule nearly none is, while the node set is
+    unchanged."""
+    ctx = ibim.Context.sphere(KIRK["R"], h=KIRK["h"], band_eps=KIRK["k"] * KIRK["h"])
+    n = ctx.nodes()
+    r = _block_radii(n["xs"])
+    assert r.max() < 2.5, r.max()
+    ijk = n["ijk"].astype(np.int64)
+    assert len({tuple(v) for v in ijk}) == ctx.N  # a permutation of distinct grid nodes
+    ctx.close()
+    z, rad, q = inputs.globule_atoms(300, seed=11)
+    ctx = ibim.Context.molecule(z, rad, q, probe=1.4, h=0.5)
+    r = _block_radii(ctx.nodes()["xs"])
+    frac = float(np.mean(r > 3.0))
+    print("block radius: globule max %.2f median %.2f, %.1f %% above 3 A" % (r.max(), np.median(r), 100 * frac))
+    # a few blocks hold a small detached piece of surface together with nodes
+    # of its neighbourhood (leaves are cut by count); nearly all are compact
+    assert np.median(r) < 1.5 and frac < 0.03, (np.median(r), frac)
     ctx.close()
