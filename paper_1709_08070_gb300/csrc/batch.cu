@@ -29,11 +29,11 @@
 namespace ibim {
 
 constexpr int kMaxBatch = 1024;
-// One 512-thread CTA per SM, two targets per thread (the fastest
-// single-molecule variant): warps coupled through the stage ring finish
-// together.
+// One 512-thread CTA per SM (warps coupled through the stage ring finish
+// together), one target per thread: the per-molecule state of the batched
+// walk leaves no registers for a second target slot without spilling.
 constexpr int kBThreads = 512;
-constexpr int kBTpt = 2;
+constexpr int kBTpt = 1;
 constexpr int kBTTile = kBThreads * kBTpt;
 static_assert(kBTTile <= kF32MaxTTile, "target tile");
 
@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(kBThreads, 1)
     int64_t v = s0 - s_off[a];
     int64_t t = v / M->n_stiles;
     int64_t st = v % M->n_stiles;
-    F32Consts k = M->k;
     Targets<TPT> T;
     int64_t gi0 = 0;
     bool idle = false;
@@ -238,7 +237,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
 #pragma unroll
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
-            tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, M->g64, gi0,
+            tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, M->k, S1, C1, S2, C2, M->g64, gi0,
                            kBThreads, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
@@ -275,7 +274,6 @@ __global__ void __launch_bounds__(kBThreads, 1)
             } else {
                 ++a;
                 M = &mols[s_mol[a]];
-                k = M->k;
                 t = 0;
             }
             load_targets();

@@ -319,7 +319,7 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 Xy[q] = f2(X[q].y);
                 Xz[q] = f2(X[q].z);
             }
-#pragma unroll 4
+#pragma unroll 8
             for (int p = 0; p < kPairsPerChunk; ++p) {
                 const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
                 const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
