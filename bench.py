@@ -49,6 +49,34 @@ NCU_TRAFFIC_BYTES = {(2, 1, 512): 5.681664e6}
 METRIC = "IBIM matvec interactions/s"
 
 
+def reduce_over_ranks(ms, count, device):
+    """Whole-job timing of independent per-rank work: (max of the ranks' times,
+    sum of their counts); a plain pass-through without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(count)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
+def shard_molecules(costs, world_size, rank):
+    """Indices of the molecules rank `rank` solves: greedy longest-first
+    assignment of the costs (N_m^2) to the least loaded rank, ties to the lower
+    rank; every molecule goes to exactly one rank."""
+    load = [0.0] * world_size
+    mine = []
+    for m in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world_size), key=lambda q: (load[q], q))
+        load[r] += costs[m]
+        if r == rank:
+            mine.append(m)
+    return sorted(mine)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -223,17 +251,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tim = ctx.timing()
     ctx.timing_enable(False)
-    total_ms = float(sum(step_ms))
     interactions = sum(int(i["matvecs_f32"] + i["matvecs_f64"]) for i in infos) * N * N
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([float(interactions)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        interactions_all = float(c.item())
-    else:
-        interactions_all = float(interactions)
+    total_ms, interactions_all = reduce_over_ranks(float(sum(step_ms)), interactions, "cuda")
     value = interactions_all / (total_ms * 1e-3)
 
     # ---- dominant kernel roofline (pair_f32_kernel), live CUDA-event timing
@@ -396,54 +415,67 @@ def run_batched(args):
     """64 globules (atoms log-uniform in [50, 3000], kappa ~ U[0, 0.2]) solved
     together by ibim_solve_batch; the timed step is a bounded number of
     lock-step GMRES rounds (--batch-rounds), value = sum over molecules of
-    operator applications x N_m^2 / time."""
+    operator applications x N_m^2 / time.  Under torchrun the molecules are
+    independent problems: each rank solves its cost-balanced share (no
+    collective on the data path), value = all ranks' interactions / the
+    slowest rank's time."""
     import torch
+    import torch.distributed as dist
 
     from paper_1709_08070_gb300 import ibim, inputs
 
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
     n_atoms, kappas = inputs.batch_sizes(args.batch_mols)
+    mine = shard_molecules([float(a) ** (4.0 / 3.0) for a in n_atoms], ws, rank)  # N^2 ~ atoms^(4/3)
     t0 = time.perf_counter()
-    ctxs = [_globule(n, inputs.SEED_BATCH + 1 + m) for m, n in enumerate(n_atoms)]
+    ctxs = [_globule(n_atoms[m], inputs.SEED_BATCH + 1 + m) for m in mine]
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     Ns = [c.N for c in ctxs]
-    physs = [ibim.Phys(1.0, 80.0, float(k), 0.5, 0) for k in kappas]
-    # autotune once per size bucket (cached for the other molecules)
-    order = np.argsort(Ns)[::-1]
-    seen = set()
-    for i in order:
-        b = int(np.log2(Ns[i]))
-        if b not in seen:
-            ctxs[i].autotune(physs[i])
-            seen.add(b)
+    physs = [ibim.Phys(1.0, 80.0, float(kappas[m]), 0.5, 0) for m in mine]
     outs = [torch.empty(2 * n, dtype=torch.float64, device="cuda") for n in Ns]
     opts = dict(precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=args.batch_rounds, allow_not_converged=True)
     for _ in range(max(1, args.warmup - 2)):
         ibim.ibim_solve_batch(ctxs, physs, outs, **dict(opts, maxit=2))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(0)
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     e0.record(stream)
     infos = ibim.ibim_solve_batch(ctxs, physs, outs, **opts)
     e1.record(stream)
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
     inter = sum((i["matvecs_f32"] + i["matvecs_f64"]) * n * n for i, n in zip(infos, Ns))
-    cfg = {"workload": "batched_globules", "molecules": len(Ns), "atoms_min": int(n_atoms.min()),
-           "atoms_max": int(n_atoms.max()), "N_total": int(sum(Ns)), "N_max": int(max(Ns)),
-           "sum_N2": float(sum(n * n for n in Ns)), "kappa_range": [0.0, 0.2], "h": 0.5, "eps_in": 1.0,
-           "eps_out": 80.0, "rounds_cap": args.batch_rounds, "tol": 1e-6, "restart": 64,
-           "step": "ibim_solve_batch capped at rounds_cap lock-step GMRES rounds"}
-    _line(args, cfg, inter / (ms * 1e-3), ms, {
-        "clocks": ck, "geometry_build_s": build_s,
-        "batch": {"converged": int(sum(i["converged"] for i in infos)), "iters_max": int(max(i["iters"] for i in infos)),
-                  "iters_median": float(np.median([i["iters"] for i in infos])),
-                  "interactions": float(inter)}})
+    ms, inter_all = reduce_over_ranks(e0.elapsed_time(e1), inter, "cuda")
+    if rank == 0:
+        cfg = {"workload": "batched_globules", "molecules": int(args.batch_mols),
+               "molecules_rank0": len(Ns), "atoms_min": int(n_atoms.min()), "atoms_max": int(n_atoms.max()),
+               "N_total_rank0": int(sum(Ns)), "N_max_rank0": int(max(Ns)),
+               "sum_N2_rank0": float(sum(n * n for n in Ns)), "kappa_range": [0.0, 0.2], "h": 0.5,
+               "eps_in": 1.0, "eps_out": 80.0, "rounds_cap": args.batch_rounds, "tol": 1e-6, "restart": 64,
+               "parallelism": "molecules sharded over %d ranks" % ws if ws > 1 else "single",
+               "step": "ibim_solve_batch capped at rounds_cap lock-step GMRES rounds"}
+        line_args = argparse.Namespace(steps=1, warmup=args.warmup)
+        _line(line_args, cfg, inter_all / (ms * 1e-3), ms, {
+            "n_gpus": ws, "scaling": "strong", "clocks": ck, "geometry_build_s_rank0": build_s,
+            "batch_rank0": {"converged": int(sum(i["converged"] for i in infos)),
+                            "iters_max": int(max(i["iters"] for i in infos)),
+                            "iters_median": float(np.median([i["iters"] for i in infos])),
+                            "interactions": float(inter)},
+            "interactions_all_ranks": inter_all})
     for c in ctxs:
         c.close()
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def run_learned(args):
