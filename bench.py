@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this
 # workload, by variant (targets/thread, min CTAs/SM, threads/CTA), from the ncu
 # full-set capture summarised in profiles/pair_f32_kernel_kirkwood80k.md.
-NCU_TRAFFIC_BYTES = {(2, 1, 512): 5.681664e6}
+NCU_TRAFFIC_BYTES = {(2, 1, 512): 5.686272e6}
 METRIC = "IBIM matvec interactions/s"
 
 
@@ -400,14 +400,24 @@ def run_protein(args):
     info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=2000, certify=1)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t0
+    extra = {"clocks": ck, "geometry_build_s": build_s,
+             "solve_f32_certified": {"s": solve_s, "iters": info["iters"], "relres_f64": info["relres"],
+                                     "converged": info["converged"], "gpol_kcal": info["gpol_kcal"],
+                                     "area": info["area"], "matvecs_f32": info["matvecs_f32"],
+                                     "matvecs_f64": info["matvecs_f64"]}}
+    if args.protein_fp64:
+        d64 = torch.empty_like(d)
+        t0 = time.perf_counter()
+        i64 = ctx.solve(P, d64, precision=ibim.IBIM_F64, tol=W["tol"], restart=W["restart"], maxit=2000)
+        torch.cuda.synchronize()
+        s64 = time.perf_counter() - t0
+        extra["solve_f64_plain"] = {"s": s64, "iters": i64["iters"], "relres": i64["relres"],
+                                    "converged": i64["converged"], "gpol_kcal": i64["gpol_kcal"]}
+        extra["speedup_certified_vs_f64"] = s64 / solve_s
+        extra["gpol_rel_diff_f32_vs_f64"] = abs(info["gpol_kcal"] - i64["gpol_kcal"]) / abs(i64["gpol_kcal"])
     cfg = dict(W, N=N, l2="256 MB buffer written between timed applications", step="one FP32 operator application",
                f32_variant={"index": variant, "ctas_per_sm": bps})
-    _line(args, cfg, value, float(np.mean(ms)), {
-        "clocks": ck, "geometry_build_s": build_s,
-        "solve_f32_certified": {"s": solve_s, "iters": info["iters"], "relres_f64": info["relres"],
-                                "converged": info["converged"], "gpol_kcal": info["gpol_kcal"],
-                                "area": info["area"], "matvecs_f32": info["matvecs_f32"],
-                                "matvecs_f64": info["matvecs_f64"]}})
+    _line(args, cfg, value, float(np.mean(ms)), extra)
     ctx.close()
 
 
@@ -447,9 +457,11 @@ def run_batched(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("ibim_timed_steps")
     e0.record(stream)
     infos = ibim.ibim_solve_batch(ctxs, physs, outs, **opts)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -602,6 +614,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
     ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein", "batched", "learned"],
                     help="kirkwood (default, the headline line) or an opt-in workload")
+    ap.add_argument("--protein-fp64", action="store_true",
+                    help="with --workload protein: also time the plain FP64 GPU solve (about ten minutes)")
     ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--batch-rounds", type=int, default=12)
     ap.add_argument("--learn-train", type=int, default=256)
