@@ -621,7 +621,7 @@ def main():
     ap.add_argument("--learn-train", type=int, default=256)
     ap.add_argument("--learn-train-lo", type=int, default=100)
     ap.add_argument("--learn-train-hi", type=int, default=1000)
-    ap.add_argument("--learn-steps", type=int, default=4000)
+    ap.add_argument("--learn-steps", type=int, default=20000)
     ap.add_argument("--learn-test", type=int, default=2)
     ap.add_argument("--learn-test-atoms", type=int, default=10000)
     args = ap.parse_args()

@@ -224,21 +224,26 @@ ibim_status ibim_solve_host(ibim_ctx* ctx, const ibim_phys* phys, const ibim_sol
  * of the paper's method, whose reference start is zero or Lambda^-1 g of
  * Sec. 3.3).  Features of node i: with S1, S2 the weighted RMS of g1, g2 and
  * L = S1/S2, (g1/S1, g2/S2, d/eps, clamp(H L,-10,10)/10, kappa L/(1+kappa L),
- * ln(eps_E/eps_I)/5, (eps_I/eps_E)/(1+kappa L), 0), H from
- * ibim_get_curvature.  Network 8 -> 64 -> 64 -> 2 (tanh), BF16 weights with
- * FP32 arithmetic; output psi = S1 o0, psin = S2 o1.  Trained on solutions
- * the method computed (ibim_wsnet_add_example) by Adam on sampled nodes with
- * loss sum (w_i/mean w) |o - t|^2 / batch, t = (psi/S1, psin/S2).
- * Parameters (IBIM_WS_NPARAMS floats, FP32 master copy): W1[64][8], b1[64],
+ * ln(eps_E/eps_I)/5, (eps_I/eps_E)/(1+kappa L), r1/S1, r2/S2), H from
+ * ibim_get_curvature, r = g - A Lambda^-1 g the residual of the Lambda^-1 g
+ * start (one application of the FP32 operator, so features and prediction
+ * cost one operator application each).  Network 9 -> 64 -> 64 -> 2 (tanh),
+ * BF16 weights with
+ * FP32 arithmetic; output psi = S1 o0 / lambda1, psin = S2 o1 / lambda2
+ * (Lambda = diag(lambda1, lambda2) of Sec. 3.3).  Trained on solutions the
+ * method computed (ibim_wsnet_add_example) by Adam on sampled nodes with loss
+ * sum (w_i/mean w) |o - t|^2 / batch, t = (lambda1 psi/S1, lambda2 psin/S2),
+ * which weights each block by its share of the initial residual.
+ * Parameters (IBIM_WS_NPARAMS floats, FP32 master copy): W1[64][9], b1[64],
  * W2[64][64], b2[64], W3[2][64], b3[2].  Use: ibim_wsnet_predict into a
  * device vector, then ibim_solve with start = 3.
  */
-#define IBIM_WS_NPARAMS 4866
+#define IBIM_WS_NPARAMS 4930
 typedef struct ibim_wsnet ibim_wsnet;
 ibim_status ibim_wsnet_create(uint64_t seed, void* stream, ibim_wsnet** out);
 ibim_status ibim_wsnet_get_params(const ibim_wsnet* net, float* h_params);
 ibim_status ibim_wsnet_set_params(ibim_wsnet* net, const float* h_params);  /* resets Adam */
-/* features (host N x 8 floats, may be NULL) and scales (host S1, S2, mean w; may be NULL) */
+/* features (host N x 9 floats, may be NULL) and scales (host S1, S2, mean w; may be NULL) */
 ibim_status ibim_wsnet_features(ibim_wsnet* net, ibim_ctx* ctx, const ibim_phys* phys, float* h_feat,
                                 double* h_scales);
 /* appends every node of ctx with the solution d_p (device 2N) as training examples */

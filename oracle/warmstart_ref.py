@@ -1,14 +1,14 @@
 """FP64 numpy reference of the learned warm start (test infrastructure only).
 
 Written independently of the CUDA library from the definition of the
-features and of the network (8 -> 64 -> 64 -> 2, tanh, BF16 weights) so that
+features and of the network (9 -> 64 -> 64 -> 2, tanh, BF16 weights) so that
 the GPU features, loss and gradient can be checked against it.
 """
 import numpy as np
 
-__all__ = ["NPARAMS", "bf16_round", "unpack", "features", "targets", "loss_and_grad", "forward"]
+__all__ = ["IN", "NPARAMS", "bf16_round", "unpack", "features", "targets", "loss_and_grad", "forward"]
 
-IN, H, OUT = 8, 64, 2
+IN, H, OUT = 9, 64, 2
 NPARAMS = H * IN + H + H * H + H + OUT * H + OUT
 
 
@@ -40,8 +40,10 @@ def _scales(g, w):
     return S1, S2, sw / N
 
 
-def features(g, w, dist, curv, band_eps, eps_in, eps_out, kappa):
-    """Per-node features (N x 8) and (S1, S2, mean w)."""
+def features(g, w, dist, curv, band_eps, eps_in, eps_out, kappa, Ax0):
+    """Per-node features (N x 9) and (S1, S2, mean w).  Ax0: the operator
+    applied to x0 = Lambda^-1 g (2N), so that r = g - Ax0 is the residual of
+    that start."""
     N = w.size
     S1, S2, mw = _scales(g, w)
     L = S1 / S2
@@ -54,13 +56,19 @@ def features(g, w, dist, curv, band_eps, eps_in, eps_out, kappa):
     F[:, 4] = kL / (1.0 + kL)
     F[:, 5] = np.log(eps_out / eps_in) / 5.0
     F[:, 6] = (eps_in / eps_out) / (1.0 + kL)
+    F[:, 7] = (g[:N] - Ax0[:N]) / S1
+    F[:, 8] = (g[N:] - Ax0[N:]) / S2
     return F, (S1, S2, mw)
 
 
-def targets(p, w, scales):
+def targets(p, w, scales, eps_in, eps_out):
+    """Training targets (lambda1 psi/S1, lambda2 psin/S2), Lambda the diagonal of
+    the system (Sec. 3.3), and the loss weights w/mean(w)."""
     N = w.size
     S1, S2, mw = scales
-    return np.stack([p[:N] / S1, p[N:] / S2], axis=1), w / mw
+    lam1 = 0.5 * (1.0 + eps_out / eps_in)
+    lam2 = 0.5 * (1.0 + eps_in / eps_out)
+    return np.stack([lam1 * p[:N] / S1, lam2 * p[N:] / S2], axis=1), w / mw
 
 
 def forward(params_bf16, F):

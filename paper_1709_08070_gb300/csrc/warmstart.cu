@@ -8,12 +8,20 @@
 //   L = S1/S2 (a length), f0 = g1/S1, f1 = g2/S2, f2 = d/eps (offset in the
 //   band), f3 = clamp(H L, -10, 10)/10 (H = Laplacian of the distance),
 //   f4 = kappa L/(1 + kappa L), f5 = ln(eps_E/eps_I)/5,
-//   f6 = (eps_I/eps_E)/(1 + kappa L), f7 = 0.
-// Network: 8 -> 64 -> 64 -> 2, tanh hidden layers; BF16 weights, FP32
+//   f6 = (eps_I/eps_E)/(1 + kappa L), f7 = r1/S1, f8 = r2/S2 with
+//   r = g - A Lambda^-1 g = -K Lambda^-1 g, the residual of the Lambda^-1 g
+//   start (one application of the FP32 operator): the only non-local input,
+//   it carries the reaction field of the first Neumann step to every node.
+// Network: 9 -> 64 -> 64 -> 2, tanh hidden layers; BF16 weights, FP32
 // arithmetic and accumulation; FP32 master weights and Adam moments.
-// Outputs: psi_i = S1 o0, psin_i = S2 o1.
+// Outputs: psi_i = S1 o0 / lambda1, psin_i = S2 o1 / lambda2 (Lambda the
+// diagonal of the system, Sec. 3.3).
 // Training loss: sum over sampled nodes of (w_i / mean w) |o - t|^2 / batch,
-// t = (psi/S1, psin/S2) of solutions the method computed.
+// t = (lambda1 psi/S1, lambda2 psin/S2) of solutions the method computed.
+// Scaling the targets by Lambda weights the two blocks by their share of
+// the initial residual g - A p0 (A = Lambda + K), which is what GMRES sees:
+// unscaled, the psi block (lambda1 = (1 + eps_E/eps_I)/2, 40.5 for
+// water/protein) would be under-weighted by lambda1^2.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -24,14 +32,14 @@
 
 namespace ibim {
 
-constexpr int kWsIn = 8, kWsH = 64, kWsOut = 2;
+constexpr int kWsIn = 9, kWsH = 64, kWsOut = 2;
 constexpr int kOffW1 = 0;
 constexpr int kOffB1 = kOffW1 + kWsH * kWsIn;
 constexpr int kOffW2 = kOffB1 + kWsH;
 constexpr int kOffB2 = kOffW2 + kWsH * kWsH;
 constexpr int kOffW3 = kOffB2 + kWsH;
 constexpr int kOffB3 = kOffW3 + kWsOut * kWsH;
-constexpr int kWsParams = kOffB3 + kWsOut;  // 4866
+constexpr int kWsParams = kOffB3 + kWsOut;  // 4930
 constexpr int kWsThreads = 128;             // nodes per training block
 constexpr int kHPad = kWsH + 1;             // padded smem row (bank conflicts)
 
@@ -94,9 +102,9 @@ struct WsPhys {
     double kappa, eps_ratio_log, inv_ratio, band_eps;
 };
 
-__global__ void ws_features_kernel(const double* __restrict__ g, const double* __restrict__ dist,
-                                   const double* __restrict__ curv, int64_t N, const double* __restrict__ scal,
-                                   WsPhys ph, float* __restrict__ feat)
+__global__ void ws_features_kernel(const double* __restrict__ g, const double* __restrict__ Ax0,
+                                   const double* __restrict__ dist, const double* __restrict__ curv, int64_t N,
+                                   const double* __restrict__ scal, WsPhys ph, float* __restrict__ feat)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -113,16 +121,28 @@ __global__ void ws_features_kernel(const double* __restrict__ g, const double* _
     f[4] = (float)(kL / (1.0 + kL));
     f[5] = (float)(ph.eps_ratio_log / 5.0);
     f[6] = (float)(ph.inv_ratio / (1.0 + kL));
-    f[7] = 0.0f;
+    f[7] = (float)((g[i] - Ax0[i]) / S1);
+    f[8] = (float)((g[N + i] - Ax0[N + i]) / S2);
 }
 
-__global__ void ws_targets_kernel(const double* __restrict__ p, const double* __restrict__ w, int64_t N,
-                                  const double* __restrict__ scal, float* __restrict__ tgt, float* __restrict__ wt)
+// x0 = Lambda^-1 g (the start of Sec. 3.3).
+__global__ void ws_start_kernel(const double* __restrict__ g, int64_t N, double lambda1, double lambda2,
+                                double* __restrict__ x0)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    tgt[2 * i] = (float)(p[i] / scal[0]);
-    tgt[2 * i + 1] = (float)(p[N + i] / scal[1]);
+    x0[i] = g[i] / lambda1;
+    x0[N + i] = g[N + i] / lambda2;
+}
+
+__global__ void ws_targets_kernel(const double* __restrict__ p, const double* __restrict__ w, int64_t N,
+                                  const double* __restrict__ scal, double lambda1, double lambda2,
+                                  float* __restrict__ tgt, float* __restrict__ wt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    tgt[2 * i] = (float)(lambda1 * p[i] / scal[0]);
+    tgt[2 * i + 1] = (float)(lambda2 * p[N + i] / scal[1]);
     wt[i] = (float)(w[i] / scal[2]);
 }
 
@@ -156,7 +176,7 @@ __device__ __forceinline__ void ws_forward(const float* sp, const float* x, floa
 
 __global__ void __launch_bounds__(kWsThreads)
     ws_predict_kernel(const float* __restrict__ feat, int64_t N, const __nv_bfloat16* __restrict__ wb,
-                      const double* __restrict__ scal, double* __restrict__ p0)
+                      const double* __restrict__ scal, double lambda1, double lambda2, double* __restrict__ p0)
 {
     extern __shared__ float smem[];
     float* sp = smem;
@@ -172,8 +192,8 @@ __global__ void __launch_bounds__(kWsThreads)
     float* h2 = h1 + kHPad;
     float o[kWsOut];
     ws_forward(sp, x, h1, h2, o);
-    p0[i] = scal[0] * (double)o[0];
-    p0[N + i] = scal[1] * (double)o[1];
+    p0[i] = scal[0] * (double)o[0] / lambda1;
+    p0[N + i] = scal[1] * (double)o[1] / lambda2;
 }
 
 // splitmix64 (Steele, Lea, Flood 2014) for minibatch sampling.
@@ -310,19 +330,27 @@ static size_t predict_smem() { return sizeof(float) * (kWsParams + kWsThreads * 
 static ibim_status ws_prepare(ibim_wsnet* net, ibim_ctx* c, const ibim_phys& p, float** feat_out)
 {
     const int64_t N = c->N;
-    // d_io: 2N doubles RHS, then N x 8 floats features
-    IBIM_TRY(ensure(c, (void**)&c->d_io, &c->io_bytes, sizeof(double) * 2 * N + sizeof(float) * kWsIn * N + 64));
+    // d_io: 2N doubles RHS g, 2N doubles x0 = Lambda^-1 g, 2N doubles A x0,
+    // then N x kWsIn floats features
+    IBIM_TRY(ensure(c, (void**)&c->d_io, &c->io_bytes, sizeof(double) * 6 * N + sizeof(float) * kWsIn * N + 64));
     double* g = c->d_io;
-    float* feat = (float*)(c->d_io + 2 * N);
+    double* x0 = c->d_io + 2 * N;
+    double* ax0 = c->d_io + 4 * N;
+    float* feat = (float*)(c->d_io + 6 * N);
     IBIM_TRY(rhs_launch(c, p.eps_in, g));
+    const PairConsts k = make_consts(p);
+    ws_start_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(g, N, k.lambda1, k.lambda2, x0);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_TRY(apply_operator(c, k, IBIM_F32C, VecRef{x0, nullptr, 0, 0}, OutRef{ax0, nullptr, 0, 0}, nullptr));
     ws_scales_kernel<<<1, 256, 0, c->stream>>>(g, c->d_geo64 + 6 * N, N, net->d_scal);
     WsPhys ph;
     ph.kappa = p.kappa;
     ph.eps_ratio_log = log(p.eps_out / p.eps_in);
     ph.inv_ratio = p.eps_in / p.eps_out;
     ph.band_eps = c->band_eps;
-    ws_features_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(g, c->d_dist, c->d_curv, N, net->d_scal,
-                                                                          ph, feat);
+    ws_features_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(g, ax0, c->d_dist, c->d_curv, N,
+                                                                          net->d_scal, ph, feat);
     count_launch(c, 2);
     IBIM_CUDA(cudaGetLastError());
     *feat_out = feat;
@@ -501,8 +529,9 @@ ibim_status ibim_wsnet_add_example(ibim_wsnet* n, ibim_ctx* c, const ibim_phys* 
     IBIM_TRY(ws_prepare(n, c, *p, &feat));
     IBIM_CUDA(cudaMemcpyAsync(n->d_feat + kWsIn * n->n_ex, feat, sizeof(float) * kWsIn * N, cudaMemcpyDeviceToDevice,
                               c->stream));
+    const PairConsts k = make_consts(*p);
     ws_targets_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(
-        d_p, c->d_geo64 + 6 * N, N, n->d_scal, n->d_tgt + kWsOut * n->n_ex, n->d_wt + n->n_ex);
+        d_p, c->d_geo64 + 6 * N, N, n->d_scal, k.lambda1, k.lambda2, n->d_tgt + kWsOut * n->n_ex, n->d_wt + n->n_ex);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_CUDA(cudaStreamSynchronize(c->stream));
@@ -591,7 +620,9 @@ ibim_status ibim_wsnet_predict(ibim_wsnet* n, ibim_ctx* c, const ibim_phys* p, d
     float* feat = nullptr;
     IBIM_TRY(ws_prepare(n, c, *p, &feat));
     const unsigned blocks = (unsigned)((c->N + kWsThreads - 1) / kWsThreads);
-    ws_predict_kernel<<<blocks, kWsThreads, predict_smem(), c->stream>>>(feat, c->N, n->d_wb, n->d_scal, d_p0);
+    const PairConsts k = make_consts(*p);
+    ws_predict_kernel<<<blocks, kWsThreads, predict_smem(), c->stream>>>(feat, c->N, n->d_wb, n->d_scal, k.lambda1,
+                                                                         k.lambda2, d_p0);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_CUDA(cudaStreamSynchronize(c->stream));

@@ -26,7 +26,8 @@ __all__ = [
 IBIM_F64 = 64
 IBIM_F32C = 32
 IBIM_NOALLOC_MAX_NODES = 131072
-IBIM_WS_NPARAMS = 4866
+IBIM_WS_NPARAMS = 4930
+IBIM_WS_NFEATURES = 9
 KCAL_PER_E2_A = 4.0 * np.pi * 332.0637
 
 _STATUS = {0: "IBIM_OK", 1: "IBIM_ERR_ARG", 2: "IBIM_ERR_EMPTY_BAND", 3: "IBIM_ERR_NONFINITE",
@@ -391,7 +392,7 @@ class WarmStartNet:
 
     def features(self, ctx, phys):
         N = ibim_num_nodes(_h(ctx))
-        f = np.empty((N, 8), dtype=np.float32)
+        f = np.empty((N, IBIM_WS_NFEATURES), dtype=np.float32)
         sc = np.empty(3)
         p = _phys(phys)
         _check(lib().ibim_wsnet_features(self.handle, _h(ctx), ctypes.byref(p),

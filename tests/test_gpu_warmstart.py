@@ -31,6 +31,15 @@ def _setup(seed=5):
     return ctx, g, z, q, perm, R, h
 
 
+def _ax0(g, go, eps_in, eps_out, kappa, tau):
+    """Oracle operator applied to the Lambda^-1 g start."""
+    N = g["w"].size
+    lam1 = 0.5 * (1.0 + eps_out / eps_in)
+    lam2 = 0.5 * (1.0 + eps_in / eps_out)
+    x0 = np.concatenate([go[:N] / lam1, go[N:] / lam2])
+    return oracle.matvec(g["xs"], g["nrm"], g["w"], oracle.Phys(eps_in, eps_out, kappa, tau, 0), x0)
+
+
 def test_features_match_reference():
     ctx, g, z, q, perm, R, h = _setup()
     for kappa in (0.0, 0.1257):
@@ -38,7 +47,8 @@ def test_features_match_reference():
         net = ibim.WarmStartNet(seed=1)
         f, sc = net.features(ctx, P)
         go = oracle.rhs(g["xs"], g["nrm"], z, q, 2.0)
-        Fo, (S1, S2, mw) = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, kappa)
+        ax0 = _ax0(g, go, 2.0, 80.0, kappa, h)
+        Fo, (S1, S2, mw) = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, kappa, ax0)
         assert sc[0] == pytest.approx(S1, rel=1e-10) and sc[1] == pytest.approx(S2, rel=1e-10)
         np.testing.assert_allclose(f, Fo[perm], rtol=2e-6, atol=2e-6)
         net.close()
@@ -58,8 +68,9 @@ def test_gradient_matches_reference():
     assert net.num_examples() == N
     loss_g, grad_g = net.gradient(0, N)
     go = oracle.rhs(g["xs"], g["nrm"], z, q, 2.0)
-    Fo, sc = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, 0.1257)
-    To, wto = ws.targets(p_orc, g["w"], sc)
+    ax0 = _ax0(g, go, 2.0, 80.0, 0.1257, h)
+    Fo, sc = ws.features(go, g["w"], g["d"], g["curv"], 2 * h, 2.0, 80.0, 0.1257, ax0)
+    To, wto = ws.targets(p_orc, g["w"], sc, 2.0, 80.0)
     loss_o, grad_o = ws.loss_and_grad(ws.bf16_round(params), Fo, To, wto)
     assert loss_g == pytest.approx(loss_o, rel=1e-4)
     err = np.linalg.norm(grad_g - grad_o) / np.linalg.norm(grad_o)

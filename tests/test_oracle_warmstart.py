@@ -23,7 +23,7 @@ def test_bf16_rounding_ties_to_even():
 def test_reference_gradient_matches_finite_differences():
     rng = np.random.default_rng(3)
     p = rng.standard_normal(ws.NPARAMS) * 0.3
-    F = rng.standard_normal((40, 8))
+    F = rng.standard_normal((40, ws.IN))
     T = rng.standard_normal((40, 2))
     wt = rng.uniform(0.5, 1.5, 40)
     loss, g = ws.loss_and_grad(p, F, T, wt)
