@@ -317,7 +317,10 @@ ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, const double* 
  * Arnoldi step per round; the operator applications of a round run as ONE
  * persistent FP32 pair-sum launch over a device-built list of the active
  * molecules' (target tile, source tile) steps, and a round is one CUDA graph
- * replay.  Molecules drop out of the list as they converge.
+ * replay.  Molecules drop out of the list as they converge.  The first
+ * batched solve of a size class (device, floor(log2 sum N_m^2)) in the process
+ * times each compiled variant of the batched pair kernel (target tiles of
+ * 512, 256 and 128 nodes) on its first round and keeps the fastest.
  *   nmol in [1, 1024]; phys: nmol entries (kappa etc. per molecule); opts must
  *   ask for IBIM_F32C, start 0, certify 0; d_p: nmol device pointers, 2 N_m
  *   doubles each (solutions out); infos: nmol entries.

@@ -20,7 +20,11 @@
 // time on the molecules still iterating.
 #include <string.h>
 
+#include <math.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "gmres_internal.cuh"
@@ -29,13 +33,11 @@
 namespace ibim {
 
 constexpr int kMaxBatch = 1024;
-// One 512-thread CTA per SM (warps coupled through the stage ring finish
-// together), one target per thread: the per-molecule state of the batched
-// walk leaves no registers for a second target slot without spilling.
-constexpr int kBThreads = 512;
-constexpr int kBTpt = 1;
-constexpr int kBTTile = kBThreads * kBTpt;
-static_assert(kBTTile <= kF32MaxTTile, "target tile");
+// Batched pair-kernel variants (targets per thread x CTA size x minimum CTAs
+// per SM, i.e. target tiles of 512, 256 or 128 nodes; one target per thread,
+// because the per-molecule state of the batched walk leaves no registers for
+// a second slot without spilling).  The first batched solve of a size class
+// times each one on its first round and keeps the fastest (see batch_solve).
 
 struct BatchMol {
     const float4* pos;
@@ -47,7 +49,7 @@ struct BatchMol {
     double* x;
     double* t;
     GmState* st;
-    int64_t N, n_ttiles, n_stiles;
+    int64_t N, n_stiles;
     int64_t sperm;  // source-tile visiting stride (see make_schedule)
     F32Consts k;
     double lambda1, lambda2;
@@ -75,6 +77,7 @@ __device__ __forceinline__ double* batch_out(const BatchMol& M, int mode)
 }
 
 __global__ void batch_plan_kernel(const BatchMol* __restrict__ mols, int nmol, int mode, const int* __restrict__ want,
+                                  int64_t ttile,
                                   int grid, BatchPlan* __restrict__ plan)
 {
     if (threadIdx.x != 0) return;
@@ -85,7 +88,7 @@ __global__ void batch_plan_kernel(const BatchMol* __restrict__ mols, int nmol, i
         if (!active) continue;
         plan->mol[a] = m;
         plan->off[a] = total;
-        total += mols[m].n_ttiles * mols[m].n_stiles;
+        total += (mols[m].N + ttile - 1) / ttile * mols[m].n_stiles;
         ++a;
     }
     plan->off[a] = total;
@@ -129,12 +132,14 @@ __global__ void batch_pack_kernel(const BatchMol* __restrict__ mols, const Batch
     }
 }
 
-__global__ void __launch_bounds__(kBThreads, 1)
+template <int TPT, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     batch_pair_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode,
                       unsigned* __restrict__ err)
 {
-    constexpr int TPT = kBTpt;
-    constexpr int NW = kBThreads / 32;
+    constexpr int TTILE = TPT * THREADS;
+    constexpr int NW = THREADS / 32;
+    static_assert(TTILE <= kF32MaxTTile, "target tile");
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
     __shared__ __align__(8) StagePipe pipe;
@@ -191,11 +196,11 @@ __global__ void __launch_bounds__(kBThreads, 1)
     double D1[TPT], D2[TPT];
 
     auto load_targets = [&]() {
-        gi0 = t * kBTTile + tid;
-        idle = t * kBTTile + warp * 32 >= M->N;
+        gi0 = t * TTILE + tid;
+        idle = t * TTILE + warp * 32 >= M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = gi0 + (int64_t)q * kBThreads;
+            const int64_t i = gi0 + (int64_t)q * THREADS;
             const float4 p4 = M->pos[i];
             const float4 n4 = M->nrm[i];
             T.x[q] = make_float3(p4.x, p4.y, p4.z);
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
         }
         __syncwarp();
         if (lane < 2 * TPT) {
-            const int64_t blk0 = t * kBTTile + (int64_t)(lane >> 1) * kBThreads + warp * 32;
+            const int64_t blk0 = t * TTILE + (int64_t)(lane >> 1) * THREADS + warp * 32;
             tfrm[warp][lane] = M->frames[2 * (blk0 / kChunk) + (lane & 1)];
         }
         __syncwarp();
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
         const int64_t N = M->N;
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            const int64_t i = gi0 + (int64_t)q * kBThreads;
+            const int64_t i = gi0 + (int64_t)q * THREADS;
             if (i < N) {
                 atomicAdd(y + i, kInv4Pi * D1[q]);
                 atomicAdd(y + N + i, kInv4Pi * D2[q]);
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
             tile_sums<TPT>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, M->k, S1, C1, S2, C2, M->g64, gi0,
-                           kBThreads, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
+                           THREADS, ((st * M->sperm) % M->n_stiles) * kF32STile, M->N);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
             ++st;
         } else {
             st = 0;
-            if (t + 1 < M->n_ttiles) {
+            if (t + 1 < (M->N + TTILE - 1) / TTILE) {
                 ++t;
             } else {
                 ++a;
@@ -280,6 +285,17 @@ __global__ void __launch_bounds__(kBThreads, 1)
         }
     }
 }
+
+struct BatchVariant {
+    int tpt, threads, minb;
+    const void* fn;
+};
+#define IBIM_BATCH_VARIANT(T, W, M) {T, W, M, (const void*)batch_pair_kernel<T, W, M>}
+static const BatchVariant kBatchVariants[] = {
+    IBIM_BATCH_VARIANT(1, 512, 1), IBIM_BATCH_VARIANT(1, 256, 2), IBIM_BATCH_VARIANT(1, 128, 4),
+};
+#undef IBIM_BATCH_VARIANT
+constexpr int kNumBatchVariants = (int)(sizeof(kBatchVariants) / sizeof(kBatchVariants[0]));
 
 // ------------------------------------------------------------------ host side
 
@@ -292,8 +308,17 @@ struct BatchRun {
     int* d_want = nullptr;
     cudaStream_t bs = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int variant = 0;
     int grid = 0;
     int pack_blocks = 0;
+    int sms = 0;
+    void set_variant(int v)
+    {
+        variant = v;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kBatchVariants[v].fn, kBatchVariants[v].threads, 0);
+        grid = (occ < 1 ? 1 : occ) * sms;
+    }
     ~BatchRun()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -304,16 +329,59 @@ struct BatchRun {
     }
 };
 
+std::mutex g_batch_tune_mu;
+std::map<std::pair<int, int>, int> g_batch_tune;  // (device, floor(log2 sum N^2)) -> variant
+
 }  // namespace
 
 static ibim_status batch_operator(ibim_ctx* c0, BatchRun& R, int mode)
 {
-    batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, R.grid, R.d_plan);
+    const BatchVariant& v = kBatchVariants[R.variant];
+    batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, (int64_t)v.tpt * v.threads, R.grid,
+                                          R.d_plan);
     batch_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
-    batch_pair_kernel<<<R.grid, kBThreads, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+    switch (R.variant) {
+    case 1:
+        batch_pair_kernel<1, 256, 2><<<R.grid, 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+        break;
+    case 2:
+        batch_pair_kernel<1, 128, 4><<<R.grid, 128, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+        break;
+    default:
+        batch_pair_kernel<1, 512, 1><<<R.grid, 512, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
+        break;
+    }
     count_launch(c0, 3);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
+}
+
+static ibim_status tune_batch_variant(ibim_ctx* c0, BatchRun& R)
+{
+    cudaEvent_t e0, e1;
+    IBIM_CUDA(cudaEventCreate(&e0));
+    IBIM_CUDA(cudaEventCreate(&e1));
+    float best = 3.0e38f;
+    int pick = R.variant;
+    ibim_status st = IBIM_OK;
+    for (int v = 0; v < kNumBatchVariants && st == IBIM_OK; ++v) {
+        R.set_variant(v);
+        cudaEventRecord(e0, R.bs);
+        st = batch_operator(c0, R, 0);
+        cudaEventRecord(e1, R.bs);
+        if (st == IBIM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                pick = v;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    R.set_variant(pick);
+    return st;
 }
 
 ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts& o,
@@ -372,9 +440,8 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
         b.t = c->gm->t;
         b.st = c->gm->st;
         b.N = c->N;
-        b.n_ttiles = (c->N + kBTTile - 1) / kBTTile;
         b.n_stiles = (c->N + kF32STile - 1) / kF32STile;
-        b.sperm = make_schedule(c->N, kBTTile, c->N, kF32STile, 1).sperm;
+        b.sperm = make_schedule(c->N, kF32STile, c->N, kF32STile, 1).sperm;  // depends on n_stiles only
         b.k = f32_consts(pk);
         b.lambda1 = pk.lambda1;
         b.lambda2 = pk.lambda2;
@@ -385,10 +452,17 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
     IBIM_CUDA(cudaMalloc((void**)&R.d_plan, sizeof(BatchPlan)));
     IBIM_CUDA(cudaMalloc((void**)&R.d_want, sizeof(int) * nmol));
     IBIM_CUDA(cudaMemcpyAsync(R.d_mols, h.data(), sizeof(BatchMol) * nmol, cudaMemcpyHostToDevice, R.bs));
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_pair_kernel, kBThreads, 0);
-    if (occ < 1) occ = 1;
-    R.grid = occ * sms;
+    R.sms = sms;
+    double sum_n2 = 0.0;
+    for (int i = 0; i < nmol; ++i) sum_n2 += (double)ctxs[i]->N * (double)ctxs[i]->N;
+    const int bucket = (int)floor(log2(sum_n2 > 1.0 ? sum_n2 : 1.0));
+    int cached = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_tune_mu);
+        auto it = g_batch_tune.find({ctxs[0]->device, bucket});
+        if (it != g_batch_tune.end()) cached = it->second;
+    }
+    R.set_variant(cached >= 0 ? cached : 0);
     R.pack_blocks = (int)std::min<int64_t>(256, (maxN + 255) / 256);
 
     std::vector<int> iters(nmol, 0), cycles(nmol, 0), conv(nmol, 0), finished(nmol, 0);
@@ -432,6 +506,15 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
             }
         }
         if (nactive == 0) break;
+        // First round of a size class not seen before: time every variant on
+        // this round (plan + pack + pairs recompute V_{k+1} from scratch, so
+        // repeating them is harmless) and keep the fastest.
+        if (cached < 0) {
+            IBIM_TRY(tune_batch_variant(ctxs[0], R));
+            cached = R.variant;
+            std::lock_guard<std::mutex> lock(g_batch_tune_mu);
+            g_batch_tune[{ctxs[0]->device, bucket}] = cached;
+        }
         // one graph per solve: plan + pack + batched pairs + every molecule's orthogonalisation
         if (R.exec == nullptr) {
             cudaGraph_t graph = nullptr;
