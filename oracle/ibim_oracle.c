@@ -267,11 +267,15 @@ double orc_area(int64_t N, const double *w)
  * order (x fastest).  Per node: projection x* = x - d grad d = c + R (x-c)/|x-c|
  * (Sec. 2.2, closest-point projection), unit normal grad d = (x-c)/|x-c|,
  * weight w = J delta_eps(d) h^3 with J = 1 (weights equation, Sec. 3.2), the
- * signed distance and the integer grid coordinates.  Returns the node count;
+ * signed distance and the integer grid coordinates; when lap and sig2 are not
+ * NULL also the Laplacian of d at the grid node, 2/|x-c|, and the sum of the
+ * 2x2 principal minors of its Hessian, 1/|x-c|^2 (the inputs of the full
+ * Jacobian J = 1 - d lap + d^2 sig2, Sec. 2.2).  Returns the node count;
  * arrays are written only when cap >= count.
  */
 int64_t orc_sphere_nodes(double R, const double *c, const double *origin, double h, double eps,
-                         int64_t cap, double *xs, double *nrm, double *w, double *dist, int32_t *ijk)
+                         int64_t cap, double *xs, double *nrm, double *w, double *dist, int32_t *ijk,
+                         double *lap, double *sig2)
 {
     int64_t lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
@@ -304,6 +308,8 @@ int64_t orc_sphere_nodes(double R, const double *c, const double *origin, double
                         ijk[3 * n] = (int32_t)i;
                         ijk[3 * n + 1] = (int32_t)j;
                         ijk[3 * n + 2] = (int32_t)k;
+                        if (lap) lap[n] = 2.0 / len;
+                        if (sig2) sig2[n] = 1.0 / (len * len);
                     }
                     ++n;
                 }

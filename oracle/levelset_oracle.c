@@ -293,10 +293,13 @@ int64_t orc_ls_cavity(const orc_grid *g, double *phi, double eps, uint8_t *label
 }
 
 /* Band nodes {|phi| < eps} (Sec. 3.2) in grid order with WENO5 central
- * gradients, unit normals, projections and cosine weights.  Returns the
- * count; arrays are written when cap >= count. */
+ * gradients, unit normals, projections and cosine weights, the Laplacian of
+ * phi (curv) and, when sig2 is not NULL, the sum of the 2x2 principal minors
+ * of its Hessian (second central differences, mixed terms by the four-point
+ * stencil), the inputs of the full Jacobian J = 1 - phi lap + phi^2 sig2
+ * (Sec. 2.2).  Returns the count; arrays are written when cap >= count. */
 int64_t orc_ls_band(const orc_grid *g, const double *phi, double eps, int64_t cap, double *xs, double *nrm,
-                    double *w, double *dist, int32_t *ijk, double *curv)
+                    double *w, double *dist, int32_t *ijk, double *curv, double *sig2)
 {
     const double h = g->h;
     int64_t n = 0;
@@ -332,6 +335,31 @@ int64_t orc_ls_band(const orc_grid *g, const double *phi, double eps, int64_t ca
                                (h * h);
                     }
                     curv[n] = lap;
+                    if (sig2) {
+                        /* Hessian H_ab by central differences (indices clamped at the box) */
+                        double H[3][3];
+                        int64_t c0[3] = {i, j, k};
+                        for (int a = 0; a < 3; ++a) {
+                            int64_t m[3] = {i, j, k}, q[3] = {i, j, k};
+                            m[a] = clampi(m[a] - 1, g->n[a]);
+                            q[a] = clampi(q[a] + 1, g->n[a]);
+                            H[a][a] = (phi[idx(g, q[0], q[1], q[2])] - 2.0 * p + phi[idx(g, m[0], m[1], m[2])]) / (h * h);
+                        }
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = a + 1; b < 3; ++b) {
+                                double v[4];
+                                const int sa[4] = {1, 1, -1, -1}, sb[4] = {1, -1, 1, -1};
+                                for (int t = 0; t < 4; ++t) {
+                                    int64_t e[3] = {c0[0], c0[1], c0[2]};
+                                    e[a] = clampi(e[a] + sa[t], g->n[a]);
+                                    e[b] = clampi(e[b] + sb[t], g->n[b]);
+                                    v[t] = phi[idx(g, e[0], e[1], e[2])];
+                                }
+                                H[a][b] = H[b][a] = (v[0] - v[1] - v[2] + v[3]) / (4.0 * h * h);
+                            }
+                        sig2[n] = H[0][0] * H[1][1] - H[0][1] * H[0][1] + H[0][0] * H[2][2] - H[0][2] * H[0][2] +
+                                  H[1][1] * H[2][2] - H[1][2] * H[1][2];
+                    }
                     ijk[3 * n] = (int32_t)gi;
                     ijk[3 * n + 1] = (int32_t)gj;
                     ijk[3 * n + 2] = (int32_t)gk;

@@ -15,7 +15,8 @@ from . import build as _build
 __all__ = [
     "Phys", "lib", "num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
     "rhs", "psi_rxn", "gpol", "area", "sphere_nodes", "gmres", "KCAL_PER_E2_A",
-    "ls_grid", "grid_coords", "ls_ses", "ls_steps", "ls_band", "ses_nodes",
+    "ls_grid", "make_grid", "grid_coords", "ls_ses", "ls_steps", "ls_band", "ses_nodes", "jacobian",
+    "jacobian_weights",
 ]
 
 # Coulomb constant in kcal mol^-1 Angstrom e^-2 times 4 pi: energies in the
@@ -73,7 +74,7 @@ def lib():
         L.orc_area.argtypes = [ctypes.c_int64, _D]
         L.orc_sphere_nodes.restype = ctypes.c_int64
         L.orc_sphere_nodes.argtypes = [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_int64, _D, _D, _D, _D, _I32]
+                                       ctypes.c_int64, _D, _D, _D, _D, _I32, _D, _D]
         L.orc_gmres.restype = ctypes.c_int
         L.orc_gmres.argtypes = [ctypes.c_int64, _D, _D, _D, _P, _D, _D, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
@@ -196,17 +197,20 @@ def sphere_nodes(R, centre=(0.0, 0.0, 0.0), h=0.25, eps=0.75, origin=(0.0, 0.0, 
     c = _f64(centre, 3)
     o = _f64(origin, 3)
     L = lib()
-    n = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), 0, None, None, None, None, None)
+    n = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), 0, None, None, None, None, None, None,
+                           None)
     xs = np.empty((n, 3))
     nrm = np.empty((n, 3))
     w = np.empty(n)
     d = np.empty(n)
     ijk = np.empty((n, 3), dtype=np.int32)
+    lap = np.empty(n)
+    sig2 = np.empty(n)
     n2 = L.orc_sphere_nodes(float(R), _d(c), _d(o), float(h), float(eps), n, _d(xs), _d(nrm), _d(w),
-                            _d(d), ijk.ctypes.data_as(_I32))
+                            _d(d), ijk.ctypes.data_as(_I32), _d(lap), _d(sig2))
     assert n2 == n
-    # twice the mean curvature of the sphere at the projections: 2/R
-    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": np.full(n, 2.0 / R)}
+    # curv: Laplacian of d at the grid node (twice the mean curvature of the level sphere through it)
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": lap, "sig2": sig2}
 
 
 def gmres(xs, nrm, w, phys, g, x0=None, tol=1e-8, restart=100, maxit=500):
@@ -244,7 +248,7 @@ def _ls_lib():
         L.orc_ls_cavity.restype = ctypes.c_int64
         L.orc_ls_cavity.argtypes = [G, _D, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
         L.orc_ls_band.restype = ctypes.c_int64
-        L.orc_ls_band.argtypes = [G, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D, _I32, _D]
+        L.orc_ls_band.argtypes = [G, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D, _I32, _D, _D]
         L.orc_ls_ses.restype = ctypes.c_int64
         L.orc_ls_ses.argtypes = [G, ctypes.c_int64, _D, _D, ctypes.c_double, ctypes.c_double, _D]
         L._ls_ready = True
@@ -257,6 +261,16 @@ def ls_grid(z, r, probe, h, eps):
     r = _f64(r, -1)
     g = _Grid()
     _ls_lib().orc_ls_grid(r.shape[0], _d(z), _d(r), float(probe), float(h), float(eps), ctypes.byref(g))
+    return g
+
+
+def make_grid(lo, n, h):
+    """A level-set grid with node (0,0,0) at integer coordinates lo, n nodes per axis, spacing h."""
+    g = _Grid()
+    for a in range(3):
+        g.lo[a] = int(lo[a])
+        g.n[a] = int(n[a])
+    g.h = float(h)
     return g
 
 
@@ -303,16 +317,32 @@ def ls_band(g, phi, eps):
     """Band nodes of a level-set grid (Sec. 3.2): dict of xs, nrm, w, d, ijk (grid order)."""
     phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
     L = _ls_lib()
-    n = L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), 0, None, None, None, None, None, None)
+    n = L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), 0, None, None, None, None, None, None, None)
     xs = np.empty((n, 3))
     nrm = np.empty((n, 3))
     w = np.empty(n)
     d = np.empty(n)
     ijk = np.empty((n, 3), dtype=np.int32)
     curv = np.empty(n)
+    sig2 = np.empty(n)
     L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), n, _d(xs), _d(nrm), _d(w), _d(d), ijk.ctypes.data_as(_I32),
-                  _d(curv))
-    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": curv}
+                  _d(curv), _d(sig2))
+    return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": curv, "sig2": sig2}
+
+
+def jacobian(nodes):
+    """Full Jacobian of the change of variables between Gamma and the level
+    surface of d through each node (Sec. 2.2, reading: the last term is the sum
+    of the 2x2 principal minors of the Hessian of d, so that J = (1 - d k1)(1 - d k2)
+    in the level surface's principal curvatures k1, k2), clamped at 0 where the
+    band is wider than a local radius of curvature."""
+    d = nodes["d"]
+    return np.maximum(1.0 - d * nodes["curv"] + d * d * nodes["sig2"], 0.0)
+
+
+def jacobian_weights(nodes):
+    """w_j = J_j delta_eps(d_j) h^3 from the J = 1 weights of the nodes."""
+    return nodes["w"] * jacobian(nodes)
 
 
 def ses_nodes(z, r, probe=1.4, h=0.5, eps=1.0):
