@@ -134,10 +134,31 @@ ibim_status ibim_num_nodes(const ibim_ctx* ctx, int64_t* N);
 ibim_status ibim_get_nodes(const ibim_ctx* ctx, double* xstar, double* normal, double* w,
                            double* d, int32_t* ijk);
 
-/* Per-node Laplacian of the signed distance (twice the mean curvature of the
- * level surface): 2/R on analytic spheres, second central differences of phi
- * for ibim_build, 0 for caller-given nodes.  curv: host, N doubles. */
+/* Per-node Laplacian of the signed distance at the grid node (twice the mean
+ * curvature of the level surface through it): 2/|x - c| on analytic spheres,
+ * second central differences of phi for ibim_build, 0 for caller-given nodes.
+ * curv: host, N doubles. */
 ibim_status ibim_get_curvature(const ibim_ctx* ctx, double* curv);
+
+/*
+ * Full Jacobian of the change of variables between Gamma and the level
+ * surface of the distance through each node (Sec. 2.2): J = 1 - d lap(d) +
+ * d^2 sigma2(Hess d), the printed last term read as the sum of the 2x2
+ * principal minors of the Hessian (so J = (1 - d k1)(1 - d k2) in the level
+ * surface's principal curvatures; (R/|x - c|)^2 on a sphere), clamped at 0
+ * where the band is wider than a local radius of curvature.  Spheres use the
+ * exact derivatives, level sets central differences of phi.
+ * ibim_set_jacobian: mode 0 (default, every run of the paper) weights
+ * w = delta_eps(d) h^3; mode 1 weights w = J delta_eps(d) h^3, which removes
+ * the O(eps^2) bias of the J = 1 weights (a sphere's area becomes 4 pi R^2
+ * instead of 4 pi (R^2 + c eps^2)).  Applies to the following operator
+ * applications, solves, energies and areas; synchronises.
+ * ibim_get_jacobian: host copy of J per node (N doubles).
+ * Both return IBIM_ERR_STATE for caller-given nodes (ibim_build_from_nodes:
+ * no distance function; mode 0 is accepted and changes nothing).
+ */
+ibim_status ibim_set_jacobian(ibim_ctx* ctx, int mode);
+ibim_status ibim_get_jacobian(const ibim_ctx* ctx, double* J);
 
 /* ----------------------------------------------------------- operator etc. */
 

@@ -252,6 +252,8 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_geo64);
     cudaFree(c->d_dist);
     cudaFree(c->d_curv);
+    cudaFree(c->d_sig2);
+    cudaFree(c->d_w1);
     cudaFree(c->d_ijk);
     cudaFree(c->d_pos32);
     cudaFree(c->d_nrm32);
@@ -380,6 +382,8 @@ ibim_status ibim_build_from_nodes(int64_t N, const double* xstar, const double* 
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_dist, 0, sizeof(double) * N, c->stream);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_curv, 0, sizeof(double) * N, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sig2, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sig2, 0, sizeof(double) * N, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_ijk, ijk.data(), sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -429,6 +433,62 @@ ibim_status ibim_get_curvature(const ibim_ctx* cc, double* curv)
     ibim_ctx* c = const_cast<ibim_ctx*>(cc);
     IBIM_CUDA(cudaMemcpyAsync(curv, c->d_curv, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
     IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    return IBIM_OK;
+}
+
+// J = 1 - d lap + d^2 sig2, clamped at 0 (Sec. 2.2 Jacobian; the last term
+// read as the sum of the Hessian's 2x2 principal minors).
+__device__ __forceinline__ double full_jacobian(double d, double lap, double sig2)
+{
+    const double J = 1.0 - d * lap + d * d * sig2;
+    return J > 0.0 ? J : 0.0;
+}
+
+__global__ void jacobian_kernel(const double* __restrict__ dist, const double* __restrict__ lap,
+                                const double* __restrict__ sig2, int64_t N, double* __restrict__ J)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) J[i] = full_jacobian(dist[i], lap[i], sig2[i]);
+}
+
+__global__ void jacobian_weights_kernel(const double* __restrict__ w1, const double* __restrict__ dist,
+                                        const double* __restrict__ lap, const double* __restrict__ sig2, int64_t N,
+                                        int mode, double* __restrict__ w)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) w[i] = mode ? w1[i] * full_jacobian(dist[i], lap[i], sig2[i]) : w1[i];
+}
+
+ibim_status ibim_get_jacobian(const ibim_ctx* cc, double* J)
+{
+    if (cc == nullptr || J == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
+    ibim_ctx* c = const_cast<ibim_ctx*>(cc);
+    if (c->d_w1 == nullptr) return fail(IBIM_ERR_STATE, "caller-given nodes carry no distance function");
+    const int64_t N = c->N;
+    IBIM_TRY(ensure(c, (void**)&c->d_io, &c->io_bytes, sizeof(double) * N));
+    jacobian_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->d_dist, c->d_curv, c->d_sig2, N, c->d_io);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_CUDA(cudaMemcpyAsync(J, c->d_io, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    return IBIM_OK;
+}
+
+ibim_status ibim_set_jacobian(ibim_ctx* c, int mode)
+{
+    if (c == nullptr || (mode != 0 && mode != 1)) return fail(IBIM_ERR_ARG, "need a context and mode 0 or 1");
+    if (c->d_w1 == nullptr) {
+        if (mode == 0) return IBIM_OK;
+        return fail(IBIM_ERR_STATE, "caller-given nodes carry no distance function: their weights stay as given");
+    }
+    const int64_t N = c->N;
+    jacobian_weights_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->d_w1, c->d_dist, c->d_curv,
+                                                                               c->d_sig2, N, mode,
+                                                                               c->d_geo64 + 6 * N);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    c->jacobian = mode;
     return IBIM_OK;
 }
 

@@ -59,12 +59,6 @@ __device__ __forceinline__ bool sphere_node(const SphereBox& B, uint64_t code, d
 
 constexpr int kCompactBlock = 1024;
 
-__global__ void fill_value_kernel(double* __restrict__ a, int64_t n, double v)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = v;
-}
-
 __global__ void __launch_bounds__(kCompactBlock) sphere_count_kernel(SphereBox B, uint64_t ncodes, int* __restrict__ counts)
 {
     const uint64_t code = (uint64_t)blockIdx.x * kCompactBlock + threadIdx.x;
@@ -106,7 +100,8 @@ __global__ void scan_counts_kernel(int* __restrict__ counts, int64_t nblocks, in
 
 __global__ void __launch_bounds__(kCompactBlock) sphere_write_kernel(SphereBox B, uint64_t ncodes, const int* __restrict__ offsets, int64_t N,
                                     double* __restrict__ geo, double* __restrict__ dist,
-                                    int32_t* __restrict__ ijk_out)
+                                    int32_t* __restrict__ ijk_out, double* __restrict__ lap,
+                                    double* __restrict__ sig2)
 {
     __shared__ int warp_tot[kCompactBlock / 32];
     const uint64_t code = (uint64_t)blockIdx.x * kCompactBlock + threadIdx.x;
@@ -130,6 +125,11 @@ __global__ void __launch_bounds__(kCompactBlock) sphere_write_kernel(SphereBox B
     geo[5 * N + j] = n[2];
     geo[6 * N + j] = w;
     dist[j] = d;
+    // Laplacian of d = |x - c| - R at the grid node and the sum of the 2x2
+    // principal minors of its Hessian (eigenvalues 1/|x-c| twice and 0)
+    const double len = B.R + d;
+    lap[j] = 2.0 / len;
+    sig2[j] = 1.0 / (len * len);
     ijk_out[3 * j] = ijk[0];
     ijk_out[3 * j + 1] = ijk[1];
     ijk_out[3 * j + 2] = ijk[2];
@@ -176,11 +176,11 @@ ibim_status build_sphere_nodes(ibim_ctx* c, double R, const double* centre, cons
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dist, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ijk, sizeof(int32_t) * 3 * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sig2, sizeof(double) * N);
     if (e == cudaSuccess) {
-        fill_value_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->d_curv, N, 2.0 / R);
-        count_launch(c);
         sphere_write_kernel<<<(unsigned)nblocks, kCompactBlock, 0, c->stream>>>(B, ncodes, d_counts, N, c->d_geo64,
-                                                                                c->d_dist, c->d_ijk);
+                                                                                c->d_dist, c->d_ijk, c->d_curv,
+                                                                                c->d_sig2);
         count_launch(c);
         e = cudaGetLastError();
     }
@@ -284,11 +284,13 @@ static ibim_status compact_order(ibim_ctx* c)
     double* geo = nullptr;
     double* dist = nullptr;
     double* curv = nullptr;
+    double* sig2 = nullptr;
     int32_t* ijk = nullptr;
     cudaError_t e = cudaMalloc((void**)&d_perm, sizeof(int64_t) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&geo, sizeof(double) * 7 * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dist, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&curv, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sig2, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ijk, sizeof(int32_t) * 3 * N);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_perm, perm.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->stream);
@@ -297,8 +299,9 @@ static ibim_status compact_order(ibim_ctx* c)
         gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_geo64, d_perm, N, 7, geo);
         gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_dist, d_perm, N, 1, dist);
         gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_curv, d_perm, N, 1, curv);
+        gather_fields_kernel<double><<<nb, 256, 0, c->stream>>>(c->d_sig2, d_perm, N, 1, sig2);
         gather_triples_kernel<<<nb, 256, 0, c->stream>>>(c->d_ijk, d_perm, N, ijk);
-        count_launch(c, 4);
+        count_launch(c, 5);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -307,16 +310,19 @@ static ibim_status compact_order(ibim_ctx* c)
         cudaFree(geo);
         cudaFree(dist);
         cudaFree(curv);
+        cudaFree(sig2);
         cudaFree(ijk);
         return cuda_fail(e, "compact node order", __FILE__, __LINE__);
     }
     std::swap(c->d_geo64, geo);
     std::swap(c->d_dist, dist);
     std::swap(c->d_curv, curv);
+    std::swap(c->d_sig2, sig2);
     std::swap(c->d_ijk, ijk);
     cudaFree(geo);
     cudaFree(dist);
     cudaFree(curv);
+    cudaFree(sig2);
     cudaFree(ijk);
     return IBIM_OK;
 }
@@ -325,6 +331,11 @@ ibim_status finish_geometry(ibim_ctx* c, bool reorder)
 {
     if (reorder) IBIM_TRY(compact_order(c));
     const int64_t N = c->N;
+    if (reorder) {  // built geometries: keep the J = 1 weights for ibim_set_jacobian
+        IBIM_CUDA(cudaMalloc((void**)&c->d_w1, sizeof(double) * N));
+        IBIM_CUDA(cudaMemcpyAsync(c->d_w1, c->d_geo64 + 6 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    }
     const int64_t n_pad = padded_nodes(N);
     IBIM_CUDA(cudaMalloc((void**)&c->d_pos32, sizeof(float4) * n_pad));
     IBIM_CUDA(cudaMalloc((void**)&c->d_nrm32, sizeof(float4) * n_pad));

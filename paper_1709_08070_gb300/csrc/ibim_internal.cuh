@@ -107,7 +107,10 @@ struct ibim_ctx {
     // FP64 geometry, SoA: x*, y*, z*, nx, ny, nz, w (7 arrays of N)
     double* d_geo64 = nullptr;
     double* d_dist = nullptr;     // signed distance per node (0 for caller nodes)
-    double* d_curv = nullptr;     // Laplacian of the distance (twice the mean curvature) per node
+    double* d_curv = nullptr;     // Laplacian of the distance at each node (twice the mean curvature)
+    double* d_sig2 = nullptr;     // sum of the 2x2 principal minors of the Hessian of the distance
+    double* d_w1 = nullptr;       // the J = 1 weights delta_eps(d) h^3 of a built geometry (else NULL)
+    int jacobian = 0;             // 0: weights with J = 1; 1: with the full Jacobian
     int32_t* d_ijk = nullptr;     // grid coordinates (N x 3) or -1
     // FP32 geometry: float4 (x* relative to its 32-node chunk centre, w),
     // float4 (n, 0), and per chunk two float4 (centre hi + radius, centre lo)

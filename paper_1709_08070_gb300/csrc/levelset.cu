@@ -294,7 +294,8 @@ __global__ void band_scan_kernel(int* __restrict__ counts, int64_t nblocks, int6
 
 __global__ void __launch_bounds__(kBandBlock) band_write_kernel(LsGrid g, const double* __restrict__ phi, double eps, uint64_t ncodes,
                                   const int* __restrict__ offsets, int64_t N, double* __restrict__ geo,
-                                  double* __restrict__ dist, int32_t* __restrict__ ijk, double* __restrict__ curv)
+                                  double* __restrict__ dist, int32_t* __restrict__ ijk, double* __restrict__ curv,
+                                  double* __restrict__ sig2)
 {
     __shared__ int warp_tot[kBandBlock / 32];
     const uint64_t code = (uint64_t)blockIdx.x * kBandBlock + threadIdx.x;
@@ -326,15 +327,33 @@ __global__ void __launch_bounds__(kBandBlock) band_write_kernel(LsGrid g, const 
     }
     geo[6 * N + jn] = (1.0 + cos(kPi * p / eps)) / (2.0 * eps) * g.h * g.h * g.h;
     dist[jn] = p;
-    // Laplacian of phi by second central differences (twice the mean curvature)
+    // Hessian of phi by central differences (indices clamped at the box):
+    // its trace (the Laplacian, twice the mean curvature) and the sum of its
+    // 2x2 principal minors, the inputs of the full Jacobian (Sec. 2.2)
+    double H[3][3];
+    const int64_t c0[3] = {i, j, k};
     double lap = 0.0;
     for (int ax = 0; ax < 3; ++ax) {
         int64_t im[3] = {i, j, k}, ip[3] = {i, j, k};
         im[ax] = clamp_i(im[ax] - 1, g.n[ax]);
         ip[ax] = clamp_i(ip[ax] + 1, g.n[ax]);
-        lap += (phi[ls_idx(g, ip[0], ip[1], ip[2])] - 2.0 * p + phi[ls_idx(g, im[0], im[1], im[2])]) / (g.h * g.h);
+        H[ax][ax] = (phi[ls_idx(g, ip[0], ip[1], ip[2])] - 2.0 * p + phi[ls_idx(g, im[0], im[1], im[2])]) / (g.h * g.h);
+        lap += H[ax][ax];
     }
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+            double v[4];
+            for (int t = 0; t < 4; ++t) {
+                int64_t e[3] = {c0[0], c0[1], c0[2]};
+                e[a] = clamp_i(e[a] + ((t < 2) ? 1 : -1), g.n[a]);
+                e[b] = clamp_i(e[b] + ((t & 1) ? -1 : 1), g.n[b]);
+                v[t] = phi[ls_idx(g, e[0], e[1], e[2])];
+            }
+            H[a][b] = H[b][a] = (v[0] - v[1] - v[2] + v[3]) / (4.0 * g.h * g.h);
+        }
     curv[jn] = lap;
+    sig2[jn] = H[0][0] * H[1][1] - H[0][1] * H[0][1] + H[0][0] * H[2][2] - H[0][2] * H[0][2] + H[1][1] * H[2][2] -
+               H[1][2] * H[1][2];
 }
 
 // ------------------------------------------------------------------ driver
@@ -527,10 +546,11 @@ ibim_status build_levelset(ibim_ctx* c, int64_t Na, const double* z, const doubl
             if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dist, sizeof(double) * N);
             if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ijk, sizeof(int32_t) * 3 * N);
             if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_curv, sizeof(double) * N);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sig2, sizeof(double) * N);
             if (e == cudaSuccess) {
                 band_write_kernel<<<(unsigned)nblocks, kBandBlock, 0, c->stream>>>(g, d_phi, eps, ncodes, d_counts, N,
                                                                                    c->d_geo64, c->d_dist, c->d_ijk,
-                                                                                   c->d_curv);
+                                                                                   c->d_curv, c->d_sig2);
                 count_launch(c);
                 e = cudaGetLastError();
             }

@@ -20,7 +20,7 @@ __all__ = [
     "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
     "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
-    "ibim_get_curvature",
+    "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian",
 ]
 
 IBIM_F64 = 64
@@ -90,6 +90,8 @@ _SIGS = {
     "ibim_solve_batch": [ctypes.c_int, ctypes.POINTER(_V), ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts),
                          ctypes.POINTER(_V), ctypes.POINTER(SolveInfo)],
     "ibim_get_curvature": [_V, _D],
+    "ibim_set_jacobian": [_V, ctypes.c_int],
+    "ibim_get_jacobian": [_V, _D],
     "ibim_wsnet_create": [ctypes.c_uint64, _V, _CTXP],
     "ibim_wsnet_get_params": [_V, ctypes.POINTER(ctypes.c_float)],
     "ibim_wsnet_set_params": [_V, ctypes.POINTER(ctypes.c_float)],
@@ -362,6 +364,17 @@ def ibim_set_f32_variant(ctx, variant, ctas_per_sm=0):
     _check(lib().ibim_set_f32_variant(ctx, int(variant), int(ctas_per_sm)))
 
 
+def ibim_set_jacobian(ctx, mode):
+    _check(lib().ibim_set_jacobian(ctx, int(mode)))
+
+
+def ibim_get_jacobian(ctx):
+    N = ibim_num_nodes(ctx)
+    out = np.empty(N)
+    _check(lib().ibim_get_jacobian(ctx, out.ctypes.data_as(_D)))
+    return out
+
+
 def ibim_get_curvature(ctx):
     out = np.empty(ibim_num_nodes(ctx))
     _check(lib().ibim_get_curvature(ctx, out.ctypes.data_as(_D)))
@@ -495,6 +508,15 @@ class Context:
 
     def autotune(self, phys):
         return ibim_autotune(self.handle, phys)
+
+    def curvature(self):
+        return ibim_get_curvature(self.handle)
+
+    def set_jacobian(self, mode):
+        ibim_set_jacobian(self.handle, mode)
+
+    def jacobian(self):
+        return ibim_get_jacobian(self.handle)
 
     def set_f32_variant(self, variant, ctas_per_sm=0):
         ibim_set_f32_variant(self.handle, variant, ctas_per_sm)

@@ -70,3 +70,23 @@ def test_levelset_sphere_area_with_full_jacobian():
     a1 = b["w"].sum() / A - 1.0
     aj = oracle.jacobian_weights(b).sum() / A - 1.0
     assert abs(aj) < 0.1 * abs(a1), (a1, aj)
+
+
+def test_born_energy_with_jacobian_does_not_depend_on_the_band_width():
+    """With J = 1 the Born energy drifts as the band widens (the O(eps^2) area
+    bias); with the full J it does not, and it is closer to the closed form."""
+    from oracle import closed_forms as cf
+    R, h = 2.0, 0.25
+    exact = cf.born_energy(R, 1.0, 1.0, 80.0, 0.1257)
+    z, q = np.zeros((1, 3)), np.ones(1)
+    P = oracle.Phys(1.0, 80.0, 0.1257, h, 0)
+    err = {}
+    for k in (3, 4):
+        g = oracle.sphere_nodes(R, h=h, eps=k * h)
+        b = oracle.rhs(g["xs"], g["nrm"], z, q, 1.0)
+        for name, w in (("one", g["w"]), ("full", oracle.jacobian_weights(g))):
+            x, *_ = oracle.gmres(g["xs"], g["nrm"], w, P, b, tol=1e-10)
+            G = oracle.gpol(q, oracle.psi_rxn(g["xs"], g["nrm"], w, z, P, x))
+            err[(name, k)] = (G - exact) / exact
+    assert abs(err[("full", 3)] - err[("full", 4)]) < 0.1 * abs(err[("one", 3)] - err[("one", 4)]), err
+    assert abs(err[("full", 3)]) < abs(err[("one", 3)]) and abs(err[("full", 4)]) < abs(err[("one", 4)]), err
