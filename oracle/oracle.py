@@ -16,7 +16,7 @@ __all__ = [
     "Phys", "lib", "num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
     "rhs", "psi_rxn", "gpol", "area", "sphere_nodes", "gmres", "KCAL_PER_E2_A",
     "ls_grid", "make_grid", "grid_coords", "ls_ses", "ls_steps", "ls_band", "ses_nodes", "jacobian",
-    "jacobian_weights",
+    "jacobian_weights", "solve_energy", "extrapolated_energy",
 ]
 
 # Coulomb constant in kcal mol^-1 Angstrom e^-2 times 4 pi: energies in the
@@ -328,6 +328,25 @@ def ls_band(g, phi, eps):
     L.orc_ls_band(ctypes.byref(g), _d(phi), float(eps), n, _d(xs), _d(nrm), _d(w), _d(d), ijk.ctypes.data_as(_I32),
                   _d(curv), _d(sig2))
     return {"xs": xs, "nrm": nrm, "w": w, "d": d, "ijk": ijk, "curv": curv, "sig2": sig2}
+
+
+def solve_energy(xs, nrm, w, phys, z, q, eps_in, tol=1e-10, maxit=2000):
+    """FP64 solve of the discrete system (Sec. 3.3, zero start) and its G_pol
+    (Sec. 3.5): returns (p, G_pol in e^2/A, GMRES iterations)."""
+    b = rhs(xs, nrm, z, q, eps_in)
+    p, it, _, _ = gmres(xs, nrm, w, phys, b, tol=tol, maxit=maxit)
+    return p, gpol(q, psi_rxn(xs, nrm, w, z, phys, p)), it
+
+
+def extrapolated_energy(xs, nrm, w, phys, z, q, eps_in, tol=1e-10):
+    """Richardson extrapolation of the tube regularisation (Sec. 2.2.1) to
+    tau -> 0, reading its error as linear in tau: the system is solved with
+    tau and with tau/2 on the same nodes and p* = 2 p(tau/2) - p(tau); G_pol is
+    linear in p, so G* = 2 G(tau/2) - G(tau).  Returns (p*, G*, G(tau), G(tau/2))."""
+    half = Phys(phys.eps_in, phys.eps_out, phys.kappa, 0.5 * phys.tau, phys.tube_rule)
+    p1, g1, _ = solve_energy(xs, nrm, w, phys, z, q, eps_in, tol)
+    p2, g2, _ = solve_energy(xs, nrm, w, half, z, q, eps_in, tol)
+    return 2.0 * p2 - p1, 2.0 * g2 - g1, g1, g2
 
 
 def jacobian(nodes):
