@@ -265,6 +265,7 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_red);
     cudaFree(c->d_err);
     cudaFree(c->d_io);
+    cudaFree(c->d_aux);
     cudaFree(c->d_phi);
     delete c;
 }
@@ -585,6 +586,64 @@ ibim_status ibim_solve(ibim_ctx* c, const ibim_phys* phys, const ibim_solve_opts
     ibim_status s2 = check_device_error(c);
     if (s2 != IBIM_OK) return s2;
     if (s == IBIM_ERR_NOT_CONVERGED) return fail(IBIM_ERR_NOT_CONVERGED, "GMRES reached maxit above tol");
+    return IBIM_OK;
+}
+
+// p = 2 p_half - p_tau (Richardson step of the tube extrapolation).
+__global__ void extrapolate_kernel(double* __restrict__ p_half, const double* __restrict__ p_tau, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p_half[i] = 2.0 * p_half[i] - p_tau[i];
+}
+
+ibim_status ibim_solve_extrapolated(ibim_ctx* c, const ibim_phys* phys, const ibim_solve_opts* o, double* d_p,
+                                    ibim_solve_info* info)
+{
+    if (c == nullptr || o == nullptr || d_p == nullptr || info == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
+    IBIM_TRY(check_phys(phys));
+    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C) return fail(IBIM_ERR_ARG, "bad precision");
+    if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
+        return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
+    if (o->start != 0 && o->start != 1 && o->start != 3) return fail(IBIM_ERR_ARG, "start must be 0, 1 or 3");
+    if (c->Nc <= 0) return fail(IBIM_ERR_STATE, "no charges set");
+    memset(info, 0, sizeof(*info));
+    const int64_t len = 2 * c->N;
+    IBIM_TRY(ensure(c, (void**)&c->d_aux, &c->aux_bytes, sizeof(double) * len));
+    // 1. the system with tau (the caller's start)
+    if (o->start == 3)
+        IBIM_CUDA(cudaMemcpyAsync(c->d_aux, d_p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    ibim_solve_info i1;
+    memset(&i1, 0, sizeof(i1));
+    ibim_status s1 = gmres_solve(c, *phys, *o, c->d_aux, &i1);
+    if (s1 != IBIM_OK && s1 != IBIM_ERR_NOT_CONVERGED) return s1;
+    // 2. the system with tau/2, started from the tau solution
+    ibim_phys half = *phys;
+    half.tau = 0.5 * phys->tau;
+    ibim_solve_opts o2 = *o;
+    o2.start = 3;
+    IBIM_CUDA(cudaMemcpyAsync(d_p, c->d_aux, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    ibim_solve_info i2;
+    memset(&i2, 0, sizeof(i2));
+    ibim_status s2 = gmres_solve(c, half, o2, d_p, &i2);
+    if (s2 != IBIM_OK && s2 != IBIM_ERR_NOT_CONVERGED) return s2;
+    // 3. p* = 2 p(tau/2) - p(tau); G_pol is linear in p
+    extrapolate_kernel<<<(unsigned)((len + 255) / 256), 256, 0, c->stream>>>(d_p, c->d_aux, len);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    double gpol = 0.0, area = 0.0;
+    IBIM_TRY(energy_launch(c, *phys, d_p, nullptr, &gpol));
+    IBIM_TRY(area_launch(c, &area));
+    info->iters = i1.iters + i2.iters;
+    info->cycles = i1.cycles + i2.cycles;
+    info->converged = (i1.converged && i2.converged) ? 1 : 0;
+    info->relres = std::max(i1.relres, i2.relres);
+    info->gpol = gpol;
+    info->gpol_kcal = gpol * kKcalPerE2A;
+    info->area = area;
+    info->matvecs_f32 = i1.matvecs_f32 + i2.matvecs_f32;
+    info->matvecs_f64 = i1.matvecs_f64 + i2.matvecs_f64;
+    IBIM_TRY(check_device_error(c));
+    if (!info->converged) return fail(IBIM_ERR_NOT_CONVERGED, "GMRES reached maxit above tol");
     return IBIM_OK;
 }
 

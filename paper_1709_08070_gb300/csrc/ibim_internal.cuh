@@ -141,6 +141,8 @@ struct ibim_ctx {
     unsigned* d_err = nullptr; // device error word (kDevErr* bits), zeroed at build
     double* d_io = nullptr;    // staging for the host-buffer entry points
     size_t io_bytes = 0;
+    double* d_aux = nullptr;   // the tau solution of an extrapolated solve
+    size_t aux_bytes = 0;
     ibim::GmresWork* gm = nullptr;
     ibim::Timing timing;
     // incremented whenever a workspace is reallocated: CUDA graphs captured

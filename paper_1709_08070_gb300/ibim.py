@@ -20,7 +20,7 @@ __all__ = [
     "ibim_timing_enable", "ibim_timing_reset", "ibim_timing_get", "ibim_destroy", "ibim_last_error",
     "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
-    "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian",
+    "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian", "ibim_solve_extrapolated",
 ]
 
 IBIM_F64 = 64
@@ -91,6 +91,7 @@ _SIGS = {
                          ctypes.POINTER(_V), ctypes.POINTER(SolveInfo)],
     "ibim_get_curvature": [_V, _D],
     "ibim_set_jacobian": [_V, ctypes.c_int],
+    "ibim_solve_extrapolated": [_V, ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts), _V, ctypes.POINTER(SolveInfo)],
     "ibim_get_jacobian": [_V, _D],
     "ibim_wsnet_create": [ctypes.c_uint64, _V, _CTXP],
     "ibim_wsnet_get_params": [_V, ctypes.POINTER(ctypes.c_float)],
@@ -279,6 +280,17 @@ def ibim_solve(ctx, phys, d_p, allow_not_converged=False, **opts):
     o = _opts(**opts)
     info = SolveInfo()
     st = lib().ibim_solve(ctx, ctypes.byref(p), ctypes.byref(o), _dptr(d_p), ctypes.byref(info))
+    if not (allow_not_converged and st == 5):
+        _check(st)
+    return info.as_dict()
+
+
+def ibim_solve_extrapolated(ctx, phys, d_p, allow_not_converged=False, **opts):
+    """Solves with tau and tau/2 and returns the Richardson combination (see include/ibim.h)."""
+    p = _phys(phys)
+    o = _opts(**opts)
+    info = SolveInfo()
+    st = lib().ibim_solve_extrapolated(ctx, ctypes.byref(p), ctypes.byref(o), _dptr(d_p), ctypes.byref(info))
     if not (allow_not_converged and st == 5):
         _check(st)
     return info.as_dict()
@@ -502,6 +514,9 @@ class Context:
 
     def solve(self, phys, d_p, **opts):
         return ibim_solve(self.handle, phys, d_p, **opts)
+
+    def solve_extrapolated(self, phys, d_p, **opts):
+        return ibim_solve_extrapolated(self.handle, phys, d_p, **opts)
 
     def solve_host(self, phys, z, q, h_p=None, **opts):
         return ibim_solve_host(self.handle, phys, z, q, h_p, **opts)
