@@ -524,6 +524,47 @@ def run_learned(args):
     loss = net.train(args.learn_steps, batch_nodes=8192, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    # FP32 + batched + warm-started vs the plain FP64 GPU solve, on held-out globules
+    cmp_atoms = rng.integers(args.learn_cmp_lo, args.learn_cmp_hi + 1, size=args.learn_cmp)
+    cmp_kappa = rng.uniform(0.0, 0.2, size=args.learn_cmp)
+    cctx = [_globule(cmp_atoms[m], inputs.SEED_LEARNED + 20000 + m) for m in range(args.learn_cmp)]
+    cphys = [ibim.Phys(1.0, 80.0, float(cmp_kappa[m]), 0.5, 0) for m in range(args.learn_cmp)]
+    couts = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in cctx]
+    bopts = dict(precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=3000)
+    ibim.ibim_solve_batch(cctx, cphys, couts, allow_not_converged=True, **dict(bopts, maxit=2))  # tunes variants
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ib0 = ibim.ibim_solve_batch(cctx, cphys, couts, **bopts)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c, P, o in zip(cctx, cphys, couts):
+        net.predict(c, P, o)
+    ibl = ibim.ibim_solve_batch(cctx, cphys, couts, start=3, **bopts)
+    torch.cuda.synchronize()
+    tbl = time.perf_counter() - t0
+    t64, g64, res64 = 0.0, [], []
+    for c, P, o in zip(cctx, cphys, couts):
+        d64 = torch.empty_like(o)
+        t0 = time.perf_counter()
+        i64 = c.solve(P, d64, precision=ibim.IBIM_F64, tol=1e-6, restart=64, maxit=3000)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t0
+        g64.append(i64["gpol"])
+        g = torch.empty_like(o)
+        c.rhs(1.0, g)
+        ao = torch.empty_like(o)
+        c.matvec(P, o, ao, precision=ibim.IBIM_F64)  # FP64 residual of the batched learned-start solution
+        res64.append(float(torch.linalg.norm(g - ao) / torch.linalg.norm(g)))
+    combined = {
+        "molecules": int(args.learn_cmp), "atoms": [int(args.learn_cmp_lo), int(args.learn_cmp_hi)],
+        "N": [int(c.N) for c in cctx], "f64_plain_s": t64, "f32_batched_zero_s": tb0,
+        "f32_batched_learned_s": tbl, "speedup_vs_f64": t64 / tbl,
+        "iters_zero": [int(i["iters"]) for i in ib0], "iters_learned": [int(i["iters"]) for i in ibl],
+        "fp64_relres_of_learned_batched_max": max(res64),
+        "gpol_rel_diff_vs_f64_max": max(abs(i["gpol"] - g) / abs(g) for i, g in zip(ibl, g64))}
+    for c in cctx:
+        c.close()
     tests = []
     for m in range(args.learn_test):
         ctx = _globule(args.learn_test_atoms, inputs.SEED_LEARNED + 10000 + m)
@@ -562,7 +603,7 @@ def run_learned(args):
             "zero_start_iters_per_solve": z_it / max(1, len(tests)),
             "iters_saved_frac": (z_it - l_it) / max(1, z_it), "time_saved_frac": (z_s - l_s) / max(1e-9, z_s),
             "train": {"examples_s": gen_s, "train_s": train_s, "loss_first": loss0, "loss_last": loss},
-            "tests": tests}
+            "tests": tests, "batched_warm_started_vs_f64": combined}
     print(json.dumps(line), flush=True)
 
 
@@ -624,6 +665,9 @@ def main():
     ap.add_argument("--learn-steps", type=int, default=20000)
     ap.add_argument("--learn-test", type=int, default=2)
     ap.add_argument("--learn-test-atoms", type=int, default=10000)
+    ap.add_argument("--learn-cmp", type=int, default=8, help="held-out globules of the batched comparison")
+    ap.add_argument("--learn-cmp-lo", type=int, default=100)
+    ap.add_argument("--learn-cmp-hi", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -356,8 +356,10 @@ ibim_status ibim_solve_extrapolated(ibim_ctx* ctx, const ibim_phys* phys, const 
  * times each compiled variant of the batched pair kernel (target tiles of
  * 512, 256 and 128 nodes) on its first round and keeps the fastest.
  *   nmol in [1, 1024]; phys: nmol entries (kappa etc. per molecule); opts must
- *   ask for IBIM_F32C, start 0, certify 0; d_p: nmol device pointers, 2 N_m
- *   doubles each (solutions out); infos: nmol entries.
+ *   ask for IBIM_F32C and certify 0, with start 0 (zero start) or 3 (each
+ *   d_p[m] holds the starting vector, e.g. an ibim_wsnet_predict result);
+ *   d_p: nmol device pointers, 2 N_m doubles each (solutions out); infos:
+ *   nmol entries.
  * The call synchronises the contexts' streams.  Returns IBIM_ERR_NOT_CONVERGED
  * (infos filled) when any molecule stopped at maxit above tol.
  */

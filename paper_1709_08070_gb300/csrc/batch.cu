@@ -471,6 +471,13 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
     std::vector<int> want(nmol, 0);
     for (int i = 0; i < nmol; ++i)
         if (gnorm[i] == 0.0) finished[i] = conv[i] = 1;
+    if (o.start == 3)  // the caller's vectors are the starting iterates (a residual round comes first)
+        for (int i = 0; i < nmol; ++i) {
+            if (finished[i]) continue;
+            IBIM_CUDA(cudaMemcpyAsync(ctxs[i]->gm->x, d_p[i], sizeof(double) * 2 * ctxs[i]->N,
+                                      cudaMemcpyDeviceToDevice, R.bs));
+            x_zero[i] = 0;
+        }
 
     for (int cycle_guard = 0; cycle_guard < 1000; ++cycle_guard) {
         // residuals of the molecules that have an iterate

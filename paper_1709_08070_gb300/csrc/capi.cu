@@ -653,8 +653,10 @@ ibim_status ibim_solve_batch(int nmol, ibim_ctx* const* ctxs, const ibim_phys* p
     if (nmol < 1 || nmol > 1024 || ctxs == nullptr || phys == nullptr || o == nullptr || d_p == nullptr ||
         infos == nullptr)
         return fail(IBIM_ERR_ARG, "need 1 <= nmol <= 1024 and non-NULL arrays");
-    if (o->precision != IBIM_F32C || o->start != 0 || o->certify != 0)
-        return fail(IBIM_ERR_ARG, "the batched solve runs the FP32 operator from a zero start without certification");
+    if (o->precision != IBIM_F32C || (o->start != 0 && o->start != 3) || o->certify != 0)
+        return fail(IBIM_ERR_ARG,
+                    "the batched solve runs the FP32 operator without certification, from a zero start (0) or "
+                    "from the vectors in d_p (3)");
     if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
         return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
     for (int i = 0; i < nmol; ++i) {

@@ -64,6 +64,36 @@ def test_batch_matches_single_solves():
             c.close()
 
 
+def test_batch_from_caller_starts():
+    """start = 3: each molecule starts from the vector in its output buffer.
+    From the converged solutions the batch stops at once with the same
+    energies; from a perturbed solution it needs fewer iterations than from
+    zero and reaches the same solution."""
+    mols = _molecules()[:4]
+    try:
+        ctxs = [c for c, _ in mols]
+        physs = [p for _, p in mols]
+        opts = dict(precision=ibim.IBIM_F32C, tol=1e-7, restart=64, maxit=400)
+        ref = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in ctxs]
+        i0 = ibim.ibim_solve_batch(ctxs, physs, ref, **opts)
+        outs = [r.clone() for r in ref]
+        i1 = ibim.ibim_solve_batch(ctxs, physs, outs, start=3, **opts)
+        for a, b, r, o in zip(i0, i1, ref, outs):
+            assert b["converged"] and b["iters"] <= 2, b
+            assert abs(a["gpol"] - b["gpol"]) <= 1e-6 * abs(a["gpol"])
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        outs = [r * (1.0 + 0.05 * torch.randn(r.shape, dtype=torch.float64, device="cuda", generator=gen))
+                for r in ref]
+        i2 = ibim.ibim_solve_batch(ctxs, physs, outs, start=3, **opts)
+        for a, b, r, o in zip(i0, i2, ref, outs):
+            err = float(torch.linalg.norm(o - r) / torch.linalg.norm(r))
+            print("batch start=3 perturbed: iters %d (zero start %d), rel diff %.1e" % (b["iters"], a["iters"], err))
+            assert b["converged"] and b["iters"] < a["iters"] and err < 1e-5
+    finally:
+        for c, _ in mols:
+            c.close()
+
+
 def test_batch_rejects_unsupported_options():
     ctx = ibim.Context.sphere(2.0, h=0.25)
     ctx.set_charges(np.zeros((1, 3)), np.ones(1))
@@ -71,6 +101,9 @@ def test_batch_rejects_unsupported_options():
     P = ibim.Phys(1.0, 80.0, 0.1257, 0.25, 0)
     with pytest.raises(ibim.IbimError) as e:
         ibim.ibim_solve_batch([ctx], [P], [d], precision=ibim.IBIM_F64)
+    assert e.value.status == 1
+    with pytest.raises(ibim.IbimError) as e:
+        ibim.ibim_solve_batch([ctx], [P], [d], start=1)
     assert e.value.status == 1
     with pytest.raises(ibim.IbimError) as e:
         ibim.ibim_solve_batch([ctx, ctx], [P, P], [d, d])
