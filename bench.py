@@ -43,11 +43,16 @@ WORKLOAD = {"workload": "kirkwood_sphere", "R": 20.0, "h": 0.5, "band_k": 2, "ta
 # three MUFU operations (rsqrt, rcp, ex2) run on the XU pipe and are not
 # counted; the per-chunk frame offsets and compensation add about 0.5.
 F32_OPS_PER_INTERACTION = 36
+# The symmetric variants evaluate each unordered source pair once for both
+# directions: the shared part (r, |r|^2, s_x, s_y, c, rho, E, g, the series
+# products, rho^-3, theta terms, hi, qf) is 28 lane-operations and each
+# direction's two sums 10 more, 48 for two interactions.
+F32_OPS_PER_INTERACTION_SYM = 24
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this
-# workload, by variant (targets/thread, min CTAs/SM, threads/CTA), from the ncu
+# workload, by variant (targets/thread, min CTAs/SM, threads/CTA, symmetric), from the ncu
 # full-set capture summarised in profiles/pair_f32_kernel_kirkwood80k.md.
-NCU_TRAFFIC_BYTES = {(2, 1, 512): 5.686272e6}
+NCU_TRAFFIC_BYTES = {(2, 1, 512, 0): 5.686272e6}
 METRIC = "IBIM matvec interactions/s"
 
 
@@ -220,7 +225,7 @@ def run_ours(args):
     N = ctx.N
     P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
     variant, bps, tune_ms = ctx.autotune(P)
-    tpt, minb, nthr = ibim.ibim_f32_variants()[variant]
+    tpt, minb, nthr, sym = ibim.ibim_f32_variants()[variant]
     opts = dict(precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=1000, start=0, certify=0)
     dp = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -264,10 +269,11 @@ def run_ours(args):
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
     avg_pair_ms = tim["pair_ms"] / max(1, tim["pair_launches"])
     per_launch = tim["pair_interactions"] / max(1, tim["pair_launches"])
-    achieved_ops = F32_OPS_PER_INTERACTION * per_launch / (avg_pair_ms * 1e-3)
+    ops_per = F32_OPS_PER_INTERACTION_SYM if sym else F32_OPS_PER_INTERACTION
+    achieved_ops = ops_per * per_launch / (avg_pair_ms * 1e-3)
     roofline = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": achieved_ops / peak_ops, "traffic": NCU_TRAFFIC_BYTES.get((tpt, minb, nthr)),
-                "kernel": "pair_f32_kernel", "ops_per_interaction": F32_OPS_PER_INTERACTION,
+                "frac": achieved_ops / peak_ops, "traffic": NCU_TRAFFIC_BYTES.get((tpt, minb, nthr, sym)),
+                "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel", "ops_per_interaction": ops_per,
                 "interactions_per_launch": per_launch, "avg_launch_ms": avg_pair_ms,
                 "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock, measured peaks file)" % (
                     props.multi_processor_count, FP32_LANES_PER_SM, sm_max)}
@@ -340,7 +346,7 @@ def run_ours(args):
                 "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
                                l2="256 MB buffer written between timed steps",
                                f32_variant={"index": variant, "targets_per_thread": tpt, "min_ctas_per_sm": minb,
-                                            "threads_per_cta": nthr, "ctas_per_sm": bps}),
+                                            "threads_per_cta": nthr, "symmetric": sym, "ctas_per_sm": bps}),
                 "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
                 "wall_s_timed": wall}
         line.update(extra)

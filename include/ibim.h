@@ -282,11 +282,17 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
  * FP32 pair-kernel variants (a GPU tuning device, not part of the paper's
  * method).  The library compiles a small table of variants, each with a fixed
  * number of targets per thread, a register budget (minimum CTAs per SM) and
- * a CTA size; ibim_f32_variant_info describes entry v of
- * [0, ibim_f32_variant_count()) (outputs may be NULL).
+ * a CTA size, and whether it is the symmetric kernel (each unordered node
+ * pair evaluated once for both ordered pairs; its reverse sums are added with
+ * FP32 shared-memory and FP64 global atomics in a varying order, so its
+ * result varies from run to run at the FP32 rounding level of one tile's
+ * partial sum, a few 1e-10 of max |y|);
+ * ibim_f32_variant_info describes entry v of [0, ibim_f32_variant_count())
+ * (outputs may be NULL).
  */
 int ibim_f32_variant_count(void);
-ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm, int* threads_per_cta);
+ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm, int* threads_per_cta,
+                                  int* symmetric);
 
 /*
  * Autotuner: times every variant on this context's geometry with CUDA events,

@@ -166,13 +166,15 @@ ibim_status ensure_operator_workspaces(ibim_ctx* c)
                     std::max((size_t)N * 8 * sizeof(double), (size_t)padded_nodes(N) * 2 * sizeof(float4))));
     const PairSchedule s64 = make_schedule(N, kF64TTile, N, kF64STile, f64_grid_cap(c));
     size_t need = (size_t)s64.grid * s64.max_segs * 2 * kF64TTile * sizeof(double);
-    const int keep = c->f32_variant;
+    const int keep = c->f32_variant, keep_bps = c->f32_bps;
+    c->f32_bps = 0;
     for (int v = 0; v < f32_variant_count(); ++v) {
         c->f32_variant = v;
-        const PairSchedule s = f32_schedule(c);
-        need = std::max(need, (size_t)s.grid * s.max_segs * 2 * f32_ttile(c) * sizeof(double));
+        need = std::max(need, f32_part_doubles(c) * sizeof(double));
     }
     c->f32_variant = keep;
+    c->f32_bps = keep_bps;
+    IBIM_TRY(ensure(c, (void**)&c->d_yrev, &c->yrev_bytes, sym_yrev_bytes(N)));
     IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, need));
     c->ws_sized = true;
     return IBIM_OK;
@@ -266,6 +268,7 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_err);
     cudaFree(c->d_io);
     cudaFree(c->d_aux);
+    cudaFree(c->d_yrev);
     cudaFree(c->d_phi);
     delete c;
 }

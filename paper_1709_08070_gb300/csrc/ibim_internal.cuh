@@ -143,6 +143,8 @@ struct ibim_ctx {
     size_t io_bytes = 0;
     double* d_aux = nullptr;   // the tau solution of an extrapolated solve
     size_t aux_bytes = 0;
+    double* d_yrev = nullptr;  // reverse sums of the symmetric FP32 kernel (2 x padded N) + segment counter
+    size_t yrev_bytes = 0;
     ibim::GmresWork* gm = nullptr;
     ibim::Timing timing;
     // incremented whenever a workspace is reallocated: CUDA graphs captured
@@ -193,7 +195,18 @@ int f32_grid_cap(ibim_ctx* c);
 int f32_ttile(const ibim_ctx* c);
 int f32_max_bps(int variant);
 int f32_variant_count();
-void f32_variant_info(int v, int* tpt, int* minb, int* threads);
+void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric);
+size_t f32_part_doubles(ibim_ctx* c);  // partial-sum doubles of the current variant and grid
+// symmetric FP32 pair kernel (pair_sym.cu)
+int sym_variant_count();
+void sym_variant_info(int v, int* tpt, int* minb, int* threads);
+int sym_occupancy(int v);
+size_t sym_part_doubles(int64_t N, int ttile, int grid_cap);
+size_t sym_yrev_bytes(int64_t N);
+ibim_status sym_pack(ibim_ctx* c, VecRef in, const int* d_skip);
+ibim_status sym_pairs(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, const int* d_skip);
+ibim_status sym_fixup(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, VecRef in, OutRef out,
+                      const int* d_skip);
 PairSchedule f32_schedule(ibim_ctx* c);
 ibim_status f32_chunk_frames(ibim_ctx* c);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,

@@ -299,16 +299,26 @@ static const F32Variant kVariants[] = {
 #undef IBIM_F32_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
-int f32_variant_count() { return kNumVariants; }
-void f32_variant_info(int v, int* tpt, int* minb, int* threads)
+// Variants kNumVariants.. are the symmetric kernel's (pair_sym.cu).
+int f32_variant_count() { return kNumVariants + sym_variant_count(); }
+static bool is_sym(int v) { return v >= kNumVariants; }
+
+void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric)
 {
+    if (is_sym(v)) {
+        sym_variant_info(v - kNumVariants, tpt, minb, threads);
+        *symmetric = 1;
+        return;
+    }
     *tpt = kVariants[v].tpt;
     *minb = kVariants[v].minb;
     *threads = kVariants[v].threads;
+    *symmetric = 0;
 }
 
 static int occupancy_of(int v)
 {
+    if (is_sym(v)) return sym_occupancy(v - kNumVariants);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kVariants[v].fn, kVariants[v].threads, 0);
     return occ < 1 ? 1 : occ;
@@ -316,13 +326,26 @@ static int occupancy_of(int v)
 
 int f32_max_bps(int v) { return occupancy_of(v); }
 
-int f32_ttile(const ibim_ctx* c) { return kVariants[c->f32_variant].threads * kVariants[c->f32_variant].tpt; }
+int f32_ttile(const ibim_ctx* c)
+{
+    int tpt, minb, threads, sym;
+    f32_variant_info(c->f32_variant, &tpt, &minb, &threads, &sym);
+    return threads * tpt;
+}
 
 int f32_grid_cap(ibim_ctx* c)
 {
     const int occ = occupancy_of(c->f32_variant);
     const int bps = (c->f32_bps > 0 && c->f32_bps < occ) ? c->f32_bps : occ;
     return bps * c->num_sms;
+}
+
+// Partial-sum doubles the current variant needs.
+size_t f32_part_doubles(ibim_ctx* c)
+{
+    if (is_sym(c->f32_variant)) return sym_part_doubles(c->N, f32_ttile(c), f32_grid_cap(c));
+    const PairSchedule s = make_schedule(c->N, f32_ttile(c), c->N, kF32STile, f32_grid_cap(c));
+    return (size_t)s.grid * s.max_segs * 2 * f32_ttile(c);
 }
 
 PairSchedule f32_schedule(ibim_ctx* c)
@@ -346,6 +369,10 @@ ibim_status f32_pack(ibim_ctx* c, VecRef in, const int* d_skip)
     const int64_t N = c->N;
     const int64_t n_pairs = padded_nodes(N) / 2;
     IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes, (size_t)n_pairs * kPairF4 * sizeof(float4)));
+    if (is_sym(c->f32_variant)) {
+        IBIM_TRY(ensure(c, (void**)&c->d_yrev, &c->yrev_bytes, sym_yrev_bytes(N)));
+        return sym_pack(c, in, d_skip);
+    }
     const double* w = c->d_geo64 + 6 * N;
     const int bs = 256;
     pack_f32_kernel<<<(unsigned)((n_pairs + bs - 1) / bs), bs, 0, c->stream>>>(
@@ -357,9 +384,8 @@ ibim_status f32_pack(ibim_ctx* c, VecRef in, const int* d_skip)
 
 ibim_status f32_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, const int* d_skip)
 {
-    const int ttile = f32_ttile(c);
-    const size_t need = (size_t)s.grid * s.max_segs * 2 * ttile * sizeof(double);
-    IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, need));
+    IBIM_TRY(ensure(c, (void**)&c->d_part, &c->part_bytes, f32_part_doubles(c) * sizeof(double)));
+    if (is_sym(c->f32_variant)) return sym_pairs(c, c->f32_variant - kNumVariants, f32_grid_cap(c), k, d_skip);
     const PairArgs a{c->d_pos32, c->d_nrm32, (const float4*)c->d_src, c->d_frames, c->N, s, f32_consts(k),
                      c->d_part, c->d_err, d_skip, Geo64{c->d_geo64, c->d_geo64 + 3 * c->N, 1, c->N}};
     kVariants[c->f32_variant].launch(a, c->stream);
@@ -382,6 +408,8 @@ ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s
 ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, VecRef in, OutRef out,
                       const int* d_skip)
 {
+    if (is_sym(c->f32_variant))
+        return sym_fixup(c, c->f32_variant - kNumVariants, f32_grid_cap(c), k, in, out, d_skip);
     return fixup_launch(c, k, s, f32_ttile(c), in, out, d_skip);
 }
 

@@ -46,17 +46,18 @@ using namespace ibim;
 extern "C" int ibim_f32_variant_count(void) { return f32_variant_count(); }
 
 extern "C" ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_per_sm,
-                                            int* threads_per_cta)
+                                            int* threads_per_cta, int* symmetric)
 {
     if (v < 0 || v >= f32_variant_count()) {
         set_error("variant index out of range");
         return IBIM_ERR_ARG;
     }
-    int t = 0, m = 0, w = 0;
-    f32_variant_info(v, &t, &m, &w);
+    int t = 0, m = 0, w = 0, y = 0;
+    f32_variant_info(v, &t, &m, &w, &y);
     if (targets_per_thread) *targets_per_thread = t;
     if (min_ctas_per_sm) *min_ctas_per_sm = m;
     if (threads_per_cta) *threads_per_cta = w;
+    if (symmetric) *symmetric = y;
     return IBIM_OK;
 }
 

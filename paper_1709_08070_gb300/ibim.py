@@ -84,7 +84,7 @@ _SIGS = {
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
     "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                              ctypes.POINTER(ctypes.c_int)],
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
     "ibim_get_levelset": [_V, _I64P, _I64P, _D],
     "ibim_solve_batch": [ctypes.c_int, ctypes.POINTER(_V), ctypes.POINTER(Phys), ctypes.POINTER(SolveOpts),
@@ -351,14 +351,12 @@ def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=Non
 
 
 def ibim_f32_variants():
-    """[(targets_per_thread, min_ctas_per_sm, threads_per_cta)] of the compiled FP32 variants."""
+    """[(targets_per_thread, min_ctas_per_sm, threads_per_cta, symmetric)] of the compiled FP32 variants."""
     out = []
     for v in range(lib().ibim_f32_variant_count()):
-        t = ctypes.c_int(0)
-        m = ctypes.c_int(0)
-        w = ctypes.c_int(0)
-        _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m), ctypes.byref(w)))
-        out.append((t.value, m.value, w.value))
+        t, m, w, y = (ctypes.c_int(0) for _ in range(4))
+        _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m), ctypes.byref(w), ctypes.byref(y)))
+        out.append((t.value, m.value, w.value, y.value))
     return out
 
 

@@ -282,13 +282,13 @@ def test_every_fp32_variant_matches_fp64():
     ctx.matvec(P, p, y64, precision=F64)
     a = y64.cpu().numpy()
     y32 = torch.empty_like(p)
-    for v, (tpt, minb, nthr) in enumerate(ibim.ibim_f32_variants()):
+    for v, (tpt, minb, nthr, sym) in enumerate(ibim.ibim_f32_variants()):
         for bps in (0, 1):
             ctx.set_f32_variant(v, bps)
             ctx.matvec(P, p, y32, precision=F32)
             torch.cuda.synchronize()
             r = _both_blocks(y32.cpu().numpy(), a, N)
-            assert max(r) < 1e-6, (v, tpt, minb, nthr, bps, r)
+            assert max(r) < 1e-6, (v, tpt, minb, nthr, sym, bps, r)
     ctx.close()
 
 
@@ -319,3 +319,63 @@ def test_built_geometries_have_compact_32_node_blocks():
     # of its neighbourhood (leaves are cut by count); nearly all are compact
     assert np.median(r) < 1.5 and frac < 0.03, (np.median(r), frac)
     ctx.close()
+
+
+def test_symmetric_kernel_all_rows_against_fp64():
+    """The symmetric FP32 kernel (each unordered pair evaluated once for both
+    directions) on every row of the 80k sphere and of a level-set globule,
+    against the FP64 operator: same bar as the one-directional kernel."""
+    sym = [v for v, info in enumerate(ibim.ibim_f32_variants()) if info[3]]
+    assert sym
+    z, r, q = inputs.globule_atoms(300, seed=9)
+    for ctx in (ibim.Context.sphere(KIRK["R"], h=KIRK["h"], band_eps=KIRK["k"] * KIRK["h"]),
+                ibim.Context.molecule(z, r, q, probe=1.4, h=0.5)):
+        N = ctx.N
+        for kappa in (0.1257, 0.0):
+            P, _ = _phys(2.0, 80.0, kappa, 0.5)
+            p = _dev(inputs.random_vector(2 * N, seed=1))
+            y64 = torch.empty_like(p)
+            ctx.matvec(P, p, y64, precision=F64)
+            a = y64.cpu().numpy()
+            for v in sym:
+                for bps in (0, 1):
+                    ctx.set_f32_variant(v, bps)
+                    y32 = torch.empty_like(p)
+                    ctx.matvec(P, p, y32, precision=F32)
+                    b = y32.cpu().numpy()
+                    rr = _both_blocks(b, a, N)
+                    worst = np.max(np.abs(b - a)) / np.max(np.abs(a))
+                    print("symmetric v%d bps %d N %d kappa %g: rel %.2e %.2e %.2e worst %.2e" % (v, bps, N, kappa,
+                                                                                            *rr, worst))
+                    assert max(rr) < 1e-6 and worst < 1e-5, (v, bps, N, kappa, rr, worst)
+        ctx.close()
+
+
+def test_symmetric_kernel_small_ragged_and_repeated():
+    """Symmetric variants on node counts with fewer steps than CTAs, a single
+    tile and a ragged last tile, against FP64; repeated calls agree to the
+    FP32 rounding of one tile's reverse partial (the atomic order of the
+    reverse sums is the only run-to-run change; a segment counter that was not
+    reset would drop a tenth of the steps)."""
+    sym = [v for v, info in enumerate(ibim.ibim_f32_variants()) if info[3]]
+    P, _ = _phys(2.0, 80.0, 0.1257, 0.3)
+    for n in (40, 700, 5000):
+        xs, nr, w = inputs.sphere_cloud(n, radius=4.0 + n / 2000.0, seed=n)
+        ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
+        N = ctx.N
+        p = _dev(inputs.random_vector(2 * N, seed=5))
+        y64 = torch.empty_like(p)
+        ctx.matvec(P, p, y64, precision=F64)
+        a = y64.cpu().numpy()
+        for v in sym:
+            ctx.set_f32_variant(v, 0)
+            outs = []
+            for _ in range(3):
+                y32 = torch.empty_like(p)
+                ctx.matvec(P, p, y32, precision=F32)
+                outs.append(y32.cpu().numpy())
+            r = _both_blocks(outs[0], a, N)
+            assert max(r) < 1e-6, (n, v, r)
+            for o in outs[1:]:
+                assert np.max(np.abs(o - outs[0])) <= 1e-8 * np.max(np.abs(outs[0])), (n, v)
+        ctx.close()
