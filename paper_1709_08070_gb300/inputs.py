@@ -5,6 +5,8 @@ numbers (charge positions and values, atom chains, node clouds, vectors) with
 numpy's seeded generators.  Everything the method computes from these inputs
 is done separately by the CUDA library and by the oracle.
 """
+import math
+
 import numpy as np
 
 # Seeds of the five standard workloads (Born sphere, Kirkwood sphere, 2,000-atom
@@ -52,6 +54,55 @@ def sphere_cloud(n, radius=10.0, jitter=0.0, seed=0, weight_range=(0.01, 0.06)):
     w = rng.uniform(weight_range[0], weight_range[1], size=n)
     key = np.lexsort((np.floor(u[:, 0] * 8), np.floor(u[:, 1] * 8), np.floor(u[:, 2] * 8)))
     return xs[key], u[key], w[key]
+
+
+def bisection_order(xs):
+    """Permutation that orders points by recursive coordinate bisection: each
+    range of n points is split across the longest side of its bounding box,
+    the left part a multiple of B points (B = 1024 for n >= 2048, 256 for
+    n >= 512, else 32; about half the range), down to 32 points, so that
+    aligned runs of 32, 256 and 1024 indices are compact (input preparation
+    for caller-ordered clouds; ties broken by the original index)."""
+    xs = np.asarray(xs, dtype=np.float64)
+    perm = np.arange(xs.shape[0])
+    stack = [(0, xs.shape[0])]
+    while stack:
+        lo, hi = stack.pop()
+        n = hi - lo
+        if n <= 32:
+            continue
+        B = 1024 if n >= 2048 else (256 if n >= 512 else 32)
+        k = B * max(1, int(math.floor(n / (2.0 * B) + 0.5)))
+        seg = xs[perm[lo:hi]]
+        ax = int(np.argmax(seg.max(axis=0) - seg.min(axis=0)))
+        order = np.lexsort((perm[lo:hi], seg[:, ax]))
+        perm[lo:hi] = perm[lo:hi][order]
+        stack.append((lo + k, hi))
+        stack.append((lo, lo + k))
+    return perm
+
+
+def compact_sphere_cloud(n, radius=10.0, seed=0, weight_range=(0.01, 0.06)):
+    """sphere_cloud(n, radius) reordered by bisection_order, so that aligned
+    blocks of consecutive indices are compact patches of the sphere."""
+    xs, u, w = sphere_cloud(n, radius=radius, seed=seed, weight_range=weight_range)
+    perm = bisection_order(xs)
+    return xs[perm], u[perm], w[perm]
+
+
+def sphere_cluster_cloud(n_per, centres, radius=5.0, seed=0, weight_range=(0.01, 0.06)):
+    """Several node spheres (n_per points each, the given centres and radius),
+    concatenated and ordered by bisection_order: a caller-ordered cloud whose
+    parts are far apart compared with a 1024-node tile."""
+    parts = []
+    for q, c in enumerate(np.asarray(centres, dtype=np.float64)):
+        xs, u, w = sphere_cloud(n_per, radius=radius, seed=seed + q, weight_range=weight_range)
+        parts.append((xs + c[None, :], u, w))
+    xs = np.concatenate([a for a, _, _ in parts])
+    u = np.concatenate([b for _, b, _ in parts])
+    w = np.concatenate([c for _, _, c in parts])
+    perm = bisection_order(xs)
+    return xs[perm], u[perm], w[perm]
 
 
 def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, beta=100.0, n_cand=128,

@@ -1,0 +1,142 @@
+"""Pins of the treecode oracle (oracle/treecode.py) to facts outside itself.
+
+* Tensor-product Lagrange interpolation on Chebyshev points reproduces
+  polynomials of degree n - 1 per axis and is the identity on its own points.
+* Interpolating a parent cube's basis on a child cube's points is exact (the
+  identity that lets a GPU build parent proxies from child proxies).
+* The far-field kernels written as linear functions of the densities equal the
+  C oracle's pair kernels (Sec. 2.2) for a single unit-normal source.
+* With no far cluster the treecode is the direct operator.
+* Every source tile is covered exactly once per target tile (near tile or
+  inside exactly one far cluster).
+* The error against the direct operator falls with the number of Chebyshev
+  points and stays small.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import treecode as tc
+from paper_1709_08070_gb300 import inputs
+
+CENTRES = [(28.0 * i, 28.0 * j, 0.0) for i in range(3) for j in range(3)]
+
+
+def _cloud(n_per=1000, radius=5.0, seed=4):
+    return inputs.sphere_cluster_cloud(n_per, CENTRES, radius=radius, seed=seed)
+
+
+def test_lagrange_reproduces_polynomials_and_is_identity_on_points():
+    rng = np.random.default_rng(0)
+    centre, half = np.array([1.5, -2.0, 0.25]), 3.0
+    for n in (3, 4, 6):
+        t = tc.proxy_points(centre, half, n)
+        M = tc.interp_matrix(t, centre, half, n)
+        np.testing.assert_allclose(M, np.eye(n ** 3), atol=1e-13)
+        C = rng.standard_normal((n, n, n))  # coefficients of x^i y^j z^k, i, j, k < n
+
+        def poly(P):
+            u = (P - centre) / half
+            V = [np.stack([u[:, a] ** e for e in range(n)], axis=1) for a in range(3)]
+            return np.einsum("pi,pj,pk,ijk->p", V[0], V[1], V[2], C)
+
+        y = centre + half * rng.uniform(-1.0, 1.0, size=(200, 3))
+        interp = tc.interp_matrix(y, centre, half, n) @ poly(t)
+        np.testing.assert_allclose(interp, poly(y), rtol=0, atol=1e-11 * np.abs(poly(y)).max())
+
+
+def test_child_to_parent_transfer_is_exact():
+    rng = np.random.default_rng(1)
+    n = 6
+    pc, ph = np.zeros(3), 4.0
+    cc, chh = np.array([1.0, -1.5, 0.5]), 1.7
+    y = cc + chh * rng.uniform(-1.0, 1.0, size=(50, 3))
+    tchild = tc.proxy_points(cc, chh, n)
+    direct = tc.interp_matrix(y, pc, ph, n)  # L^p_l(y)
+    via = tc.interp_matrix(y, cc, chh, n) @ tc.interp_matrix(tchild, pc, ph, n)
+    np.testing.assert_allclose(via, direct, rtol=0, atol=1e-12)
+
+
+def test_far_kernels_match_pair_kernels_for_unit_sources():
+    rng = np.random.default_rng(2)
+    for kappa, eps_in in ((0.1257, 2.0), (0.0, 1.0), (0.5, 4.0)):
+        P = oracle.Phys(eps_in, 80.0, kappa, 0.3)
+        x = rng.standard_normal((3, 3)) * 2.0
+        nx = rng.standard_normal((3, 3))
+        nx /= np.linalg.norm(nx, axis=1, keepdims=True)
+        y = x[0] + np.array([6.0, 1.0, -2.0]) + rng.standard_normal((4, 3))
+        m = rng.standard_normal((4, 3))
+        m /= np.linalg.norm(m, axis=1, keepdims=True)
+        a, b = rng.uniform(-1, 1, 4), rng.uniform(-1, 1, 4)
+        f1, f2 = tc.far_kernels(x, nx, y, a[:, None] * m, b, P)
+        for i in range(3):
+            e1 = e2 = 0.0
+            for j in range(4):
+                K, tube = oracle.pair_kernels(x[i], nx[i], y[j], m[j], P)
+                assert not tube
+                e1 += K[0] * a[j] - K[1] * b[j]
+                e2 += K[2] * a[j] - K[3] * b[j]
+            np.testing.assert_allclose([f1[i], f2[i]], [e1, e2], rtol=1e-12, atol=1e-15)
+
+
+def test_no_far_cluster_is_the_direct_operator():
+    xs, nr, w = _cloud(n_per=400)
+    N = xs.shape[0]
+    P = oracle.Phys(2.0, 80.0, 0.1257, 0.3)
+    p = inputs.random_vector(2 * N, seed=3)
+    tree = tc.TileTree(xs)
+    lists = tree.lists(1e-9, 0.3)
+    assert tc.list_sizes(lists)[1] == 0
+    y = tc.treecode_matvec(xs, nr, w, P, p, tree=tree, lists=lists)
+    ye = oracle.matvec(xs, nr, w, P, p)
+    np.testing.assert_allclose(y, ye, rtol=0, atol=1e-13 * np.abs(ye).max())
+
+
+def test_every_source_tile_once_per_target_tile():
+    xs, nr, w = _cloud(n_per=1000)
+    tree = tc.TileTree(xs)
+    tiles = set(range(tree.n_s))
+    for theta in (0.4, 0.7, 1.0):
+        lists = tree.lists(theta, 0.3)
+        assert tc.list_sizes(lists)[1] > 0
+        for near, far in lists:
+            seen = list(near)
+            for ci in far:
+                c = tree.clusters[ci]
+                assert c.j0 % tree.stile == 0
+                seen += list(range(c.j0 // tree.stile, -(-c.j1 // tree.stile)))
+            assert sorted(seen) == sorted(tiles)
+
+
+def test_far_clusters_keep_proxies_out_of_the_tube():
+    xs, nr, w = _cloud(n_per=1000)
+    tree = tc.TileTree(xs)
+    tau = 0.4
+    fd = max(2 * tau, 1.5) * 1.001 + 1e-3
+    for t, (near, far) in enumerate(tree.lists(0.8, tau)):
+        tx = xs[t * tree.ttile:min((t + 1) * tree.ttile, tree.N)]
+        for ci in far:
+            c = tree.clusters[ci]
+            pr = tc.proxy_points(c.centre, c.half, 6)
+            dmin = np.sqrt(((tx[:, None, :] - pr[None, :, :]) ** 2).sum(-1)).min()
+            assert dmin >= fd
+
+
+@pytest.mark.parametrize("theta", [0.6])
+def test_error_falls_with_the_chebyshev_order(theta):
+    xs, nr, w = _cloud(n_per=1000)
+    N = xs.shape[0]
+    P = oracle.Phys(2.0, 80.0, 0.1257, 0.3)
+    p = inputs.random_vector(2 * N, seed=1)
+    ye = oracle.matvec(xs, nr, w, P, p)
+    tree = tc.TileTree(xs)
+    lists = tree.lists(theta, 0.3)
+    assert tc.list_sizes(lists)[1] > 0
+    errs = []
+    for n in (3, 4, 6):
+        y = tc.treecode_matvec(xs, nr, w, P, p, n=n, tree=tree, lists=lists)
+        errs.append(max(np.linalg.norm(y[:N] - ye[:N]) / np.linalg.norm(ye[:N]),
+                        np.linalg.norm(y[N:] - ye[N:]) / np.linalg.norm(ye[N:])))
+    print("treecode error vs direct, theta %.1f, n = 3, 4, 6: %s" % (theta, ["%.2e" % e for e in errs]))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-7
