@@ -48,7 +48,9 @@ typedef enum {
 /* Arithmetic of the pair sums (the N x N kernel evaluations). */
 typedef enum {
     IBIM_F64 = 64,  /* plain FP64 pair sums */
-    IBIM_F32C = 32  /* FP32 pair sums, Kahan-compensated per source tile, tile sums in FP64 */
+    IBIM_F32C = 32, /* FP32 pair sums, Kahan-compensated per source tile, tile sums in FP64 */
+    IBIM_F32T = 33  /* as IBIM_F32C near each target tile, far clusters through Chebyshev
+                       proxies (ibim_treecode_setup first; tube rule 0 only) */
 } ibim_precision;
 
 /*
@@ -169,7 +171,7 @@ ibim_status ibim_get_jacobian(const ibim_ctx* ctx, double* J);
  *   y1_i = lambda1 psi_i  + sum_j [K11(i,j) w_j psi_j - K12(i,j) w_j psin_j]
  *   y2_i = lambda2 psin_i + sum_j [K21(i,j) w_j psi_j - K22(i,j) w_j psin_j]
  * d_in, d_out: device, 2N doubles each, must not overlap.  Asynchronous on
- * the context stream.  precision: IBIM_F64 or IBIM_F32C.
+ * the context stream.  precision: IBIM_F64, IBIM_F32C or IBIM_F32T.
  */
 ibim_status ibim_matvec(ibim_ctx* ctx, const ibim_phys* phys, int precision, const double* d_in,
                         double* d_out);
@@ -197,7 +199,7 @@ ibim_status ibim_area(ibim_ctx* ctx, double* area);
 /* ------------------------------------------------------------------ solve */
 
 typedef struct {
-    int precision;  /* IBIM_F64 or IBIM_F32C: operator used inside GMRES                */
+    int precision;  /* IBIM_F64, IBIM_F32C or IBIM_F32T: operator used inside GMRES  */
     double tol;     /* relative residual ||g - A p||_2 / ||g||_2 target (e.g. 1e-6)      */
     int maxit;      /* maximum Arnoldi steps in total                                    */
     int restart;    /* GMRES restart length m (1..128)                                   */
@@ -277,6 +279,46 @@ ibim_status ibim_wsnet_predict(ibim_wsnet* net, ibim_ctx* ctx, const ibim_phys* 
 void ibim_wsnet_destroy(ibim_wsnet* net);
 
 /* ---------------------------------------------------------------- tuning */
+
+/*
+ * Treecode form of the operator (far-field acceleration; the paper's own
+ * accelerator is a black-box FMM built on Chebyshev interpolation, Sec. 4).
+ * Every kernel of the discrete system (Sec. 2.2) is linear in the source's
+ * densities d_j = a_j m_j and b_j (a_j = w_j psi_j, b_j = w_j psin_j), so a
+ * cluster of sources far from a target tile is replaced by the 216 proxies
+ * (6 Chebyshev points of the second kind per axis) of its bounding cube,
+ * carrying D_k = sum_j L_k(y_j) d_j and beta_k = sum_j L_k(y_j) b_j (L_k the
+ * tensor-product Lagrange basis).  Near sources are summed as in IBIM_F32C,
+ * tube rule included.
+ *
+ * ibim_treecode_setup builds the tree and the interaction lists of the
+ * context's current nodes:
+ *   - clusters are node ranges split as the coordinate bisection of built
+ *     geometries splits them (left part B max(1, round(n / 2B)), B = 1024 for
+ *     n >= 2048, 256 otherwise), down to 256-node tiles; target tiles have
+ *     1024 nodes;
+ *   - a cluster is far from a target tile when r_T + r_C <= theta D and
+ *     D >= max(2 tau_max, 1.5) 1.001 + 1e-3 + r_T + r_C + 0.25 (Angstrom;
+ *     D the distance of the box centres, r_T the tile's box half-diagonal,
+ *     r_C the proxy cube's half-diagonal), so no proxy lies in the
+ *     regularisation tube (Sec. 2.2.1) of any target.
+ * theta in (0, 1) (smaller: more accurate and slower; 0.5-0.8 give relative
+ * operator errors of about 1e-9 to 1e-7); tau_max > 0 is the largest tau the
+ * operator will be applied with.  Allocates device memory on the context
+ * (released by ibim_destroy or a new setup); synchronises the context stream.
+ * Caller nodes should be ordered so that runs of consecutive indices are
+ * compact (built geometries are).  Applying IBIM_F32T with tau > tau_max or
+ * tube_rule 1 returns IBIM_ERR_ARG; before any setup, IBIM_ERR_STATE.
+ * Errors: IBIM_ERR_ARG (NULL context, theta or tau_max out of range),
+ * IBIM_ERR_STATE (no nodes), IBIM_ERR_CUDA.
+ *
+ * ibim_treecode_info: list sizes of the current setup (outputs may be NULL):
+ * near source-tile steps, far cluster steps (each step is 1024 targets x 256
+ * sources or proxies), clusters, target tiles.  IBIM_ERR_STATE before setup.
+ */
+ibim_status ibim_treecode_setup(ibim_ctx* ctx, double theta, double tau_max);
+ibim_status ibim_treecode_info(ibim_ctx* ctx, int64_t* near_steps, int64_t* far_steps, int64_t* clusters,
+                               int64_t* target_tiles);
 
 /*
  * FP32 pair-kernel variants (a GPU tuning device, not part of the paper's

@@ -25,9 +25,11 @@ Structure (the tiling is chosen so that a GPU can stream proxies like sources):
     n > 256 nodes into a left part of B max(1, round(n / 2B)) nodes, B = 1024
     for n >= 2048 and 256 otherwise, down to single tiles (for nodes ordered by
     that bisection every cluster is one of its ranges);
-  * proxy cube of a cluster: centred on the centre of its nodes' bounding box,
-    half side the largest half extent (at least kMinHalf), n^3 Chebyshev
-    points of the second kind, radius = half side x sqrt(3);
+  * proxy cube of a cluster: the smallest axis box holding its nodes and its
+    children's cubes, made a cube about the box centre with the largest half
+    extent (at least kMinHalf) as half side, so every cube lies inside its
+    parent's; n^3 Chebyshev points of the second kind, radius = half side x
+    sqrt(3);
   * target tiles of 1024 consecutive nodes, bounding box centre and
     half-diagonal r_T;
   * a cluster is far from a target tile when r_T + r_C <= theta D and
@@ -137,14 +139,20 @@ class TileTree:
         c.j0, c.j1, c.children = j0, j1, ()
         idx = len(self.clusters)
         self.clusters.append(c)
-        mn, mx = self._box(j0, j1)
-        c.centre = 0.5 * (mn + mx)
-        e = 0.5 * (mx - mn)
-        c.half = max(max(e[0], e[1], e[2]), kMinHalf)
-        c.radius = math.sqrt(3.0 * c.half * c.half)
         if j1 - j0 > self.stile:
             k = split_point(j1 - j0)
             c.children = (self._make(j0, j0 + k), self._make(j0 + k, j1))
+        mn, mx = self._box(j0, j1)
+        mn, mx = [float(v) for v in mn], [float(v) for v in mx]
+        for ci in c.children:
+            q = self.clusters[ci]
+            for a in range(3):
+                mn[a] = min(mn[a], q.centre[a] - q.half)
+                mx[a] = max(mx[a], q.centre[a] + q.half)
+        c.centre = np.array([0.5 * (mn[a] + mx[a]) for a in range(3)])
+        e = [0.5 * (mx[a] - mn[a]) for a in range(3)]
+        c.half = max(max(e[0], e[1], e[2]), kMinHalf)
+        c.radius = math.sqrt(3.0 * c.half * c.half)
         return idx
 
     def far(self, t, ci, theta, far_dist):

@@ -18,8 +18,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libibim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-file extra flags: the level-set stencils are compiled without FMA
-# contraction so that their FP64 rounding follows plain C arithmetic.
-FILE_FLAGS = {"levelset.cu": ["-fmad=false"]}
+# contraction so that their FP64 rounding follows plain C arithmetic, and the
+# treecode's host-side list builder likewise (its far/near decisions then
+# depend on plain IEEE arithmetic on every host).
+FILE_FLAGS = {"levelset.cu": ["-fmad=false"], "treecode.cu": ["-Xcompiler", "-ffp-contract=off"]}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
 

@@ -194,6 +194,7 @@ ibim_status apply_operator(ibim_ctx* c, const PairConsts& k, int precision, VecR
         IBIM_TRY(timing_end(c, N * N));
         return f32_fixup(c, k, s, in, out, d_skip);
     }
+    if (precision == IBIM_F32T) return tc_apply(c, k, in, out, d_skip);
     if (precision == IBIM_F64) {
         const PairSchedule s = make_schedule(N, kF64TTile, N, kF64STile, f64_grid_cap(c));
         IBIM_TRY(f64_pack(c, in, d_skip));
@@ -202,7 +203,7 @@ ibim_status apply_operator(ibim_ctx* c, const PairConsts& k, int precision, VecR
         IBIM_TRY(timing_end(c, N * N));
         return f64_fixup(c, k, s, in, out, d_skip);
     }
-    return fail(IBIM_ERR_ARG, "precision must be IBIM_F64 (64) or IBIM_F32C (32)");
+    return fail(IBIM_ERR_ARG, "precision must be IBIM_F64 (64), IBIM_F32C (32) or IBIM_F32T (33)");
 }
 
 // Reads the device error word after a synchronisation point.
@@ -269,6 +270,7 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_io);
     cudaFree(c->d_aux);
     cudaFree(c->d_yrev);
+    ibim::tc_destroy(c->tc);
     cudaFree(c->d_phi);
     delete c;
 }
@@ -561,7 +563,7 @@ ibim_status ibim_energy(ibim_ctx* c, const ibim_phys* phys, int precision, const
 {
     if (c == nullptr || d_p == nullptr || gpol == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (precision != IBIM_F64 && precision != IBIM_F32C) return fail(IBIM_ERR_ARG, "bad precision");
+    if (precision != IBIM_F64 && precision != IBIM_F32C && precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
     if (c->Nc <= 0) return fail(IBIM_ERR_STATE, "no charges set");
     IBIM_TRY(energy_launch(c, *phys, d_p, d_psi_rxn, gpol));
     return check_device_error(c);
@@ -578,7 +580,7 @@ ibim_status ibim_solve(ibim_ctx* c, const ibim_phys* phys, const ibim_solve_opts
 {
     if (c == nullptr || o == nullptr || d_p == nullptr || info == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C) return fail(IBIM_ERR_ARG, "bad precision");
+    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C && o->precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
     if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
         return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
     if (o->start != 0 && o->start != 1 && o->start != 3) return fail(IBIM_ERR_ARG, "start must be 0, 1 or 3");
@@ -604,7 +606,7 @@ ibim_status ibim_solve_extrapolated(ibim_ctx* c, const ibim_phys* phys, const ib
 {
     if (c == nullptr || o == nullptr || d_p == nullptr || info == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C) return fail(IBIM_ERR_ARG, "bad precision");
+    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C && o->precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
     if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
         return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
     if (o->start != 0 && o->start != 1 && o->start != 3) return fail(IBIM_ERR_ARG, "start must be 0, 1 or 3");

@@ -234,9 +234,13 @@ __global__ void gather_triples_kernel(const int32_t* __restrict__ in, const int6
 namespace {
 
 // Recursive coordinate bisection of x* into aligned blocks of kRcbLeaf nodes:
-// each range is split across the longest side of its bounding box, the left
-// part holding a multiple of kRcbLeaf nodes (ties broken by node index, so the
-// order is a deterministic function of the coordinates).
+// each range of n nodes is split across the longest side of its bounding box,
+// the left part holding B max(1, round(n / 2B)) nodes with B = 1024 for
+// n >= 2048, 256 for n >= 512 and kRcbLeaf below (ties broken by node index,
+// so the order is a deterministic function of the coordinates).  Aligned runs
+// of 32, 256 and 1024 nodes are then bisection ranges (all but those holding
+// the last node), so the pair kernels' chunks, source tiles and target tiles
+// and the treecode's clusters are compact.
 constexpr int64_t kRcbLeaf = 32;
 
 void rcb_split(const std::vector<double>& xs, int64_t N, std::vector<int64_t>& perm, int64_t lo, int64_t hi)
@@ -253,8 +257,9 @@ void rcb_split(const std::vector<double>& xs, int64_t N, std::vector<int64_t>& p
     int ax = 0;
     for (int a = 1; a < 3; ++a)
         if (mx[a] - mn[a] > mx[ax] - mn[ax]) ax = a;
-    const int64_t half = std::max<int64_t>(1, (int64_t)llround((double)n / (2.0 * kRcbLeaf)));
-    const int64_t k = lo + kRcbLeaf * half;
+    const int64_t B = n >= 2048 ? 1024 : (n >= 512 ? 256 : kRcbLeaf);
+    const int64_t half = std::max<int64_t>(1, (int64_t)llround((double)n / (2.0 * (double)B)));
+    const int64_t k = lo + B * half;
     const double* key = xs.data() + ax * N;
     std::nth_element(perm.begin() + lo, perm.begin() + k, perm.begin() + hi, [key](int64_t a, int64_t b) {
         return key[a] < key[b] || (key[a] == key[b] && a < b);

@@ -528,7 +528,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         const int kmax = std::min(m, o.maxit - iters);
         const int prec_r = (check || kmax <= 0) ? prec_out : prec_in;
         if (!x_zero) {
-            if (prec_r == IBIM_F32C) info->matvecs_f32 += 1;
+            if (prec_r == IBIM_F32C || prec_r == IBIM_F32T) info->matvecs_f32 += 1;
             else info->matvecs_f64 += 1;
         }
         IBIM_TRY(begin_cycle(c, k, prec_r, x_zero, inner_target, std::max(kmax, 0), &beta));
@@ -548,7 +548,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         IBIM_TRY(run_cycle(c, k, prec_in, use_graph, &steps, &conv));
         iters += steps;
         ++cycles;
-        info->matvecs_f32 += (prec_in == IBIM_F32C) ? steps : 0;
+        info->matvecs_f32 += (prec_in == IBIM_F32C || prec_in == IBIM_F32T) ? steps : 0;
         info->matvecs_f64 += (prec_in == IBIM_F64) ? steps : 0;
         if (steps > 0) {
             trisolve_kernel<<<1, 1, 0, c->stream>>>(w->st);

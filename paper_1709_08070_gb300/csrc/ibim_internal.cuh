@@ -81,6 +81,7 @@ ibim_status check_phys(const ibim_phys* p);
 
 // --------------------------------------------------------------- context
 struct GmresWork;
+struct TreeCode;
 
 // Pair-kernel timing: event pairs recorded around each pair-sum launch on the
 // launching stream while enabled; summed (and recycled) when read.
@@ -146,6 +147,7 @@ struct ibim_ctx {
     double* d_yrev = nullptr;  // reverse sums of the symmetric FP32 kernel (2 x padded N) + segment counter
     size_t yrev_bytes = 0;
     ibim::GmresWork* gm = nullptr;
+    ibim::TreeCode* tc = nullptr;  // treecode tree, lists and proxy buffers (ibim_treecode_setup)
     ibim::Timing timing;
     // incremented whenever a workspace is reallocated: CUDA graphs captured
     // with the old pointers must be re-captured
@@ -209,6 +211,11 @@ ibim_status sym_fixup(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, Ve
                       const int* d_skip);
 PairSchedule f32_schedule(ibim_ctx* c);
 ibim_status f32_chunk_frames(ibim_ctx* c);
+ibim_status f32_pack_to(ibim_ctx* c, VecRef in, float4* dst, const int* d_skip);
+// treecode form of the FP32 operator (treecode.cu)
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max);
+ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, const int* d_skip);
+void tc_destroy(TreeCode* t);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,
                          OutRef out, const int* d_skip);
 // FP64 path pieces (pair_f64.cu)

@@ -413,6 +413,19 @@ ibim_status f32_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, V
     return fixup_launch(c, k, s, f32_ttile(c), in, out, d_skip);
 }
 
+// FP32 source payload of the context's nodes for input `in`, written to dst
+// (padded N / 2 node pairs; the treecode packs into its own tile buffer).
+ibim_status f32_pack_to(ibim_ctx* c, VecRef in, float4* dst, const int* d_skip)
+{
+    const int64_t n_pairs = padded_nodes(c->N) / 2;
+    const int bs = 256;
+    pack_f32_kernel<<<(unsigned)((n_pairs + bs - 1) / bs), bs, 0, c->stream>>>(
+        c->d_pos32, c->d_nrm32, c->d_geo64 + 6 * c->N, in, c->N, n_pairs, dst, d_skip);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
 // Launchers on caller-supplied buffers (used by the allocation-free entry
 // point): variant (kF32Tpt, 1), no chunk frames (positions relative to one
 // common origin), arrays padded as above.

@@ -276,19 +276,24 @@ struct Targets {
 // (kF32STile nodes as kF32STile / 2 payload pairs at sb, chunk frames at
 // sfrm).  tfrm: the frames of the warp's target blocks (2 float4 per slot).
 // Adds the tile's sums to the compensated pairs (S, C).  gi0: node index of
-// the thread's slot-0 target, slot q adding q * qstride.
-template <int TPT>
+// the thread's slot-0 target, slot q adding q * qstride.  LIST kernels may
+// pass force_far for a tile whose every source is known to lie at least
+// far_dist from every target (treecode proxies): it then takes the far-field
+// branch without the per-chunk distance test.
+template <int TPT, bool LIST = false>
 __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* tfrm, bool have_frames,
                                           const float4* sb, const float4* sfrm, const F32Consts& k,
                                           float (&S1)[TPT], float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
-                                          const Geo64& g64, int64_t gi0, int qstride, int64_t j0, int64_t N)
+                                          const Geo64& g64, int64_t gi0, int qstride, int64_t j0, int64_t N,
+                                          bool force_far = false)
 {
     const FarConsts fc = far_consts(k);
 #pragma unroll 1
     for (int c = 0; c < kChunksPerTile; ++c) {
         // targets in the source chunk's frame; far test on the two bounding spheres
         float3 X[TPT];
-        bool far = have_frames && k.rule0;
+        const bool forced = LIST && force_far;
+        bool far = (have_frames && k.rule0) || forced;
         if (have_frames) {
             const float4 mh = sfrm[2 * c];
             const float4 ml = sfrm[2 * c + 1];
@@ -301,7 +306,7 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 const float dz = (th.z - mh.z) + (tl.z - ml.z);
                 X[q] = make_float3(T.x[q].x + dx, T.x[q].y + dy, T.x[q].z + dz);
                 const float lim = k.far_dist + th.w + mh.w;
-                far = far && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim);
+                far = far && (forced || (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim));
             }
         } else {
 #pragma unroll

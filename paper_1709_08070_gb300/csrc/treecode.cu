@@ -1,0 +1,658 @@
+// Treecode form of the FP32 operator: far-field acceleration of the pair sums
+// (the role the paper gives to its black-box FMM, Sec. 4), sm_103a.
+//
+// Every kernel of the operator (Sec. 2.2, discrete system) is linear in the
+// source's densities d_j = a_j m_j (a vector) and b_j:
+//   K11 a_j = r.d_j (1 - th1 A) / (4 pi rho^3),   K12 b_j = (1 - E) b_j / (4 pi rho),
+//   K21 a_j = [(1 - A) n.d_j - (3 - B) s_x r.d_j / rho^2] / (4 pi rho^3),
+//   K22 b_j = -s_x (1 - th2 A) b_j / (4 pi rho^3),
+// so the sum over a cluster of sources seen from far away is approximated by
+// moving the densities onto the 216 proxies of the cluster's bounding cube (6
+// Chebyshev points of the second kind per axis): D_k = sum_j L_k(y_j) d_j,
+// beta_k = sum_j L_k(y_j) b_j, L_k the tensor-product Lagrange basis.
+//
+// A proxy tile holds one cluster's proxies in the FP32 source payload format
+// (-t, beta, D; 40 zero-density pads at the cube centre), so the list kernel
+// streams proxy tiles and ordinary 256-node source tiles through the same
+// stage ring and chunk code as the direct kernel: ordinary tiles keep the
+// tube rule and the near/far split, proxy tiles always take the far branch.
+//
+// Tree: clusters are node ranges split as the coordinate bisection of the node
+// order splits them (left part B max(1, round(n / 2B)), B = 1024 for n >= 2048,
+// 256 otherwise) down to 256-node tiles.  Target tiles: 1024 nodes.  A
+// cluster C is far from a target tile T when r_T + r_C <= theta D and
+// D >= far_dist + r_T + r_C + 0.25 A (D the distance of the box centres, r_T
+// the tile box half-diagonal, r_C the cube half-diagonal, far_dist =
+// max(2 tau_max, 1.5) 1.001 + 1e-3): no target-proxy distance is below
+// far_dist, so no proxy enters the regularisation tube (Sec. 2.2.1, tube
+// rule 0).  Lists come from a depth-first traversal from the root.
+//
+// Per operator application: pack the node payload into the tile buffer,
+// proxies of the leaves from their nodes (P2M), of each inner cluster from its
+// two children's proxies (M2M: exact for this interpolation, the parent's
+// basis being a polynomial of degree 5 per axis), level by level; then the
+// list kernel (stream-K over the flattened lists, FP64 partial per (CTA,
+// target tile)) and the fixup.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pair_f32_core.cuh"
+
+namespace ibim {
+
+constexpr int kCheb = 6;
+constexpr int kProxies = kCheb * kCheb * kCheb;  // 216 of a 256-node tile
+constexpr int kTcTpt = 2, kTcThreads = 512;
+constexpr int kTcTTile = kTcTpt * kTcThreads;  // 1024 targets
+constexpr double kTcMinHalf = 1e-3;            // smallest proxy-cube half side (A)
+constexpr double kTcFarMargin = 0.25;          // extra gap of a far cluster (A)
+static_assert(kProxies <= kF32STile, "proxies of a cluster fit one source tile");
+
+struct TcCube {  // proxy cube of a cluster: centre and half side
+    double x, y, z, w;
+};
+
+struct TcClusters {  // device arrays, one entry per cluster
+    const int64_t* j0;
+    const int64_t* j1;
+    const int2* child;      // (-1, -1) for a leaf
+    const TcCube* cube;    // centre and half side
+};
+
+struct TreeCode {
+    double theta = 0.0, tau_max = 0.0;
+    int64_t n_real_tiles = 0;  // padded N / 256
+    int n_clusters = 0;
+    int64_t n_t = 0;           // target tiles
+    int64_t near_steps = 0, far_steps = 0, total = 0;
+    int64_t per_cta = 0;
+    int grid = 0;
+    std::vector<int> level_off;  // clusters by height: ids[level_off[h] .. level_off[h + 1])
+    int64_t* d_j0 = nullptr;
+    int64_t* d_j1 = nullptr;
+    int2* d_child = nullptr;
+    TcCube* d_cube = nullptr;
+    int* d_ids = nullptr;
+    float4* d_src = nullptr;       // payload of the real tiles, then one proxy tile per cluster
+    float4* d_frm = nullptr;       // chunk frames of all those tiles
+    int64_t* d_row_ptr = nullptr;  // n_t + 1
+    int32_t* d_step_src = nullptr; // total: source tile of each step
+    double* d_part = nullptr;      // (grid + n_t) x 2 x kTcTTile
+};
+
+void tc_destroy(TreeCode* t)
+{
+    if (t == nullptr) return;
+    cudaFree(t->d_j0);
+    cudaFree(t->d_j1);
+    cudaFree(t->d_child);
+    cudaFree(t->d_cube);
+    cudaFree(t->d_ids);
+    cudaFree(t->d_src);
+    cudaFree(t->d_frm);
+    cudaFree(t->d_row_ptr);
+    cudaFree(t->d_step_src);
+    cudaFree(t->d_part);
+    delete t;
+}
+
+// ------------------------------------------------------------------ device
+
+// Lagrange basis of the 6 Chebyshev points of [-1, 1] at u (barycentric
+// form; u on a point gives the unit vector).
+__device__ __forceinline__ void cheb_basis(double u, float (&l)[kCheb])
+{
+    double q[kCheb], s = 0.0;
+    int hit = -1;
+#pragma unroll
+    for (int k = 0; k < kCheb; ++k) {
+        const double t = cospi((double)k / (double)(kCheb - 1));
+        const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == kCheb - 1) ? 0.5 : 1.0);
+        const double d = u - t;
+        if (d == 0.0) hit = k;
+        q[k] = wk / d;
+        s += q[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kCheb; ++k) l[k] = (hit >= 0) ? (k == hit ? 1.0f : 0.0f) : (float)(q[k] / s);
+}
+
+// Proxies of the clusters ids[0 .. gridDim.x) (one CTA of kF32STile threads
+// each): from the cluster's nodes for a leaf, from its children's proxies
+// otherwise; written as the cluster's proxy tile in the source payload format.
+__global__ void __launch_bounds__(kF32STile)
+    tc_upward_kernel(TcClusters cl, const int* __restrict__ ids, const double* __restrict__ geo, int64_t N,
+                     int64_t n_real_tiles, float4* __restrict__ src, const int* __restrict__ skip)
+{
+    if (skip != nullptr && *skip) return;
+    __shared__ float lw[kF32STile][3 * kCheb];
+    __shared__ float4 dens[kF32STile];   // (d.x, d.y, d.z, b) of each source of the pass
+    __shared__ float4 outp[kF32STile];   // (rel.x, rel.y, rel.z, b) of each proxy
+    __shared__ float4 outd[kF32STile];   // (D.x, D.y, D.z, 0)
+    const int tid = threadIdx.x;
+    const int ci = ids[blockIdx.x];
+    const TcCube cube = cl.cube[ci];
+    const double inv = 1.0 / cube.w;
+    const int2 ch = cl.child[ci];
+    const int kx = tid / (kCheb * kCheb), ky = (tid / kCheb) % kCheb, kz = tid % kCheb;
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, ab = 0.0f;
+
+    auto accumulate = [&](int count) {
+        __syncthreads();
+        if (tid < kProxies)
+            for (int s = 0; s < count; ++s) {
+                const float wgt = lw[s][kx] * lw[s][kCheb + ky] * lw[s][2 * kCheb + kz];
+                const float4 d = dens[s];
+                ax = fmaf(wgt, d.x, ax);
+                ay = fmaf(wgt, d.y, ay);
+                az = fmaf(wgt, d.z, az);
+                ab = fmaf(wgt, d.w, ab);
+            }
+        __syncthreads();
+    };
+    auto set_source = [&](double x, double y, double z, float4 d) {
+        float l[kCheb];
+        cheb_basis((x - cube.x) * inv, l);
+#pragma unroll
+        for (int k = 0; k < kCheb; ++k) lw[tid][k] = l[k];
+        cheb_basis((y - cube.y) * inv, l);
+#pragma unroll
+        for (int k = 0; k < kCheb; ++k) lw[tid][kCheb + k] = l[k];
+        cheb_basis((z - cube.z) * inv, l);
+#pragma unroll
+        for (int k = 0; k < kCheb; ++k) lw[tid][2 * kCheb + k] = l[k];
+        dens[tid] = d;
+    };
+
+    if (ch.x < 0) {  // leaf: its nodes (payload densities of this application)
+        const int64_t j0 = cl.j0[ci], j1 = cl.j1[ci];
+        for (int64_t base = j0; base < j1; base += kF32STile) {
+            const int64_t j = base + tid;
+            if (j < j1) {
+                const float4* pr = src + kPairF4 * (j >> 1);
+                const float4 B = pr[1], C = pr[2], D = pr[3];
+                const bool odd = j & 1;
+                const float4 d = odd ? make_float4(C.y, C.w, D.y, B.w) : make_float4(C.x, C.z, D.x, B.z);
+                set_source(geo[j], geo[N + j], geo[2 * N + j], d);
+            } else {
+                set_source(cube.x, cube.y, cube.z, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+            }
+            const int64_t left = j1 - base;
+            accumulate(left < kF32STile ? (int)left : kF32STile);
+        }
+    } else {  // inner cluster: the proxies of its two children
+        for (int side = 0; side < 2; ++side) {
+            const int cc = side ? ch.y : ch.x;
+            const TcCube cb = cl.cube[cc];
+            if (tid < kProxies) {
+                const int qx = tid / (kCheb * kCheb), qy = (tid / kCheb) % kCheb, qz = tid % kCheb;
+                const float4* pr = src + (n_real_tiles + cc) * (kF32STile / 2) * kPairF4 + kPairF4 * (tid >> 1);
+                const float4 B = pr[1], C = pr[2], D = pr[3];
+                const bool odd = tid & 1;
+                const float4 d = odd ? make_float4(C.y, C.w, D.y, B.w) : make_float4(C.x, C.z, D.x, B.z);
+                set_source(cb.x + cb.w * cospi((double)qx / (kCheb - 1)), cb.y + cb.w * cospi((double)qy / (kCheb - 1)),
+                           cb.z + cb.w * cospi((double)qz / (kCheb - 1)), d);
+            }
+            accumulate(kProxies);
+        }
+    }
+
+    // proxy tile: positions relative to the cube centre (the tile's chunk frame)
+    if (tid < kProxies) {
+        outp[tid] = make_float4((float)(cube.w * cospi((double)kx / (kCheb - 1))),
+                                (float)(cube.w * cospi((double)ky / (kCheb - 1))),
+                                (float)(cube.w * cospi((double)kz / (kCheb - 1))), ab);
+        outd[tid] = make_float4(ax, ay, az, 0.0f);
+    } else {
+        outp[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        outd[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    if (tid < kF32STile / 2) {
+        const float4 p0 = outp[2 * tid], p1 = outp[2 * tid + 1];
+        const float4 d0 = outd[2 * tid], d1 = outd[2 * tid + 1];
+        float4* dst = src + (n_real_tiles + ci) * (kF32STile / 2) * kPairF4 + kPairF4 * tid;
+        dst[0] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
+        dst[1] = make_float4(-p0.z, -p1.z, p0.w, p1.w);
+        dst[2] = make_float4(d0.x, d1.x, d0.y, d1.y);
+        dst[3] = make_float4(d0.z, d1.z, 0.0f, 0.0f);
+    }
+}
+
+struct TcSchedule {
+    const int64_t* row_ptr;   // n_t + 1, row t = steps [row_ptr[t], row_ptr[t + 1])
+    const int32_t* step_src;  // source tile of each step (>= n_real_tiles: a proxy tile)
+    int64_t n_t, total, per_cta, n_real_tiles;
+};
+
+// The FP32 pair sums over the interaction lists: as pair_f32_kernel, with the
+// (target tile, source tile) of each step read from the lists.
+template <int TPT, int MINB, int THREADS>
+__global__ void __launch_bounds__(THREADS, MINB)
+    tc_pair_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm, const float4* __restrict__ src,
+                   const float4* __restrict__ frames, int64_t N, TcSchedule s, F32Consts k,
+                   double* __restrict__ part, unsigned* __restrict__ err, const int* __restrict__ skip, Geo64 g64)
+{
+    constexpr int TTILE = THREADS * TPT;
+    constexpr int NW = THREADS / 32;
+    if (skip != nullptr && *skip) return;
+    __shared__ __align__(128) SourceStage stg[kF32Stages];
+    __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
+    __shared__ __align__(8) StagePipe pipe;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int64_t s0 = (int64_t)blockIdx.x * s.per_cta;
+    const int64_t s1 = (s0 + s.per_cta < s.total) ? s0 + s.per_cta : s.total;
+    if (s0 >= s1) return;
+
+    if (tid == 0) pipe_init(pipe, NW);
+    __syncthreads();
+
+    auto issue = [&](int64_t u) {
+        const int64_t st = s.step_src[u];
+        const int stage = (int)((u - s0) % kF32Stages);
+        pipe_issue(pipe, stg[stage], stage, src + st * (kF32STile / 2) * kPairF4, frames + st * 2 * kChunksPerTile);
+    };
+    if (tid == 0)
+        for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
+
+    // the row holding step s0: the last t with row_ptr[t] <= s0
+    int64_t lo = 0, hi = s.n_t;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (s.row_ptr[mid] <= s0) lo = mid;
+        else hi = mid;
+    }
+    int64_t t = lo;
+    int64_t row_end = s.row_ptr[t + 1];
+    Targets<TPT> T;
+    int64_t gi0 = 0;
+    bool idle = false;
+    double D1[TPT], D2[TPT];
+
+    auto load_targets = [&](int64_t tile) {
+        gi0 = tile * TTILE + tid;
+        idle = tile * TTILE + warp * 32 >= N;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t i = gi0 + (int64_t)q * THREADS;
+            const float4 a = tpos[i];
+            const float4 b = tnrm[i];
+            T.x[q] = make_float3(a.x, a.y, a.z);
+            T.nx[q] = f2(b.x);
+            T.ny[q] = f2(b.y);
+            T.nz[q] = f2(b.z);
+            D1[q] = 0.0;
+            D2[q] = 0.0;
+        }
+        __syncwarp();
+        if (lane < 2 * TPT) {
+            const int64_t blk0 = tile * TTILE + (int64_t)(lane >> 1) * THREADS + warp * 32;
+            tfrm[warp][lane] = frames[2 * (blk0 / kChunk) + (lane & 1)];
+        }
+        __syncwarp();
+    };
+    load_targets(t);
+
+    for (int64_t u = s0; u < s1; ++u) {
+        const int stage = (int)((u - s0) % kF32Stages);
+        const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+            if (lane == 0) atomicOr(err, kDevErrTimeout);
+            return;
+        }
+        const int64_t st = s.step_src[u];
+        float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+        if (!idle)
+            tile_sums<TPT, true>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64,
+                                 gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles);
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            D1[q] += (double)S1[q] - (double)C1[q];
+            D2[q] += (double)S2[q] - (double)C2[q];
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+        if (warp == 0) {  // thread 0 refills the stage of step u - 1
+            bool ok = true;
+            if (lane == 0 && u > s0 && u - 1 + kF32Stages < s1) {
+                const int64_t v = u - 1 - s0;
+                ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(v % kF32Stages)], (uint32_t)((v / kF32Stages) & 1),
+                                            kWaitLimitNs);
+                if (ok) {
+                    ptx::fence_proxy_async_smem();
+                    issue(u - 1 + kF32Stages);
+                } else {
+                    atomicOr(err, kDevErrTimeout);
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+        }
+
+        if (u + 1 == row_end || u + 1 == s1) {
+            double* dst = part + ((int64_t)blockIdx.x + t) * 2 * TTILE;
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+                dst[q * THREADS + tid] = D1[q];
+                dst[TTILE + q * THREADS + tid] = D2[q];
+            }
+            if (u + 1 < s1) {  // rows are never empty: the next step starts row t + 1
+                ++t;
+                row_end = s.row_ptr[t + 1];
+                load_targets(t);
+            }
+        }
+    }
+}
+
+// y = Lambda p + (1/(4 pi)) (partials of the CTAs that covered the row).
+__global__ void tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, int64_t N, double lambda1,
+                                double lambda2, VecRef in, OutRef out, const int* __restrict__ skip)
+{
+    if (skip != nullptr && *skip) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
+    double* y = out.base + (out.kidx ? (int64_t)(*out.kidx + out.koff) * out.stride : 0);
+    const int64_t t = i / kTcTTile;
+    const int64_t l = i - t * kTcTTile;
+    const int64_t c0 = s.row_ptr[t] / s.per_cta;
+    const int64_t c1 = (s.row_ptr[t + 1] - 1) / s.per_cta;
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t c = c0; c <= c1; ++c) {
+        const double* q = part + (c + t) * 2 * kTcTTile;
+        a1 += q[l];
+        a2 += q[kTcTTile + l];
+    }
+    y[i] = lambda1 * p[i] + kInv4Pi * a1;
+    y[N + i] = lambda2 * p[N + i] + kInv4Pi * a2;
+}
+
+// ------------------------------------------------------------------ host
+
+static ibim_status tc_fail(ibim_status s, const char* msg)
+{
+    set_error(msg);
+    return s;
+}
+
+namespace {
+
+struct HostCluster {
+    int64_t j0, j1;
+    int c0 = -1, c1 = -1;
+    int height = 0;
+    double cx, cy, cz, half, radius;
+};
+
+int64_t tc_split_point(int64_t n)
+{
+    const int64_t B = n >= 2048 ? 1024 : 256;
+    const int64_t half = std::max<int64_t>(1, (int64_t)std::floor((double)n / (2.0 * (double)B) + 0.5));
+    return B * half;
+}
+
+void box_of(const std::vector<double>& xs, int64_t N, int64_t j0, int64_t j1, double mn[3], double mx[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = HUGE_VAL;
+        mx[a] = -HUGE_VAL;
+    }
+    for (int64_t j = j0; j < j1; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const double v = xs[a * N + j];
+            mn[a] = std::min(mn[a], v);
+            mx[a] = std::max(mx[a], v);
+        }
+}
+
+// Cluster of nodes [j0, j1) and its subtree (pre-order indices).  Its proxy
+// cube bounds its nodes and its children's cubes, so M2M never evaluates a
+// parent's basis outside its cube.
+int make_cluster(std::vector<HostCluster>& cl, const std::vector<double>& xs, int64_t N, int64_t j0, int64_t j1)
+{
+    const int idx = (int)cl.size();
+    cl.emplace_back();
+    HostCluster c;
+    c.j0 = j0;
+    c.j1 = j1;
+    if (j1 - j0 > kF32STile) {
+        const int64_t k = tc_split_point(j1 - j0);
+        c.c0 = make_cluster(cl, xs, N, j0, j0 + k);
+        c.c1 = make_cluster(cl, xs, N, j0 + k, j1);
+        c.height = 1 + std::max(cl[c.c0].height, cl[c.c1].height);
+    }
+    double mn[3], mx[3];
+    box_of(xs, N, j0, j1, mn, mx);
+    for (int side = 0; side < 2 && c.c0 >= 0; ++side) {
+        const HostCluster& q = cl[side ? c.c1 : c.c0];
+        const double qc[3] = {q.cx, q.cy, q.cz};
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min(mn[a], qc[a] - q.half);
+            mx[a] = std::max(mx[a], qc[a] + q.half);
+        }
+    }
+    c.cx = 0.5 * (mn[0] + mx[0]);
+    c.cy = 0.5 * (mn[1] + mx[1]);
+    c.cz = 0.5 * (mn[2] + mx[2]);
+    const double e0 = 0.5 * (mx[0] - mn[0]), e1 = 0.5 * (mx[1] - mn[1]), e2 = 0.5 * (mx[2] - mn[2]);
+    c.half = std::max(std::max(std::max(e0, e1), e2), kTcMinHalf);
+    c.radius = std::sqrt(3.0 * c.half * c.half);
+    cl[idx] = c;
+    return idx;
+}
+
+template <class T>
+ibim_status upload(T** dst, const std::vector<T>& v)
+{
+    IBIM_CUDA(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(1, v.size())));
+    if (!v.empty()) IBIM_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return IBIM_OK;
+}
+
+}  // namespace
+
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
+{
+    const int64_t N = c->N;
+    std::vector<double> xs(3 * (size_t)N);
+    IBIM_CUDA(cudaMemcpyAsync(xs.data(), c->d_geo64, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+
+    std::vector<HostCluster> cl;
+    cl.reserve((size_t)(2 * (N / kF32STile) + 4));
+    make_cluster(cl, xs, N, 0, N);
+    const int nc = (int)cl.size();
+
+    // target tiles
+    const int64_t n_t = (N + kTcTTile - 1) / kTcTTile;
+    std::vector<double> tcx(n_t), tcy(n_t), tcz(n_t), trad(n_t);
+    for (int64_t t = 0; t < n_t; ++t) {
+        double mn[3], mx[3];
+        box_of(xs, N, t * kTcTTile, std::min<int64_t>((t + 1) * kTcTTile, N), mn, mx);
+        tcx[t] = 0.5 * (mn[0] + mx[0]);
+        tcy[t] = 0.5 * (mn[1] + mx[1]);
+        tcz[t] = 0.5 * (mn[2] + mx[2]);
+        const double e0 = 0.5 * (mx[0] - mn[0]), e1 = 0.5 * (mx[1] - mn[1]), e2 = 0.5 * (mx[2] - mn[2]);
+        trad[t] = std::sqrt((e0 * e0 + e1 * e1) + e2 * e2);
+    }
+
+    // lists, depth-first from the root
+    const int64_t n_real = padded_nodes(N) / kF32STile;
+    const double fd = std::max(2.0 * tau_max, 1.5) * 1.001 + 1e-3;
+    std::vector<int64_t> row_ptr(n_t + 1, 0);
+    std::vector<int32_t> steps;
+    int64_t near_steps = 0, far_steps = 0;
+    std::vector<int> stack;
+    for (int64_t t = 0; t < n_t; ++t) {
+        stack.assign(1, 0);
+        while (!stack.empty()) {
+            const int ci = stack.back();
+            stack.pop_back();
+            const HostCluster& q = cl[ci];
+            const double dx = tcx[t] - q.cx, dy = tcy[t] - q.cy, dz = tcz[t] - q.cz;
+            const double D = std::sqrt((dx * dx + dy * dy) + dz * dz);
+            const double rT = trad[t];
+            const bool far = (rT + q.radius <= theta * D) && (D >= fd + rT + q.radius + kTcFarMargin);
+            if (far) {
+                steps.push_back((int32_t)(n_real + ci));
+                ++far_steps;
+            } else if (q.c0 < 0) {
+                steps.push_back((int32_t)(q.j0 / kF32STile));
+                ++near_steps;
+            } else {
+                stack.push_back(q.c1);
+                stack.push_back(q.c0);
+            }
+        }
+        row_ptr[t + 1] = (int64_t)steps.size();
+    }
+    if (n_real + nc > INT32_MAX) return tc_fail(IBIM_ERR_ARG, "treecode: too many tiles");
+
+    // clusters by height (leaves first) for the upward pass
+    int hmax = 0;
+    for (const HostCluster& q : cl) hmax = std::max(hmax, q.height);
+    std::vector<int> ids;
+    std::vector<int> level_off(1, 0);
+    for (int h = 0; h <= hmax; ++h) {
+        for (int i = 0; i < nc; ++i)
+            if (cl[i].height == h) ids.push_back(i);
+        level_off.push_back((int)ids.size());
+    }
+
+    // proxy frames: every chunk of a proxy tile has the cube centre (hi + lo) and radius
+    std::vector<float4> pfrm((size_t)nc * 2 * kChunksPerTile);
+    for (int i = 0; i < nc; ++i) {
+        const float hx = (float)cl[i].cx, hy = (float)cl[i].cy, hz = (float)cl[i].cz;
+        const float4 f0 = make_float4(hx, hy, hz, (float)(cl[i].radius * 1.0001 + 1e-4));
+        const float4 f1 = make_float4((float)(cl[i].cx - (double)hx), (float)(cl[i].cy - (double)hy),
+                                      (float)(cl[i].cz - (double)hz), 0.0f);
+        for (int ch = 0; ch < kChunksPerTile; ++ch) {
+            pfrm[(size_t)i * 2 * kChunksPerTile + 2 * ch] = f0;
+            pfrm[(size_t)i * 2 * kChunksPerTile + 2 * ch + 1] = f1;
+        }
+    }
+    std::vector<int64_t> hj0(nc), hj1(nc);
+    std::vector<int2> hch(nc);
+    std::vector<TcCube> hcube(nc);
+    for (int i = 0; i < nc; ++i) {
+        hj0[i] = cl[i].j0;
+        hj1[i] = cl[i].j1;
+        hch[i] = make_int2(cl[i].c0, cl[i].c1);
+        hcube[i] = TcCube{cl[i].cx, cl[i].cy, cl[i].cz, cl[i].half};
+    }
+
+    TreeCode* T = new TreeCode();
+    T->theta = theta;
+    T->tau_max = tau_max;
+    T->n_real_tiles = n_real;
+    T->n_clusters = nc;
+    T->n_t = n_t;
+    T->near_steps = near_steps;
+    T->far_steps = far_steps;
+    T->total = (int64_t)steps.size();
+    T->level_off = level_off;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, 1, kTcThreads>, kTcThreads, 0);
+    const int64_t cap = (int64_t)std::max(1, occ) * c->num_sms;
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(cap, T->total));
+    T->per_cta = (T->total + g - 1) / g;
+    T->grid = (int)((T->total + T->per_cta - 1) / T->per_cta);
+
+    ibim_status st = IBIM_OK;
+    auto chk = [&](ibim_status s) {
+        if (st == IBIM_OK) st = s;
+    };
+    chk(upload(&T->d_j0, hj0));
+    chk(upload(&T->d_j1, hj1));
+    chk(upload(&T->d_child, hch));
+    chk(upload(&T->d_cube, hcube));
+    chk(upload(&T->d_ids, ids));
+    chk(upload(&T->d_row_ptr, row_ptr));
+    chk(upload(&T->d_step_src, steps));
+    const size_t frm_real = (size_t)n_real * 2 * kChunksPerTile;
+    if (st == IBIM_OK) {
+        cudaError_t e = cudaMalloc((void**)&T->d_src, sizeof(float4) * (size_t)(n_real + nc) * (kF32STile / 2) * kPairF4);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_frm, sizeof(float4) * (frm_real + pfrm.size()));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void**)&T->d_part, sizeof(double) * (size_t)(T->grid + n_t) * 2 * kTcTTile);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T->d_frm, c->d_frames, sizeof(float4) * frm_real, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T->d_frm + frm_real, pfrm.data(), sizeof(float4) * pfrm.size(), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = tc_fail(IBIM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (st != IBIM_OK) {
+        tc_destroy(T);
+        return st;
+    }
+    tc_destroy(c->tc);
+    c->tc = T;
+    c->ws_generation += 1;  // graphs captured with another tree must be re-captured
+    return IBIM_OK;
+}
+
+ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, const int* d_skip)
+{
+    TreeCode* T = c->tc;
+    if (T == nullptr) return tc_fail(IBIM_ERR_STATE, "the treecode operator needs ibim_treecode_setup first");
+    if (!(k.four_tau2 < 3.0e38)) return tc_fail(IBIM_ERR_ARG, "the treecode operator needs tube rule 0");
+    if (std::sqrt(k.tau2) > T->tau_max * (1.0 + 1e-12))
+        return tc_fail(IBIM_ERR_ARG, "tau exceeds the tau_max the treecode lists were built for");
+    const int64_t N = c->N;
+    IBIM_TRY(f32_pack_to(c, in, T->d_src, d_skip));
+    const TcClusters cl{T->d_j0, T->d_j1, T->d_child, T->d_cube};
+    for (size_t h = 0; h + 1 < T->level_off.size(); ++h) {
+        const int n = T->level_off[h + 1] - T->level_off[h];
+        if (n == 0) continue;
+        tc_upward_kernel<<<n, kF32STile, 0, c->stream>>>(cl, T->d_ids + T->level_off[h], c->d_geo64, N,
+                                                         T->n_real_tiles, T->d_src, d_skip);
+        count_launch(c);
+        IBIM_CUDA(cudaGetLastError());
+    }
+    const TcSchedule s{T->d_row_ptr, T->d_step_src, T->n_t, T->total, T->per_cta, T->n_real_tiles};
+    const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * N, 1, N};
+    IBIM_TRY(timing_begin(c));
+    tc_pair_kernel<kTcTpt, 1, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
+        c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, c->d_err, d_skip, g64);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_TRY(timing_end(c, (T->near_steps + T->far_steps) * (int64_t)kTcTTile * kF32STile));
+    const int bs = 256;
+    tc_fixup_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(T->d_part, s, N, k.lambda1, k.lambda2, in,
+                                                                          out, d_skip);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
+}  // namespace ibim
+
+extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau_max)
+{
+    using namespace ibim;
+    if (c == nullptr || !(theta > 0.0 && theta < 1.0) || !(tau_max > 0.0) || !std::isfinite(tau_max))
+        return tc_fail(IBIM_ERR_ARG, "need a context, 0 < theta < 1 and a finite tau_max > 0");
+    if (c->N <= 0 || c->d_frames == nullptr) return tc_fail(IBIM_ERR_STATE, "the context has no nodes");
+    return tc_setup(c, theta, tau_max);
+}
+
+extern "C" ibim_status ibim_treecode_info(ibim_ctx* c, int64_t* near_steps, int64_t* far_steps, int64_t* clusters,
+                                          int64_t* target_tiles)
+{
+    using namespace ibim;
+    if (c == nullptr) return tc_fail(IBIM_ERR_ARG, "need a context");
+    if (c->tc == nullptr) return tc_fail(IBIM_ERR_STATE, "no treecode: call ibim_treecode_setup");
+    if (near_steps) *near_steps = c->tc->near_steps;
+    if (far_steps) *far_steps = c->tc->far_steps;
+    if (clusters) *clusters = c->tc->n_clusters;
+    if (target_tiles) *target_tiles = c->tc->n_t;
+    return IBIM_OK;
+}

@@ -21,10 +21,12 @@ __all__ = [
     "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
     "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian", "ibim_solve_extrapolated",
+    "IBIM_F32T", "ibim_treecode_setup", "ibim_treecode_info",
 ]
 
 IBIM_F64 = 64
 IBIM_F32C = 32
+IBIM_F32T = 33
 IBIM_NOALLOC_MAX_NODES = 131072
 IBIM_WS_NPARAMS = 4930
 IBIM_WS_NFEATURES = 9
@@ -83,6 +85,8 @@ _SIGS = {
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
+    "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double],
+    "ibim_treecode_info": [_V, _I64P, _I64P, _I64P, _I64P],
     "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
@@ -370,6 +374,18 @@ def ibim_autotune(ctx, phys):
     return t.value, b.value, ms.value
 
 
+def ibim_treecode_setup(ctx, theta, tau_max):
+    """Build the treecode tree and interaction lists (IBIM_F32T operator)."""
+    _check(lib().ibim_treecode_setup(ctx, float(theta), float(tau_max)))
+
+
+def ibim_treecode_info(ctx):
+    """{'near_steps', 'far_steps', 'clusters', 'target_tiles'} of the current treecode setup."""
+    v = [ctypes.c_int64(0) for _ in range(4)]
+    _check(lib().ibim_treecode_info(ctx, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("near_steps", "far_steps", "clusters", "target_tiles"), (x.value for x in v)))
+
+
 def ibim_set_f32_variant(ctx, variant, ctas_per_sm=0):
     _check(lib().ibim_set_f32_variant(ctx, int(variant), int(ctas_per_sm)))
 
@@ -533,6 +549,12 @@ class Context:
 
     def set_f32_variant(self, variant, ctas_per_sm=0):
         ibim_set_f32_variant(self.handle, variant, ctas_per_sm)
+
+    def treecode_setup(self, theta, tau_max):
+        ibim_treecode_setup(self.handle, theta, tau_max)
+
+    def treecode_info(self):
+        return ibim_treecode_info(self.handle)
 
     def timing_enable(self, enable=True):
         ibim_timing_enable(self.handle, enable)

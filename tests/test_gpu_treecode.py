@@ -1,0 +1,126 @@
+"""Treecode operator (IBIM_F32T) against the oracle's treecode and the direct operator.
+
+On caller-ordered clouds both sides build the same tree and lists from the
+same coordinates, so their list sizes must be equal and the operators must
+agree to FP32 rounding.  On a built sphere the treecode must stay within its
+approximation error of the direct FP64 operator, and a GMRES solve with it
+must give the direct solve's energy.  Misuse returns the documented errors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import treecode as tc
+from paper_1709_08070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1709_08070_gb300 import ibim  # noqa: E402
+
+CENTRES = [(28.0 * i, 28.0 * j, 0.0) for i in range(3) for j in range(3)]
+
+
+def _rel(a, b, N):
+    return (np.linalg.norm(a[:N] - b[:N]) / np.linalg.norm(b[:N]), np.linalg.norm(a[N:] - b[N:]) / np.linalg.norm(b[N:]))
+
+
+@pytest.mark.parametrize("theta,n_per", [(0.6, 1000), (0.8, 1500)])
+def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per):
+    xs, nr, w = inputs.sphere_cluster_cloud(n_per, CENTRES, radius=5.0, seed=4)
+    N = xs.shape[0]
+    tau = 0.3
+    ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
+    ctx.treecode_setup(theta, tau)
+    info = ctx.treecode_info()
+    tree = tc.TileTree(xs)
+    lists = tree.lists(theta, tau)
+    near, far = tc.list_sizes(lists)
+    assert (info["near_steps"], info["far_steps"]) == (near, far), (info, near, far)
+    assert info["clusters"] == len(tree.clusters) and info["target_tiles"] == tree.n_t
+    assert far > 0
+    P = ibim.Phys(2.0, 80.0, 0.1257, tau, 0)
+    Po = oracle.Phys(2.0, 80.0, 0.1257, tau)
+    p = inputs.random_vector(2 * N, seed=6)
+    yo = tc.treecode_matvec(xs, nr, w, Po, p, tree=tree, lists=lists)
+    d_in = torch.from_numpy(p).cuda()
+    y = torch.empty_like(d_in)
+    ctx.matvec(P, d_in, y, precision=ibim.IBIM_F32T)
+    y = y.cpu().numpy()
+    r = _rel(y, yo, N)
+    worst = np.max(np.abs(y - yo)) / np.max(np.abs(yo))
+    ye = oracle.matvec(xs, nr, w, Po, p)
+    approx = _rel(yo, ye, N)
+    print("theta %.1f N %d steps near %d far %d: GPU vs oracle treecode %.2e %.2e (worst %.2e); "
+          "oracle treecode vs direct %.2e %.2e" % (theta, N, near, far, *r, worst, *approx))
+    assert max(r) < 1e-6 and worst < 1e-5
+    ctx.close()
+
+
+def test_treecode_without_far_clusters_is_the_fp32_operator():
+    xs, nr, w = inputs.compact_sphere_cloud(3000, radius=6.0, seed=2)
+    N = xs.shape[0]
+    ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
+    ctx.treecode_setup(0.5, 0.3)
+    assert ctx.treecode_info()["far_steps"] == 0
+    P = ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0)
+    d_in = torch.from_numpy(inputs.random_vector(2 * N, seed=1)).cuda()
+    yt, y32, y64 = (torch.empty_like(d_in) for _ in range(3))
+    ctx.matvec(P, d_in, yt, precision=ibim.IBIM_F32T)
+    ctx.matvec(P, d_in, y32, precision=ibim.IBIM_F32C)
+    ctx.matvec(P, d_in, y64, precision=ibim.IBIM_F64)
+    a = y64.cpu().numpy()
+    assert max(_rel(yt.cpu().numpy(), a, N)) < 1e-7
+    assert max(_rel(yt.cpu().numpy(), y32.cpu().numpy(), N)) < 1e-7
+    ctx.close()
+
+
+def test_treecode_on_built_sphere_operator_and_solve():
+    R, h = 20.0, 0.5
+    ctx = ibim.Context.sphere(R, h=h, band_eps=2 * h)
+    N = ctx.N
+    z, q = inputs.kirkwood_charges(50, 16.0)
+    ctx.set_charges(z, q)
+    P = ibim.Phys(2.0, 80.0, 0.1257, h, 0)
+    ctx.treecode_setup(0.7, h)
+    info = ctx.treecode_info()
+    assert info["far_steps"] > 0
+    d_in = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
+    yt, y64 = torch.empty_like(d_in), torch.empty_like(d_in)
+    ctx.matvec(P, d_in, yt, precision=ibim.IBIM_F32T)
+    ctx.matvec(P, d_in, y64, precision=ibim.IBIM_F64)
+    r = _rel(yt.cpu().numpy(), y64.cpu().numpy(), N)
+    direct_steps = info["target_tiles"] * (-(-N // 256))
+    print("Kirkwood sphere N %d: steps near %d + far %d of %d direct; treecode vs FP64 %.2e %.2e"
+          % (N, info["near_steps"], info["far_steps"], direct_steps, *r))
+    assert max(r) < 1e-6
+    d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    opts = dict(tol=1e-7, restart=64, maxit=400)
+    it = ctx.solve(P, d, precision=ibim.IBIM_F32T, certify=0, **opts)
+    i32 = ctx.solve(P, d, precision=ibim.IBIM_F32C, certify=0, **opts)
+    print("G_pol treecode %.10f direct %.10f (iterations %d, %d)" % (it["gpol"], i32["gpol"], it["iters"], i32["iters"]))
+    assert it["converged"] and abs(it["gpol"] - i32["gpol"]) < 1e-6 * abs(i32["gpol"])
+    ctx.close()
+
+
+def test_treecode_misuse_is_reported():
+    xs, nr, w = inputs.compact_sphere_cloud(2000, radius=6.0, seed=5)
+    ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
+    d_in = torch.from_numpy(inputs.random_vector(4000, seed=1)).cuda()
+    y = torch.empty_like(d_in)
+    with pytest.raises(ibim.IbimError) as e:
+        ctx.matvec(ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0), d_in, y, precision=ibim.IBIM_F32T)
+    assert e.value.status == 7  # IBIM_ERR_STATE: no setup
+    for theta, tau_max in ((0.0, 0.3), (1.0, 0.3), (0.5, 0.0), (0.5, float("inf"))):
+        with pytest.raises(ibim.IbimError) as e:
+            ctx.treecode_setup(theta, tau_max)
+        assert e.value.status == 1  # IBIM_ERR_ARG
+    ctx.treecode_setup(0.5, 0.3)
+    for P in (ibim.Phys(2.0, 80.0, 0.1257, 0.4, 0), ibim.Phys(2.0, 80.0, 0.1257, 0.3, 1)):
+        with pytest.raises(ibim.IbimError) as e:
+            ctx.matvec(P, d_in, y, precision=ibim.IBIM_F32T)
+        assert e.value.status == 1
+    ctx.close()

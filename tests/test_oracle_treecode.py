@@ -140,3 +140,14 @@ def test_error_falls_with_the_chebyshev_order(theta):
     print("treecode error vs direct, theta %.1f, n = 3, 4, 6: %s" % (theta, ["%.2e" % e for e in errs]))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 1e-7
+
+
+def test_cubes_nest_and_hold_their_nodes():
+    xs, nr, w = _cloud(n_per=700)
+    tree = tc.TileTree(xs)
+    for c in tree.clusters:
+        seg = xs[c.j0:c.j1]
+        assert np.all(np.abs(seg - c.centre) <= c.half * (1 + 1e-12))
+        for ci in c.children:
+            q = tree.clusters[ci]
+            assert np.all(np.abs(q.centre - c.centre) + q.half <= c.half * (1 + 1e-12))
