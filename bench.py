@@ -440,6 +440,99 @@ def run_protein(args):
     ctx.close()
 
 
+TREECODE = {"workload": "kirkwood_sphere_large", "R": 60.0, "h": 0.5, "band_k": 2, "tau_k": 1.0, "n_charges": 50,
+            "charge_ball": 48.0, "eps_in": 2.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64,
+            "theta": 0.7}
+
+
+def run_treecode(args):
+    """Kirkwood-type sphere three times the default size (R = 60 A, N = 722,830)
+    with the treecode operator (IBIM_F32T, theta 0.7): timed applications, the
+    direct FP32 operator timed beside it, the operator difference, and one FP32
+    solve to 1e-6 with each operator (energies against each other and against
+    the Kirkwood series).  value = N^2 x applications / time: the interactions
+    of the operator the treecode approximates; pairs_per_s counts the pair
+    evaluations the treecode actually performs."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    W = TREECODE
+    h = W["h"]
+    t0 = time.perf_counter()
+    ctx = ibim.Context.sphere(W["R"], h=h, band_eps=W["band_k"] * h)
+    z, q = inputs.kirkwood_charges(W["n_charges"], W["charge_ball"])
+    ctx.set_charges(z, q)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    N = ctx.N
+    P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
+    variant, bps, _ = ctx.autotune(P)
+    t0 = time.perf_counter()
+    ctx.treecode_setup(W["theta"], W["tau_k"] * h)
+    setup_s = time.perf_counter() - t0
+    tinfo = ctx.treecode_info()
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
+    yt, yd = torch.empty_like(x), torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.matvec(P, x, yt, precision=ibim.IBIM_F32T)
+    ctx.timing_enable(True)
+    ctx.timing_reset()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ctx.matvec(P, x, yt, precision=ibim.IBIM_F32T)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    tim = ctx.timing()
+    ctx.timing_enable(False)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    value = N * N * len(ms) / (sum(ms) * 1e-3)
+    pairs = (tinfo["near_steps"] + tinfo["far_steps"]) * 1024 * 256
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.matvec(P, x, yd)
+    e0.record(stream)
+    ctx.matvec(P, x, yd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    direct_ms = e0.elapsed_time(e1)
+    a, b = yd.cpu().numpy(), yt.cpu().numpy()
+    op_err = [float(np.linalg.norm(b[:N] - a[:N]) / np.linalg.norm(a[:N])),
+              float(np.linalg.norm(b[N:] - a[N:]) / np.linalg.norm(a[N:]))]
+    d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    solves = {}
+    for name, prec in (("treecode", ibim.IBIM_F32T), ("direct_f32", ibim.IBIM_F32C)):
+        t0 = time.perf_counter()
+        info = ctx.solve(P, d, precision=prec, tol=W["tol"], restart=W["restart"], maxit=1000, certify=0)
+        torch.cuda.synchronize()
+        solves[name] = {"s": time.perf_counter() - t0, "iters": info["iters"], "relres": info["relres"],
+                        "converged": info["converged"], "gpol_kcal": info["gpol_kcal"]}
+    from oracle import closed_forms as cf
+    Gs = cf.kirkwood_energy(W["R"], z, q, W["eps_in"], W["eps_out"], W["kappa"]) * ibim.KCAL_PER_E2_A
+    gt, gd = solves["treecode"]["gpol_kcal"], solves["direct_f32"]["gpol_kcal"]
+    extra = {"clocks": ck, "geometry_build_s": build_s, "treecode_setup_s": setup_s,
+             "treecode": dict(tinfo, theta=W["theta"], chebyshev_points_per_axis=6, pairs_per_application=pairs,
+                              pairs_per_s=pairs * len(ms) / (sum(ms) * 1e-3),
+                              list_kernel_ms=tim["pair_ms"] / max(1, tim["pair_launches"])),
+             "direct_f32_ms": direct_ms, "speedup_per_application": direct_ms / float(np.mean(ms)),
+             "operator_rel_err_vs_direct_f32": op_err, "solves": solves,
+             "speedup_solve": solves["direct_f32"]["s"] / solves["treecode"]["s"],
+             "gpol_rel_diff_treecode_vs_direct": abs(gt - gd) / abs(gd), "kirkwood_series_kcal": Gs,
+             "gpol_rel_err_vs_series": {"treecode": (gt - Gs) / Gs, "direct_f32": (gd - Gs) / Gs}}
+    cfg = dict(W, N=N, l2="256 MB buffer written between timed applications",
+               step="one treecode operator application (P2M/M2M, list kernel, fixup)",
+               f32_variant={"index": variant, "ctas_per_sm": bps})
+    _line(args, cfg, value, float(np.mean(ms)), extra)
+    ctx.close()
+
+
 def run_batched(args):
     """64 globules (atoms log-uniform in [50, 3000], kappa ~ U[0, 0.2]) solved
     together by ibim_solve_batch; the timed step is a bounded number of
@@ -643,19 +736,24 @@ def run_profile(args):
         variant, bps = args.variant, args.ctas_per_sm
     else:
         variant, bps, _ = ctx.autotune(P)
+    prec = ibim.IBIM_F32C
+    if args.treecode_theta > 0:
+        ctx.treecode_setup(args.treecode_theta, W["tau_k"] * h)
+        prec = ibim.IBIM_F32T
     x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
     y = torch.empty_like(x)
     for _ in range(args.warmup):
-        ctx.matvec(P, x, y, precision=ibim.IBIM_F32C)
+        ctx.matvec(P, x, y, precision=prec)
     torch.cuda.synchronize()
     ctx.timing_enable(True)
     ctx.timing_reset()
     for _ in range(args.steps):
-        ctx.matvec(P, x, y, precision=ibim.IBIM_F32C)
+        ctx.matvec(P, x, y, precision=prec)
     torch.cuda.synchronize()
     tim = ctx.timing()
     ctx.close()
     print(json.dumps({"mode": "profile", "N": N, "variant": variant, "ctas_per_sm": bps,
+                      "treecode_theta": args.treecode_theta,
                       "pair_ms": tim["pair_ms"] / max(1, tim["pair_launches"])}), flush=True)
 
 
@@ -672,7 +770,9 @@ def main():
                     help="operator applications only (for profiler captures); prints no bench line")
     ap.add_argument("--variant", type=int, default=None, help="with --profile: FP32 kernel variant (no autotune)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
-    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein", "batched", "learned"],
+    ap.add_argument("--treecode-theta", type=float, default=0.0,
+                    help="with --profile: apply the treecode operator (IBIM_F32T) with this theta instead")
+    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein", "batched", "learned", "treecode"],
                     help="kirkwood (default, the headline line) or an opt-in workload")
     ap.add_argument("--protein-fp64", action="store_true",
                     help="with --workload protein: also time the plain FP64 GPU solve (about ten minutes)")
@@ -696,6 +796,8 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.workload == "treecode":
+        run_treecode(args)
     elif args.workload == "protein":
         run_protein(args)
     elif args.workload == "batched":

@@ -279,17 +279,18 @@ struct Targets {
 // the thread's slot-0 target, slot q adding q * qstride.  LIST kernels may
 // pass force_far for a tile whose every source is known to lie at least
 // far_dist from every target (treecode proxies): it then takes the far-field
-// branch without the per-chunk distance test.
+// branch without the per-chunk distance test; n_chunks < kChunksPerTile
+// skips the tile's trailing chunks (all padding).
 template <int TPT, bool LIST = false>
 __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* tfrm, bool have_frames,
                                           const float4* sb, const float4* sfrm, const F32Consts& k,
                                           float (&S1)[TPT], float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
                                           const Geo64& g64, int64_t gi0, int qstride, int64_t j0, int64_t N,
-                                          bool force_far = false)
+                                          bool force_far = false, int n_chunks = kChunksPerTile)
 {
     const FarConsts fc = far_consts(k);
 #pragma unroll 1
-    for (int c = 0; c < kChunksPerTile; ++c) {
+    for (int c = 0; c < (LIST ? n_chunks : kChunksPerTile); ++c) {
         // targets in the source chunk's frame; far test on the two bounding spheres
         float3 X[TPT];
         const bool forced = LIST && force_far;

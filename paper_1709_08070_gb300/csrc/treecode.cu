@@ -43,6 +43,7 @@ namespace ibim {
 
 constexpr int kCheb = 6;
 constexpr int kProxies = kCheb * kCheb * kCheb;  // 216 of a 256-node tile
+constexpr int kProxyChunks = (kProxies + kChunk - 1) / kChunk;  // 7 chunks hold them (the 8th is padding)
 constexpr int kTcTpt = 2, kTcThreads = 512;
 constexpr int kTcTTile = kTcTpt * kTcThreads;  // 1024 targets
 constexpr double kTcMinHalf = 1e-3;            // smallest proxy-cube half side (A)
@@ -99,23 +100,30 @@ void tc_destroy(TreeCode* t)
 
 // ------------------------------------------------------------------ device
 
-// Lagrange basis of the 6 Chebyshev points of [-1, 1] at u (barycentric
-// form; u on a point gives the unit vector).
-__device__ __forceinline__ void cheb_basis(double u, float (&l)[kCheb])
+// The 6 Chebyshev points of the second kind cos(k pi / 5) on [-1, 1].
+__device__ __forceinline__ double cheb_point(int k)
 {
-    double q[kCheb], s = 0.0;
+    const double c1 = 0.8090169943749475, c2 = 0.30901699437494745;  // cos(pi/5), cos(2 pi/5)
+    return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? c2 : k == 3 ? -c2 : k == 4 ? -c1 : -1.0;
+}
+
+// Lagrange basis of those points at u in FP32 (barycentric form, weights
+// (-1)^k halved at the ends; u on a point gives the unit vector).
+__device__ __forceinline__ void cheb_basis(float u, float (&l)[kCheb])
+{
+    float q[kCheb], s = 0.0f;
     int hit = -1;
 #pragma unroll
     for (int k = 0; k < kCheb; ++k) {
-        const double t = cospi((double)k / (double)(kCheb - 1));
-        const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == kCheb - 1) ? 0.5 : 1.0);
-        const double d = u - t;
-        if (d == 0.0) hit = k;
+        const float wk = ((k & 1) ? -1.0f : 1.0f) * ((k == 0 || k == kCheb - 1) ? 0.5f : 1.0f);
+        const float d = u - (float)cheb_point(k);
+        if (d == 0.0f) hit = k;
         q[k] = wk / d;
         s += q[k];
     }
+    const float rs = 1.0f / s;
 #pragma unroll
-    for (int k = 0; k < kCheb; ++k) l[k] = (hit >= 0) ? (k == hit ? 1.0f : 0.0f) : (float)(q[k] / s);
+    for (int k = 0; k < kCheb; ++k) l[k] = (hit >= 0) ? (k == hit ? 1.0f : 0.0f) : q[k] * rs;
 }
 
 // Proxies of the clusters ids[0 .. gridDim.x) (one CTA of kF32STile threads
@@ -153,13 +161,13 @@ __global__ void __launch_bounds__(kF32STile)
     };
     auto set_source = [&](double x, double y, double z, float4 d) {
         float l[kCheb];
-        cheb_basis((x - cube.x) * inv, l);
+        cheb_basis((float)((x - cube.x) * inv), l);
 #pragma unroll
         for (int k = 0; k < kCheb; ++k) lw[tid][k] = l[k];
-        cheb_basis((y - cube.y) * inv, l);
+        cheb_basis((float)((y - cube.y) * inv), l);
 #pragma unroll
         for (int k = 0; k < kCheb; ++k) lw[tid][kCheb + k] = l[k];
-        cheb_basis((z - cube.z) * inv, l);
+        cheb_basis((float)((z - cube.z) * inv), l);
 #pragma unroll
         for (int k = 0; k < kCheb; ++k) lw[tid][2 * kCheb + k] = l[k];
         dens[tid] = d;
@@ -191,8 +199,7 @@ __global__ void __launch_bounds__(kF32STile)
                 const float4 B = pr[1], C = pr[2], D = pr[3];
                 const bool odd = tid & 1;
                 const float4 d = odd ? make_float4(C.y, C.w, D.y, B.w) : make_float4(C.x, C.z, D.x, B.z);
-                set_source(cb.x + cb.w * cospi((double)qx / (kCheb - 1)), cb.y + cb.w * cospi((double)qy / (kCheb - 1)),
-                           cb.z + cb.w * cospi((double)qz / (kCheb - 1)), d);
+                set_source(cb.x + cb.w * cheb_point(qx), cb.y + cb.w * cheb_point(qy), cb.z + cb.w * cheb_point(qz), d);
             }
             accumulate(kProxies);
         }
@@ -200,9 +207,8 @@ __global__ void __launch_bounds__(kF32STile)
 
     // proxy tile: positions relative to the cube centre (the tile's chunk frame)
     if (tid < kProxies) {
-        outp[tid] = make_float4((float)(cube.w * cospi((double)kx / (kCheb - 1))),
-                                (float)(cube.w * cospi((double)ky / (kCheb - 1))),
-                                (float)(cube.w * cospi((double)kz / (kCheb - 1))), ab);
+        outp[tid] = make_float4((float)(cube.w * cheb_point(kx)), (float)(cube.w * cheb_point(ky)),
+                                (float)(cube.w * cheb_point(kz)), ab);
         outd[tid] = make_float4(ax, ay, az, 0.0f);
     } else {
         outp[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -310,7 +316,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
         for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
         if (!idle)
             tile_sums<TPT, true>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64,
-                                 gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles);
+                                 gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles,
+                                 st >= s.n_real_tiles ? kProxyChunks : kChunksPerTile);
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             D1[q] += (double)S1[q] - (double)C1[q];
