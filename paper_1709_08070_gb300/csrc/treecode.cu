@@ -67,7 +67,7 @@ struct TreeCode {
     int n_clusters = 0;
     int64_t n_t = 0;           // target tiles
     int64_t near_steps = 0, far_steps = 0, total = 0;
-    int64_t per_cta = 0;
+    int64_t Lb = 0, Ls = 0, nseg = 0;  // large segments (one per CTA) of Lb steps, then small ones of Ls
     int grid = 0;
     std::vector<int> level_off;  // clusters by height: ids[level_off[h] .. level_off[h + 1])
     int64_t* d_j0 = nullptr;
@@ -79,7 +79,8 @@ struct TreeCode {
     float4* d_frm = nullptr;       // chunk frames of all those tiles
     int64_t* d_row_ptr = nullptr;  // n_t + 1
     int32_t* d_step_src = nullptr; // total: source tile of each step
-    double* d_part = nullptr;      // (grid + n_t) x 2 x kTcTTile
+    double* d_part = nullptr;      // (nseg + n_t) x 2 x kTcTTile
+    unsigned long long* d_ctr = nullptr;  // small-segment counter (reset by the leaf-level upward launch)
 };
 
 void tc_destroy(TreeCode* t)
@@ -95,6 +96,7 @@ void tc_destroy(TreeCode* t)
     cudaFree(t->d_row_ptr);
     cudaFree(t->d_step_src);
     cudaFree(t->d_part);
+    cudaFree(t->d_ctr);
     delete t;
 }
 
@@ -131,9 +133,11 @@ __device__ __forceinline__ void cheb_basis(float u, float (&l)[kCheb])
 // otherwise; written as the cluster's proxy tile in the source payload format.
 __global__ void __launch_bounds__(kF32STile)
     tc_upward_kernel(TcClusters cl, const int* __restrict__ ids, const double* __restrict__ geo, int64_t N,
-                     int64_t n_real_tiles, float4* __restrict__ src, const int* __restrict__ skip)
+                     int64_t n_real_tiles, float4* __restrict__ src, unsigned long long* __restrict__ ctr,
+                     const int* __restrict__ skip)
 {
     if (skip != nullptr && *skip) return;
+    if (ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0ull;  // the list kernel's segment counter
     __shared__ float lw[kF32STile][3 * kCheb];
     __shared__ float4 dens[kF32STile];   // (d.x, d.y, d.z, b) of each source of the pass
     __shared__ float4 outp[kF32STile];   // (rel.x, rel.y, rel.z, b) of each proxy
@@ -229,16 +233,34 @@ __global__ void __launch_bounds__(kF32STile)
 struct TcSchedule {
     const int64_t* row_ptr;   // n_t + 1, row t = steps [row_ptr[t], row_ptr[t + 1])
     const int32_t* step_src;  // source tile of each step (>= n_real_tiles: a proxy tile)
-    int64_t n_t, total, per_cta, n_real_tiles;
+    int64_t n_t, total, n_real_tiles;
+    int64_t Lb, nbig, Ls, nseg;  // segments: nbig of Lb steps, then small ones of Ls steps
 };
 
+// First step of segment q (total for q = nseg) and the segment of step u.
+__host__ __device__ __forceinline__ int64_t tc_seg_start(const TcSchedule& s, int64_t q)
+{
+    const int64_t v = q < s.nbig ? q * s.Lb : s.nbig * s.Lb + (q - s.nbig) * s.Ls;
+    return v < s.total ? v : s.total;
+}
+__host__ __device__ __forceinline__ int64_t tc_seg_of(const TcSchedule& s, int64_t u)
+{
+    const int64_t big = s.nbig * s.Lb;
+    return u < big ? u / s.Lb : s.nbig + (u - big) / s.Ls;
+}
+
 // The FP32 pair sums over the interaction lists: as pair_f32_kernel, with the
-// (target tile, source tile) of each step read from the lists.
+// (target tile, source tile) of each step read from the lists.  The step
+// sequence is cut into one large segment per CTA (9/10 of an even share)
+// and small segments handed out by a counter, so that CTAs whose steps were
+// cheaper (far steps skip the tube tests) take more of the rest.  Partials:
+// one per (segment, target tile), slot = segment + tile.
 template <int TPT, int MINB, int THREADS>
 __global__ void __launch_bounds__(THREADS, MINB)
     tc_pair_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm, const float4* __restrict__ src,
                    const float4* __restrict__ frames, int64_t N, TcSchedule s, F32Consts k,
-                   double* __restrict__ part, unsigned* __restrict__ err, const int* __restrict__ skip, Geo64 g64)
+                   double* __restrict__ part, unsigned long long* __restrict__ ctr, unsigned* __restrict__ err,
+                   const int* __restrict__ skip, Geo64 g64)
 {
     constexpr int TTILE = THREADS * TPT;
     constexpr int NW = THREADS / 32;
@@ -246,34 +268,33 @@ __global__ void __launch_bounds__(THREADS, MINB)
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
     __shared__ __align__(8) StagePipe pipe;
+    __shared__ int64_t seg_next[2];
+    __shared__ int abort_sh;  // a bounded wait gave up: every warp leaves after the segment barrier
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int64_t s0 = (int64_t)blockIdx.x * s.per_cta;
-    const int64_t s1 = (s0 + s.per_cta < s.total) ? s0 + s.per_cta : s.total;
-    if (s0 >= s1) return;
-
-    if (tid == 0) pipe_init(pipe, NW);
+    if (tid == 0) {
+        pipe_init(pipe, NW);
+        abort_sh = 0;
+    }
     __syncthreads();
 
+    // ring position of step u of the current segment: done + (u - s0) = u + off
+    int64_t s0 = 0, s1 = 0, off = 0, done = 0;
     auto issue = [&](int64_t u) {
         const int64_t st = s.step_src[u];
-        const int stage = (int)((u - s0) % kF32Stages);
+        const int stage = (int)((u + off) % kF32Stages);
         pipe_issue(pipe, stg[stage], stage, src + st * (kF32STile / 2) * kPairF4, frames + st * 2 * kChunksPerTile);
     };
-    if (tid == 0)
-        for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
+    auto give_up = [&]() {
+        if (lane == 0) {
+            atomicOr(err, kDevErrTimeout);
+            *(volatile int*)&abort_sh = 1;
+        }
+    };
 
-    // the row holding step s0: the last t with row_ptr[t] <= s0
-    int64_t lo = 0, hi = s.n_t;
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (s.row_ptr[mid] <= s0) lo = mid;
-        else hi = mid;
-    }
-    int64_t t = lo;
-    int64_t row_end = s.row_ptr[t + 1];
+    int64_t t = 0, row_end = 0;
     Targets<TPT> T;
     int64_t gi0 = 0;
     bool idle = false;
@@ -301,59 +322,105 @@ __global__ void __launch_bounds__(THREADS, MINB)
         }
         __syncwarp();
     };
-    load_targets(t);
 
-    for (int64_t u = s0; u < s1; ++u) {
-        const int stage = (int)((u - s0) % kF32Stages);
-        const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
-        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
-            if (lane == 0) atomicOr(err, kDevErrTimeout);
-            return;
+    int64_t seg = blockIdx.x;
+    int sp = 0;
+    while (seg < s.nseg) {
+        s0 = tc_seg_start(s, seg);
+        s1 = tc_seg_start(s, seg + 1);
+        off = done - s0;
+        // every stage is free here: thread 0 waited for each earlier step's release
+        if (tid == 0) {
+            ptx::fence_proxy_async_smem();
+            for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
         }
-        const int64_t st = s.step_src[u];
-        float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
-        if (!idle)
-            tile_sums<TPT, true>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64,
-                                 gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles,
-                                 st >= s.n_real_tiles ? kProxyChunks : kChunksPerTile);
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) {
-            D1[q] += (double)S1[q] - (double)C1[q];
-            D2[q] += (double)S2[q] - (double)C2[q];
+        // the row holding step s0: the last t with row_ptr[t] <= s0
+        int64_t lo = 0, hi = s.n_t;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (s.row_ptr[mid] <= s0) lo = mid;
+            else hi = mid;
         }
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
-        if (warp == 0) {  // thread 0 refills the stage of step u - 1
-            bool ok = true;
-            if (lane == 0 && u > s0 && u - 1 + kF32Stages < s1) {
-                const int64_t v = u - 1 - s0;
-                ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(v % kF32Stages)], (uint32_t)((v / kF32Stages) & 1),
-                                            kWaitLimitNs);
-                if (ok) {
-                    ptx::fence_proxy_async_smem();
-                    issue(u - 1 + kF32Stages);
-                } else {
-                    atomicOr(err, kDevErrTimeout);
-                }
+        t = lo;
+        row_end = s.row_ptr[t + 1];
+        load_targets(t);
+
+        bool bad = false;
+        for (int64_t u = s0; u < s1; ++u) {
+            const int stage = (int)((u + off) % kF32Stages);
+            const uint32_t parity = (uint32_t)(((u + off) / kF32Stages) & 1);
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+                give_up();
+                bad = true;
+                break;
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
-        }
-
-        if (u + 1 == row_end || u + 1 == s1) {
-            double* dst = part + ((int64_t)blockIdx.x + t) * 2 * TTILE;
+            const int64_t st = s.step_src[u];
+            float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+            if (!idle)
+                tile_sums<TPT, true>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2,
+                                     g64, gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles,
+                                     st >= s.n_real_tiles ? kProxyChunks : kChunksPerTile);
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
-                dst[q * THREADS + tid] = D1[q];
-                dst[TTILE + q * THREADS + tid] = D2[q];
+                D1[q] += (double)S1[q] - (double)C1[q];
+                D2[q] += (double)S2[q] - (double)C2[q];
             }
-            if (u + 1 < s1) {  // rows are never empty: the next step starts row t + 1
-                ++t;
-                row_end = s.row_ptr[t + 1];
-                load_targets(t);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+            if (warp == 0) {  // thread 0 refills the stage of step u - 1
+                bool ok = true;
+                if (lane == 0 && u > s0 && u - 1 + kF32Stages < s1) {
+                    const int64_t v = u - 1 + off;
+                    ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(v % kF32Stages)], (uint32_t)((v / kF32Stages) & 1),
+                                                kWaitLimitNs);
+                    if (ok) {
+                        ptx::fence_proxy_async_smem();
+                        issue(u - 1 + kF32Stages);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    give_up();
+                    bad = true;
+                    break;
+                }
+            }
+
+            if (u + 1 == row_end || u + 1 == s1) {
+                double* dst = part + (seg + t) * 2 * TTILE;
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) {
+                    dst[q * THREADS + tid] = D1[q];
+                    dst[TTILE + q * THREADS + tid] = D2[q];
+                }
+                if (u + 1 < s1) {  // rows are never empty: the next step starts row t + 1
+                    ++t;
+                    row_end = s.row_ptr[t + 1];
+                    load_targets(t);
+                }
             }
         }
+        // before the next segment reuses the stages: every step of this one released
+        if (warp == 0) {
+            bool ok = !bad;
+            if (ok && lane == 0) {
+                const int64_t first = (s1 - s0 > kF32Stages) ? s1 - kF32Stages : s0;
+                for (int64_t v = first; v < s1 && ok; ++v) {
+                    const int64_t w = v + off;
+                    ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(w % kF32Stages)], (uint32_t)((w / kF32Stages) & 1),
+                                                kWaitLimitNs);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok && !bad) give_up();
+            if (lane == 0) seg_next[sp] = ok ? s.nbig + (int64_t)atomicAdd(ctr, 1ull) : s.nseg;
+        }
+        done += s1 - s0;
+        __syncthreads();
+        if (*(volatile int*)&abort_sh) return;
+        seg = seg_next[sp];
+        sp ^= 1;
     }
 }
 
@@ -368,8 +435,8 @@ __global__ void tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, i
     double* y = out.base + (out.kidx ? (int64_t)(*out.kidx + out.koff) * out.stride : 0);
     const int64_t t = i / kTcTTile;
     const int64_t l = i - t * kTcTTile;
-    const int64_t c0 = s.row_ptr[t] / s.per_cta;
-    const int64_t c1 = (s.row_ptr[t + 1] - 1) / s.per_cta;
+    const int64_t c0 = tc_seg_of(s, s.row_ptr[t]);
+    const int64_t c1 = tc_seg_of(s, s.row_ptr[t + 1] - 1);
     double a1 = 0.0, a2 = 0.0;
     for (int64_t c = c0; c <= c1; ++c) {
         const double* q = part + (c + t) * 2 * kTcTTile;
@@ -568,8 +635,11 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, 1, kTcThreads>, kTcThreads, 0);
     const int64_t cap = (int64_t)std::max(1, occ) * c->num_sms;
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>(cap, T->total));
-    T->per_cta = (T->total + g - 1) / g;
-    T->grid = (int)((T->total + T->per_cta - 1) / T->per_cta);
+    T->Lb = std::max<int64_t>(1, (9 * T->total) / (10 * g));  // g Lb <= total as g <= total
+    const int64_t rest = T->total - g * T->Lb;
+    T->Ls = std::max<int64_t>(1, (rest + 16 * g - 1) / (16 * g));
+    T->nseg = g + (rest + T->Ls - 1) / T->Ls;
+    T->grid = (int)g;
 
     ibim_status st = IBIM_OK;
     auto chk = [&](ibim_status s) {
@@ -587,7 +657,8 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
         cudaError_t e = cudaMalloc((void**)&T->d_src, sizeof(float4) * (size_t)(n_real + nc) * (kF32STile / 2) * kPairF4);
         if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_frm, sizeof(float4) * (frm_real + pfrm.size()));
         if (e == cudaSuccess)
-            e = cudaMalloc((void**)&T->d_part, sizeof(double) * (size_t)(T->grid + n_t) * 2 * kTcTTile);
+            e = cudaMalloc((void**)&T->d_part, sizeof(double) * (size_t)(T->nseg + n_t) * 2 * kTcTTile);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_ctr, sizeof(unsigned long long));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(T->d_frm, c->d_frames, sizeof(float4) * frm_real, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess)
@@ -620,15 +691,17 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
         const int n = T->level_off[h + 1] - T->level_off[h];
         if (n == 0) continue;
         tc_upward_kernel<<<n, kF32STile, 0, c->stream>>>(cl, T->d_ids + T->level_off[h], c->d_geo64, N,
-                                                         T->n_real_tiles, T->d_src, d_skip);
+                                                         T->n_real_tiles, T->d_src, h == 0 ? T->d_ctr : nullptr,
+                                                         d_skip);
         count_launch(c);
         IBIM_CUDA(cudaGetLastError());
     }
-    const TcSchedule s{T->d_row_ptr, T->d_step_src, T->n_t, T->total, T->per_cta, T->n_real_tiles};
+    const TcSchedule s{T->d_row_ptr, T->d_step_src, T->n_t, T->total, T->n_real_tiles,
+                       T->Lb, (int64_t)T->grid, T->Ls, T->nseg};
     const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * N, 1, N};
     IBIM_TRY(timing_begin(c));
     tc_pair_kernel<kTcTpt, 1, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
-        c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, c->d_err, d_skip, g64);
+        c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, T->d_ctr, c->d_err, d_skip, g64);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_TRY(timing_end(c, (T->near_steps + T->far_steps) * (int64_t)kTcTTile * kF32STile));
