@@ -38,7 +38,16 @@ Structure (the tiling is chosen so that a GPU can stream proxies like sources):
     is then at least far_dist, so no proxy lies in the regularisation tube
     (Sec. 2.2.1) and the kernels need no near-field care;
   * lists by depth-first traversal from the root: far clusters take proxies,
-    a one-tile cluster that is not far is summed directly.
+    a one-tile cluster that is not far is summed directly;
+  * target-side interpolation (optional): a far cluster that is also far from
+    the target tile's own proxy cube (radius r_Tc = half side x sqrt(3):
+    r_Tc + r_C <= theta D and D >= far_dist + r_Tc + r_C + kFarMargin) is
+    evaluated at the tile's n^3 target proxies instead of its targets.  y1 is
+    a scalar function of the target position and y2 = n_x . V(x) with the
+    vector field
+        V = [g d - (3 - B) (r.d / rho^2) r + (1 - th2 A) b r] / (4 pi rho^3),
+    g = 1 - A, so the four fields (y1, V) are interpolated from the target
+    proxies to the targets with the same tensor-product Lagrange basis.
 
 Parity: pinned by polynomial reproduction of the interpolation, the
 child-to-parent transfer identity, agreement with the direct operator when no
@@ -109,6 +118,12 @@ def split_point(n):
     return B * max(1, int(math.floor(n / (2.0 * B) + 0.5)))
 
 
+def target_cube(centre, half_extent):
+    """Proxy cube of a target tile: about its box centre, the largest half
+    extent (at least kMinHalf) as half side."""
+    return centre, max(max(half_extent[0], half_extent[1], half_extent[2]), kMinHalf)
+
+
 class TileTree:
     """Clusters of source tiles and the target tiles of an ordered node set."""
 
@@ -124,11 +139,15 @@ class TileTree:
         self.n_t = -(-self.N // ttile)
         self.t_centre = np.zeros((self.n_t, 3))
         self.t_radius = np.zeros(self.n_t)
+        self.t_half = np.zeros(self.n_t)    # target proxy cube half side
+        self.t_cradius = np.zeros(self.n_t)  # its half-diagonal
         for t in range(self.n_t):
             mn, mx = self._box(t * ttile, min((t + 1) * ttile, self.N))
             self.t_centre[t] = 0.5 * (mn + mx)
             e = 0.5 * (mx - mn)
             self.t_radius[t] = math.sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2])
+            _, self.t_half[t] = target_cube(self.t_centre[t], e)
+            self.t_cradius[t] = math.sqrt(3.0 * self.t_half[t] * self.t_half[t])
 
     def _box(self, j0, j1):
         seg = self.xs[j0:j1]
@@ -162,24 +181,37 @@ class TileTree:
         rT = self.t_radius[t]
         return (rT + c.radius <= theta * D) and (D >= far_dist + rT + c.radius + kFarMargin)
 
-    def lists(self, theta, tau_max):
-        """Per target tile: (near source tiles, far clusters), depth-first order."""
+    def far_interp(self, t, ci, theta, far_dist):
+        """Far also from the target tile's proxy cube (target-side interpolation)."""
+        c = self.clusters[ci]
+        d = self.t_centre[t] - c.centre
+        D = math.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
+        rT = self.t_cradius[t]
+        return (rT + c.radius <= theta * D) and (D >= far_dist + rT + c.radius + kFarMargin)
+
+    def lists(self, theta, tau_max, interp=False):
+        """Per target tile: (near source tiles, far clusters), depth-first order;
+        with interp, (near, far, far_interp): far clusters that pass the target
+        cube's test go to far_interp instead of far."""
         fd = max(2.0 * tau_max, 1.5) * 1.001 + 1e-3
         out = []
         for t in range(self.n_t):
-            near, far = [], []
+            near, far, fint = [], [], []
             stack = [0]
             while stack:
                 ci = stack.pop()
                 c = self.clusters[ci]
                 if self.far(t, ci, theta, fd):
-                    far.append(ci)
+                    if interp and self.far_interp(t, ci, theta, fd):
+                        fint.append(ci)
+                    else:
+                        far.append(ci)
                 elif not c.children:
                     near.append(c.j0 // self.stile)
                 else:
                     stack.append(c.children[1])
                     stack.append(c.children[0])
-            out.append((near, far))
+            out.append((near, far, fint) if interp else (near, far))
         return out
 
 
@@ -211,6 +243,28 @@ def far_kernels(x, nx, t, d, beta, phys):
     return y1, y2
 
 
+def far_fields(s, t, d, beta, phys):
+    """The fields (y1, V) at points s of proxies at t with densities (d, beta):
+    y1 as in far_kernels and V with y2 = n_x . V (Sec. 2.2 kernels, linear in
+    the target normal).  Returns (m,) and (m, 3)."""
+    r = s[:, None, :] - t[None, :, :]
+    rho2 = np.einsum("ijk,ijk->ij", r, r)
+    rho = np.sqrt(rho2)
+    s_d = np.einsum("ijk,jk->ij", r, d)
+    kap = phys.kappa
+    E = np.exp(-kap * rho)
+    A = E * (1.0 + kap * rho)
+    B = E * (3.0 + 3.0 * kap * rho + kap * kap * rho2)
+    th1 = phys.eps_out / phys.eps_in
+    th2 = phys.eps_in / phys.eps_out
+    fp = 4.0 * np.pi
+    rho3 = rho2 * rho
+    y1 = (s_d * (1.0 - th1 * A) / (fp * rho3) - (1.0 - E) / (fp * rho) * beta[None, :]).sum(axis=1)
+    coef = (-(3.0 - B) * s_d / rho2 + (1.0 - th2 * A) * beta[None, :]) / (fp * rho3)
+    V = np.einsum("ij,jk->ik", (1.0 - A) / (fp * rho3), d) + np.einsum("ij,ijk->ik", coef, r)
+    return y1, V
+
+
 def cluster_densities(tree, ci, nrm, a, b, n):
     """Proxy densities of cluster ci: (proxies (n^3, 3), D (n^3, 3), beta (n^3,)),
     D_k = sum_j L_k(y_j) a_j m_j and beta_k = sum_j L_k(y_j) b_j over its nodes."""
@@ -222,10 +276,12 @@ def cluster_densities(tree, ci, nrm, a, b, n):
     return proxy_points(c.centre, c.half, n), D, beta
 
 
-def treecode_matvec(xs, nrm, w, phys, p, theta=0.5, n=6, tau_max=None, tree=None, lists=None):
+def treecode_matvec(xs, nrm, w, phys, p, theta=0.5, n=6, tau_max=None, tree=None, lists=None, interp=False):
     """(Lambda + K W) p with the far field of every target tile taken from the
     proxies of its far clusters and the rest summed exactly (tube rule
-    included) by the direct oracle."""
+    included) by the direct oracle; with interp, the far clusters that pass
+    the target cube's test act on the tile's target proxies and their fields
+    are interpolated to the targets."""
     xs, nrm, w = _orc._geom(xs, nrm, w)
     N = w.shape[0]
     p = _orc._f64(p, 2 * N)
@@ -234,12 +290,14 @@ def treecode_matvec(xs, nrm, w, phys, p, theta=0.5, n=6, tau_max=None, tree=None
         tree = TileTree(xs)
     stile, ttile = tree.stile, tree.ttile
     if lists is None:
-        lists = tree.lists(theta, tau_max)
+        lists = tree.lists(theta, tau_max, interp)
     a = w * p[:N]
     b = w * p[N:]
     cache = {}
     y = np.empty(2 * N)
-    for t, (near, far) in enumerate(lists):
+    for t, entry in enumerate(lists):
+        near, far = entry[0], entry[1]
+        fint = entry[2] if len(entry) > 2 else []
         i0, i1 = t * ttile, min((t + 1) * ttile, N)
         rows = np.arange(i0, i1)
         wn = np.zeros(N)
@@ -253,11 +311,26 @@ def treecode_matvec(xs, nrm, w, phys, p, theta=0.5, n=6, tau_max=None, tree=None
             f1, f2 = far_kernels(xs[i0:i1], nrm[i0:i1], tp, D, beta, phys)
             y1 = y1 + f1
             y2 = y2 + f2
+        if fint:
+            th = tree.t_half[t]
+            sp = proxy_points(tree.t_centre[t], th, n)
+            F1 = np.zeros(sp.shape[0])
+            FV = np.zeros((sp.shape[0], 3))
+            for ci in fint:
+                if ci not in cache:
+                    cache[ci] = cluster_densities(tree, ci, nrm, a, b, n)
+                tp, D, beta = cache[ci]
+                g1, gV = far_fields(sp, tp, D, beta, phys)
+                F1 += g1
+                FV += gV
+            M = interp_matrix(xs[i0:i1], tree.t_centre[t], th, n)
+            y1 = y1 + M @ F1
+            y2 = y2 + np.einsum("ik,ik->i", nrm[i0:i1], M @ FV)
         y[i0:i1] = y1
         y[N + i0:N + i1] = y2
     return y
 
 
 def list_sizes(lists):
-    """(near source tiles, far clusters) summed over target tiles."""
-    return sum(len(nr) for nr, _ in lists), sum(len(fr) for _, fr in lists)
+    """(near source tiles, far clusters[, far clusters by interpolation]) summed over target tiles."""
+    return tuple(sum(len(e[k]) for e in lists) for k in range(len(lists[0])))

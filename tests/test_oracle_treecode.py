@@ -151,3 +151,51 @@ def test_cubes_nest_and_hold_their_nodes():
         for ci in c.children:
             q = tree.clusters[ci]
             assert np.all(np.abs(q.centre - c.centre) + q.half <= c.half * (1 + 1e-12))
+
+
+def test_far_fields_equal_far_kernels_for_any_target_normal():
+    rng = np.random.default_rng(7)
+    for kappa, eps_in in ((0.1257, 2.0), (0.0, 1.0)):
+        P = oracle.Phys(eps_in, 80.0, kappa, 0.3)
+        s = rng.standard_normal((5, 3))
+        nx = rng.standard_normal((5, 3))
+        nx /= np.linalg.norm(nx, axis=1, keepdims=True)
+        t = np.array([7.0, -2.0, 3.0]) + rng.standard_normal((6, 3))
+        d, beta = rng.standard_normal((6, 3)), rng.standard_normal(6)
+        f1, f2 = tc.far_kernels(s, nx, t, d, beta, P)
+        g1, V = tc.far_fields(s, t, d, beta, P)
+        np.testing.assert_allclose(g1, f1, rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(np.einsum("ik,ik->i", nx, V), f2, rtol=1e-12, atol=1e-16)
+
+
+def test_target_interpolation_clears_the_tube_and_stays_accurate():
+    xs, nr, w = _cloud(n_per=1000)
+    N = xs.shape[0]
+    tau = 0.3
+    P = oracle.Phys(2.0, 80.0, 0.1257, tau)
+    p = inputs.random_vector(2 * N, seed=1)
+    ye = oracle.matvec(xs, nr, w, P, p)
+    tree = tc.TileTree(xs)
+    fd = max(2 * tau, 1.5) * 1.001 + 1e-3
+    lists = tree.lists(0.8, tau, interp=True)
+    sizes = tc.list_sizes(lists)
+    assert sizes[2] > 0
+    for t, (near, far, fint) in enumerate(lists):
+        sp = tc.proxy_points(tree.t_centre[t], tree.t_half[t], 6)
+        tx = xs[t * tree.ttile:min((t + 1) * tree.ttile, tree.N)]
+        assert np.all(np.abs(tx - tree.t_centre[t]) <= tree.t_half[t] * (1 + 1e-12))
+        for ci in fint:
+            c = tree.clusters[ci]
+            pr = tc.proxy_points(c.centre, c.half, 6)
+            assert np.sqrt(((sp[:, None, :] - pr[None, :, :]) ** 2).sum(-1)).min() >= fd
+    errs = []
+    for n in (4, 6):
+        y = tc.treecode_matvec(xs, nr, w, P, p, n=n, tree=tree, lists=lists)
+        errs.append(max(np.linalg.norm(y[:N] - ye[:N]) / np.linalg.norm(ye[:N]),
+                        np.linalg.norm(y[N:] - ye[N:]) / np.linalg.norm(ye[N:])))
+    y0 = tc.treecode_matvec(xs, nr, w, P, p, n=6, tree=tree, lists=tree.lists(0.8, tau))
+    e0 = max(np.linalg.norm(y0[:N] - ye[:N]) / np.linalg.norm(ye[:N]),
+             np.linalg.norm(y0[N:] - ye[N:]) / np.linalg.norm(ye[N:]))
+    print("target interpolation, theta 0.8, lists %s: error n = 4, 6: %s (source side only: %.2e)"
+          % (sizes, ["%.2e" % e for e in errs], e0))
+    assert errs[0] > errs[1] and errs[1] < 5.0 * e0 + 1e-9 and errs[1] < 1e-6
