@@ -453,12 +453,13 @@ def run_protein(args):
 
 TREECODE = {"workload": "kirkwood_sphere_large", "R": 60.0, "h": 0.5, "band_k": 2, "tau_k": 1.0, "n_charges": 50,
             "charge_ball": 48.0, "eps_in": 2.0, "eps_out": 80.0, "kappa": 0.1257, "tol": 1e-6, "restart": 64,
-            "theta": 0.7}
+            "theta": 0.7, "target_interp": 1}
 
 
 def run_treecode(args):
     """Kirkwood-type sphere three times the default size (R = 60 A, N = 722,830)
-    with the treecode operator (IBIM_F32T, theta 0.7): timed applications, the
+    with the treecode operator (IBIM_F32T, theta 0.7, target-side
+    interpolation of the well-separated far clusters): timed applications, the
     direct FP32 operator timed beside it, the operator difference, and one FP32
     solve to 1e-6 with each operator (energies against each other and against
     the Kirkwood series).  value = N^2 x applications / time: the interactions
@@ -480,7 +481,7 @@ def run_treecode(args):
     P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * h, 0)
     variant, bps, _ = ctx.autotune(P)
     t0 = time.perf_counter()
-    ctx.treecode_setup(W["theta"], W["tau_k"] * h)
+    ctx.treecode_setup(W["theta"], W["tau_k"] * h, W["target_interp"])
     setup_s = time.perf_counter() - t0
     tinfo = ctx.treecode_info()
     stream = torch.cuda.current_stream()
@@ -506,7 +507,7 @@ def run_treecode(args):
     ctx.timing_enable(False)
     ms = [a.elapsed_time(b) for a, b in ev]
     value = N * N * len(ms) / (sum(ms) * 1e-3)
-    pairs = (tinfo["near_steps"] + tinfo["far_steps"]) * 1024 * 256
+    pairs = (tinfo["near_steps"] * 256 + tinfo["far_steps"] * 224) * 1024 + tinfo["interp_steps"] * 216 * 224
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx.matvec(P, x, yd)
     e0.record(stream)
@@ -748,7 +749,7 @@ def run_profile(args):
         variant, bps, _ = ctx.autotune(P)
     prec = ibim.IBIM_F32C
     if args.treecode_theta > 0:
-        ctx.treecode_setup(args.treecode_theta, W["tau_k"] * h)
+        ctx.treecode_setup(args.treecode_theta, W["tau_k"] * h, args.treecode_interp)
         prec = ibim.IBIM_F32T
     x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
     y = torch.empty_like(x)
@@ -782,6 +783,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
     ap.add_argument("--treecode-theta", type=float, default=0.0,
                     help="with --profile: apply the treecode operator (IBIM_F32T) with this theta instead")
+    ap.add_argument("--treecode-interp", type=int, default=0, choices=[0, 1],
+                    help="with --treecode-theta: target-side interpolation of well-separated far clusters")
     ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein", "batched", "learned", "treecode"],
                     help="kirkwood (default, the headline line) or an opt-in workload")
     ap.add_argument("--protein-fp64", action="store_true",

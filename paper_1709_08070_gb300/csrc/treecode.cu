@@ -27,6 +27,14 @@
 // far_dist, so no proxy enters the regularisation tube (Sec. 2.2.1, tube
 // rule 0).  Lists come from a depth-first traversal from the root.
 //
+// Target-side interpolation (optional): a far cluster that is also far from
+// the target tile's own Chebyshev cube (r_Tc + r_C <= theta D, D >= far_dist +
+// r_Tc + r_C + 0.25 A, r_Tc the cube half-diagonal) is evaluated at the tile's
+// 216 target proxies instead of its 1024 targets (tc_m2l_kernel).  y1 is a
+// scalar field of the target position and y2 = n_x . V(x) with
+//   V = [g d - (3 - B) (r.d / rho^2) r + (1 - th2 A) b r] / (4 pi rho^3),
+// so the fixup interpolates the four fields (y1, V) to each target.
+//
 // Per operator application: pack the node payload into the tile buffer,
 // proxies of the leaves from their nodes (P2M), of each inner cluster from its
 // two children's proxies (M2M: exact for this interpolation, the parent's
@@ -80,7 +88,16 @@ struct TreeCode {
     int64_t* d_row_ptr = nullptr;  // n_t + 1
     int32_t* d_step_src = nullptr; // total: source tile of each step
     double* d_part = nullptr;      // (nseg + n_t) x 2 x kTcTTile
-    unsigned long long* d_ctr = nullptr;  // small-segment counter (reset by the leaf-level upward launch)
+    unsigned long long* d_ctr = nullptr;  // [0] list-kernel segments, [1] m2l tiles (reset by the leaf upward launch)
+    // target-side interpolation
+    int interp = 0;
+    int64_t interp_steps = 0, n_mtiles = 0;
+    int m2l_grid = 0;
+    int64_t* d_irow = nullptr;     // n_t + 1: interpolated far clusters of tile t = isrc[irow[t] .. irow[t + 1])
+    int32_t* d_isrc = nullptr;     // their proxy tiles
+    int32_t* d_mtiles = nullptr;   // target tiles with at least one such cluster
+    TcCube* d_tcube = nullptr;     // target proxy cube of each tile
+    double* d_fields = nullptr;    // n_t x 216 x (y1, Vx, Vy, Vz) at the target proxies
 };
 
 void tc_destroy(TreeCode* t)
@@ -97,6 +114,11 @@ void tc_destroy(TreeCode* t)
     cudaFree(t->d_step_src);
     cudaFree(t->d_part);
     cudaFree(t->d_ctr);
+    cudaFree(t->d_irow);
+    cudaFree(t->d_isrc);
+    cudaFree(t->d_mtiles);
+    cudaFree(t->d_tcube);
+    cudaFree(t->d_fields);
     delete t;
 }
 
@@ -137,7 +159,10 @@ __global__ void __launch_bounds__(kF32STile)
                      const int* __restrict__ skip)
 {
     if (skip != nullptr && *skip) return;
-    if (ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0ull;  // the list kernel's segment counter
+    if (ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {  // the list and m2l kernels' counters
+        ctr[0] = 0ull;
+        ctr[1] = 0ull;
+    }
     __shared__ float lw[kF32STile][3 * kCheb];
     __shared__ float4 dens[kF32STile];   // (d.x, d.y, d.z, b) of each source of the pass
     __shared__ float4 outp[kF32STile];   // (rel.x, rel.y, rel.z, b) of each proxy
@@ -424,16 +449,209 @@ __global__ void __launch_bounds__(THREADS, MINB)
     }
 }
 
-// y = Lambda p + (1/(4 pi)) (partials of the CTAs that covered the row).
-__global__ void tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, int64_t N, double lambda1,
-                                double lambda2, VecRef in, OutRef out, const int* __restrict__ skip)
+// The fields at target proxies of one packed pair of source proxies (the two
+// lanes of each float2): y1 as in pair_far2, and V with y2 = n_x . V.
+__device__ __forceinline__ void pair_field2(float2 Xx, float2 Xy, float2 Xz, const float4& A, const float4& B,
+                                            const float4& C, const float4& D, const FarConsts& c, float2& f1,
+                                            float2& vx, float2& vy, float2& vz)
 {
+    const float2 rx = __fadd2_rn(Xx, make_float2(A.x, A.y));
+    const float2 ry = __fadd2_rn(Xy, make_float2(A.z, A.w));
+    const float2 rz = __fadd2_rn(Xz, make_float2(B.x, B.y));
+    const float2 b = make_float2(B.z, B.w);
+    const float2 dx = make_float2(C.x, C.y), dy = make_float2(C.z, C.w), dz = make_float2(D.x, D.y);
+    float2 rr = __fmul2_rn(rx, rx);
+    rr = __ffma2_rn(ry, ry, rr);
+    rr = __ffma2_rn(rz, rz, rr);
+    float2 sd = __fmul2_rn(rx, dx);
+    sd = __ffma2_rn(ry, dy, sd);
+    sd = __ffma2_rn(rz, dz, sd);
+    const float2 inv = make_float2(ptx::rsqrt_approx(rr.x), ptx::rsqrt_approx(rr.y));
+    const float2 rho = __fmul2_rn(rr, inv);
+    const float2 ea = __fmul2_rn(rho, c.kl2e);
+    const float2 xn = __fmul2_rn(rho, c.nkappa);
+    const float2 E = make_float2(ptx::ex2_approx(ea.x), ptx::ex2_approx(ea.y));
+    const float2 En = __fmul2_rn(E, xn);
+    const float2 fn = __fadd2_rn(E, c.neg1);               // -(1 - E)
+    const float2 g = __ffma2_rn(fn, c.neg1, En);           // 1 - A
+    const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));  // -(3 - B)
+    const float2 inv2 = make_float2(ptx::rcp_approx(rr.x), ptx::rcp_approx(rr.y));
+    const float2 P = __fmul2_rn(inv2, inv);
+    const float2 u1 = __ffma2_rn(c.th1, g, c.omth1);
+    const float2 u2 = __ffma2_rn(c.th2, g, c.omth2);
+    f1 = __ffma2_rn(P, __fmul2_rn(u1, sd), f1);
+    f1 = __ffma2_rn(__fmul2_rn(fn, inv), b, f1);
+    const float2 v = __ffma2_rn(__fmul2_rn(hn, inv2), sd, __fmul2_rn(u2, b));
+    const float2 Pg = __fmul2_rn(P, g), Pv = __fmul2_rn(P, v);
+    vx = __ffma2_rn(Pg, dx, __ffma2_rn(Pv, rx, vx));
+    vy = __ffma2_rn(Pg, dy, __ffma2_rn(Pv, ry, vy));
+    vz = __ffma2_rn(Pg, dz, __ffma2_rn(Pv, rz, vz));
+}
+
+struct TcM2l {
+    const int64_t* irow;     // n_t + 1
+    const int32_t* isrc;     // proxy tile of each entry
+    const int32_t* mtiles;   // target tiles with entries
+    const TcCube* tcube;     // target proxy cube per tile
+    int64_t n_mtiles;
+};
+
+constexpr int kM2lThreads = kF32STile;  // one thread per target proxy (216 of 256 active)
+
+// Fields at the target proxies of each listed target tile from the proxy
+// tiles of its interpolated far clusters.  CTA b takes tile mtiles[b] and then
+// tiles from the counter; the source proxy tiles stream through the stage
+// ring as in the list kernel (ring position continued across tiles).
+__global__ void __launch_bounds__(kM2lThreads)
+    tc_m2l_kernel(const float4* __restrict__ src, const float4* __restrict__ frames, TcM2l m, F32Consts k,
+                  double* __restrict__ fields, unsigned long long* __restrict__ ctr, unsigned* __restrict__ err,
+                  const int* __restrict__ skip)
+{
+    constexpr int NW = kM2lThreads / 32;
     if (skip != nullptr && *skip) return;
+    __shared__ __align__(128) SourceStage stg[kF32Stages];
+    __shared__ __align__(8) StagePipe pipe;
+    __shared__ int64_t tile_next[2];
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const bool active = tid < kProxies;
+    const int lx = tid / (kCheb * kCheb), ly = (tid / kCheb) % kCheb, lz = tid % kCheb;
+    if (tid == 0) {
+        pipe_init(pipe, NW);
+        abort_sh = 0;
+    }
+    __syncthreads();
+    const FarConsts fc = far_consts(k);
+    int64_t done = 0, off = 0, e1 = 0;
+    auto issue = [&](int64_t u) {
+        const int64_t st = m.isrc[u];
+        const int stage = (int)((u + off) % kF32Stages);
+        pipe_issue(pipe, stg[stage], stage, src + st * (kF32STile / 2) * kPairF4, frames + st * 2 * kChunksPerTile);
+    };
+    auto give_up = [&]() {
+        if (lane == 0) {
+            atomicOr(err, kDevErrTimeout);
+            *(volatile int*)&abort_sh = 1;
+        }
+    };
+
+    int64_t q = blockIdx.x;
+    int sp = 0;
+    while (q < m.n_mtiles) {
+        const int64_t t = m.mtiles[q];
+        const int64_t e0 = m.irow[t];
+        e1 = m.irow[t + 1];
+        off = done - e0;
+        if (tid == 0) {
+            ptx::fence_proxy_async_smem();
+            for (int r = 0; r < kF32Stages && e0 + r < e1; ++r) issue(e0 + r);
+        }
+        const TcCube cube = m.tcube[t];
+        // target proxy relative to the cube centre; the centre as hi + lo floats
+        const float3 X0 = make_float3((float)(cube.w * cheb_point(lx)), (float)(cube.w * cheb_point(ly)),
+                                      (float)(cube.w * cheb_point(lz)));
+        const float hx = (float)cube.x, hy = (float)cube.y, hz = (float)cube.z;
+        const float3 lo = make_float3((float)(cube.x - (double)hx), (float)(cube.y - (double)hy),
+                                      (float)(cube.z - (double)hz));
+        double F1 = 0.0, FX = 0.0, FY = 0.0, FZ = 0.0;
+        bool bad = false;
+        for (int64_t u = e0; u < e1; ++u) {
+            const int stage = (int)((u + off) % kF32Stages);
+            const uint32_t parity = (uint32_t)(((u + off) / kF32Stages) & 1);
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+                give_up();
+                bad = true;
+                break;
+            }
+            if (active) {
+                const float4 mh = stg[stage].frm[0], ml = stg[stage].frm[1];  // one frame for the whole proxy tile
+                const float2 Xx = f2(X0.x + ((hx - mh.x) + (lo.x - ml.x)));
+                const float2 Xy = f2(X0.y + ((hy - mh.y) + (lo.y - ml.y)));
+                const float2 Xz = f2(X0.z + ((hz - mh.z) + (lo.z - ml.z)));
+                float2 f1 = make_float2(0.0f, 0.0f), vx = f1, vy = f1, vz = f1;
+                const float4* cb = stg[stage].buf;
+#pragma unroll 4
+                for (int pr = 0; pr < kProxyChunks * kPairsPerChunk; ++pr) {
+                    const float4 A = cb[kPairF4 * pr], B = cb[kPairF4 * pr + 1];
+                    const float4 C = cb[kPairF4 * pr + 2], D = cb[kPairF4 * pr + 3];
+                    pair_field2(Xx, Xy, Xz, A, B, C, D, fc, f1, vx, vy, vz);
+                }
+                F1 += (double)f1.x + (double)f1.y;
+                FX += (double)vx.x + (double)vx.y;
+                FY += (double)vy.x + (double)vy.y;
+                FZ += (double)vz.x + (double)vz.y;
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+            if (warp == 0) {  // thread 0 refills the stage of step u - 1
+                bool ok = true;
+                if (lane == 0 && u > e0 && u - 1 + kF32Stages < e1) {
+                    const int64_t v = u - 1 + off;
+                    ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(v % kF32Stages)], (uint32_t)((v / kF32Stages) & 1),
+                                                kWaitLimitNs);
+                    if (ok) {
+                        ptx::fence_proxy_async_smem();
+                        issue(u - 1 + kF32Stages);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    give_up();
+                    bad = true;
+                    break;
+                }
+            }
+        }
+        if (active && !bad) {
+            double* f = fields + (t * kProxies + tid) * 4;
+            f[0] = F1;
+            f[1] = FX;
+            f[2] = FY;
+            f[3] = FZ;
+        }
+        if (warp == 0) {  // every step of this tile released before the stages are reused
+            bool ok = !bad;
+            if (ok && lane == 0) {
+                const int64_t first = (e1 - e0 > kF32Stages) ? e1 - kF32Stages : e0;
+                for (int64_t v = first; v < e1 && ok; ++v) {
+                    const int64_t w = v + off;
+                    ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(w % kF32Stages)], (uint32_t)((w / kF32Stages) & 1),
+                                                kWaitLimitNs);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok && !bad) give_up();
+            if (lane == 0) tile_next[sp] = ok ? (int64_t)gridDim.x + (int64_t)atomicAdd(ctr, 1ull) : m.n_mtiles;
+        }
+        done += e1 - e0;
+        __syncthreads();
+        if (*(volatile int*)&abort_sh) return;
+        q = tile_next[sp];
+        sp ^= 1;
+    }
+}
+
+// y = Lambda p + (1/(4 pi)) (partials of the segments that covered the row
+// + the interpolated far fields of the row's target proxies, when it has any).
+// One 256-thread block lies inside one 1024-node target tile.
+__global__ void __launch_bounds__(256)
+    tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, int64_t N, double lambda1, double lambda2,
+                    VecRef in, OutRef out, TcM2l m, const double* __restrict__ fields,
+                    const double* __restrict__ geo, int interp, const int* __restrict__ skip)
+{
+    static_assert(kTcTTile % 256 == 0, "a fixup block lies in one target tile");
+    if (skip != nullptr && *skip) return;
+    __shared__ float fl[kProxies][4];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x) / kTcTTile;
+    const bool has = interp && m.irow[t + 1] > m.irow[t];
+    if (has)
+        for (int q = threadIdx.x; q < kProxies * 4; q += blockDim.x) (&fl[0][0])[q] = (float)fields[t * kProxies * 4 + q];
+    __syncthreads();
     if (i >= N) return;
     const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
     double* y = out.base + (out.kidx ? (int64_t)(*out.kidx + out.koff) * out.stride : 0);
-    const int64_t t = i / kTcTTile;
     const int64_t l = i - t * kTcTTile;
     const int64_t c0 = tc_seg_of(s, s.row_ptr[t]);
     const int64_t c1 = tc_seg_of(s, s.row_ptr[t + 1] - 1);
@@ -442,6 +660,30 @@ __global__ void tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, i
         const double* q = part + (c + t) * 2 * kTcTTile;
         a1 += q[l];
         a2 += q[kTcTTile + l];
+    }
+    if (has) {  // L2P: the tile's fields at this target
+        const TcCube cube = m.tcube[t];
+        const double inv = 1.0 / cube.w;
+        float wx[kCheb], wy[kCheb], wz[kCheb];
+        cheb_basis((float)((geo[i] - cube.x) * inv), wx);
+        cheb_basis((float)((geo[N + i] - cube.y) * inv), wy);
+        cheb_basis((float)((geo[2 * N + i] - cube.z) * inv), wz);
+        float F1 = 0.0f, FX = 0.0f, FY = 0.0f, FZ = 0.0f;
+        for (int ax = 0; ax < kCheb; ++ax)
+            for (int ay = 0; ay < kCheb; ++ay) {
+                const float wxy = wx[ax] * wy[ay];
+#pragma unroll
+                for (int az = 0; az < kCheb; ++az) {
+                    const float wgt = wxy * wz[az];
+                    const float* f = fl[(ax * kCheb + ay) * kCheb + az];
+                    F1 = fmaf(wgt, f[0], F1);
+                    FX = fmaf(wgt, f[1], FX);
+                    FY = fmaf(wgt, f[2], FY);
+                    FZ = fmaf(wgt, f[3], FZ);
+                }
+            }
+        a1 += (double)F1;
+        a2 += geo[3 * N + i] * (double)FX + geo[4 * N + i] * (double)FY + geo[5 * N + i] * (double)FZ;
     }
     y[i] = lambda1 * p[i] + kInv4Pi * a1;
     y[N + i] = lambda2 * p[N + i] + kInv4Pi * a2;
@@ -531,7 +773,7 @@ ibim_status upload(T** dst, const std::vector<T>& v)
 
 }  // namespace
 
-ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
 {
     const int64_t N = c->N;
     std::vector<double> xs(3 * (size_t)N);
@@ -545,7 +787,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
 
     // target tiles
     const int64_t n_t = (N + kTcTTile - 1) / kTcTTile;
-    std::vector<double> tcx(n_t), tcy(n_t), tcz(n_t), trad(n_t);
+    std::vector<double> tcx(n_t), tcy(n_t), tcz(n_t), trad(n_t), thalf(n_t), tcrad(n_t);
     for (int64_t t = 0; t < n_t; ++t) {
         double mn[3], mx[3];
         box_of(xs, N, t * kTcTTile, std::min<int64_t>((t + 1) * kTcTTile, N), mn, mx);
@@ -554,13 +796,15 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
         tcz[t] = 0.5 * (mn[2] + mx[2]);
         const double e0 = 0.5 * (mx[0] - mn[0]), e1 = 0.5 * (mx[1] - mn[1]), e2 = 0.5 * (mx[2] - mn[2]);
         trad[t] = std::sqrt((e0 * e0 + e1 * e1) + e2 * e2);
+        thalf[t] = std::max(std::max(std::max(e0, e1), e2), kTcMinHalf);  // target proxy cube
+        tcrad[t] = std::sqrt(3.0 * thalf[t] * thalf[t]);
     }
 
     // lists, depth-first from the root
     const int64_t n_real = padded_nodes(N) / kF32STile;
     const double fd = std::max(2.0 * tau_max, 1.5) * 1.001 + 1e-3;
-    std::vector<int64_t> row_ptr(n_t + 1, 0);
-    std::vector<int32_t> steps;
+    std::vector<int64_t> row_ptr(n_t + 1, 0), irow(n_t + 1, 0);
+    std::vector<int32_t> steps, isrc, mtiles;
     int64_t near_steps = 0, far_steps = 0;
     std::vector<int> stack;
     for (int64_t t = 0; t < n_t; ++t) {
@@ -573,7 +817,12 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
             const double D = std::sqrt((dx * dx + dy * dy) + dz * dz);
             const double rT = trad[t];
             const bool far = (rT + q.radius <= theta * D) && (D >= fd + rT + q.radius + kTcFarMargin);
-            if (far) {
+            const double rTc = tcrad[t];
+            const bool fint =
+                far && interp && (rTc + q.radius <= theta * D) && (D >= fd + rTc + q.radius + kTcFarMargin);
+            if (fint) {
+                isrc.push_back((int32_t)(n_real + ci));
+            } else if (far) {
                 steps.push_back((int32_t)(n_real + ci));
                 ++far_steps;
             } else if (q.c0 < 0) {
@@ -585,6 +834,8 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
             }
         }
         row_ptr[t + 1] = (int64_t)steps.size();
+        irow[t + 1] = (int64_t)isrc.size();
+        if (irow[t + 1] > irow[t]) mtiles.push_back((int32_t)t);
     }
     if (n_real + nc > INT32_MAX) return tc_fail(IBIM_ERR_ARG, "treecode: too many tiles");
 
@@ -611,6 +862,8 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
             pfrm[(size_t)i * 2 * kChunksPerTile + 2 * ch + 1] = f1;
         }
     }
+    std::vector<TcCube> tcube(n_t);
+    for (int64_t t = 0; t < n_t; ++t) tcube[t] = TcCube{tcx[t], tcy[t], tcz[t], thalf[t]};
     std::vector<int64_t> hj0(nc), hj1(nc);
     std::vector<int2> hch(nc);
     std::vector<TcCube> hcube(nc);
@@ -631,6 +884,9 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
     T->far_steps = far_steps;
     T->total = (int64_t)steps.size();
     T->level_off = level_off;
+    T->interp = interp ? 1 : 0;
+    T->interp_steps = (int64_t)isrc.size();
+    T->n_mtiles = (int64_t)mtiles.size();
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, 1, kTcThreads>, kTcThreads, 0);
     const int64_t cap = (int64_t)std::max(1, occ) * c->num_sms;
@@ -640,6 +896,9 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
     T->Ls = std::max<int64_t>(1, (rest + 16 * g - 1) / (16 * g));
     T->nseg = g + (rest + T->Ls - 1) / T->Ls;
     T->grid = (int)g;
+    int occm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, tc_m2l_kernel, kM2lThreads, 0);
+    T->m2l_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, occm) * c->num_sms, T->n_mtiles));
 
     ibim_status st = IBIM_OK;
     auto chk = [&](ibim_status s) {
@@ -652,13 +911,21 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max)
     chk(upload(&T->d_ids, ids));
     chk(upload(&T->d_row_ptr, row_ptr));
     chk(upload(&T->d_step_src, steps));
+    if (T->interp) {
+        chk(upload(&T->d_irow, irow));
+        chk(upload(&T->d_isrc, isrc));
+        chk(upload(&T->d_mtiles, mtiles));
+        chk(upload(&T->d_tcube, tcube));
+    }
     const size_t frm_real = (size_t)n_real * 2 * kChunksPerTile;
     if (st == IBIM_OK) {
         cudaError_t e = cudaMalloc((void**)&T->d_src, sizeof(float4) * (size_t)(n_real + nc) * (kF32STile / 2) * kPairF4);
         if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_frm, sizeof(float4) * (frm_real + pfrm.size()));
         if (e == cudaSuccess)
             e = cudaMalloc((void**)&T->d_part, sizeof(double) * (size_t)(T->nseg + n_t) * 2 * kTcTTile);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_ctr, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_ctr, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess && T->interp)
+            e = cudaMalloc((void**)&T->d_fields, sizeof(double) * (size_t)n_t * kProxies * 4);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(T->d_frm, c->d_frames, sizeof(float4) * frm_real, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess)
@@ -705,9 +972,16 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_TRY(timing_end(c, (T->near_steps + T->far_steps) * (int64_t)kTcTTile * kF32STile));
+    const TcM2l m{T->d_irow, T->d_isrc, T->d_mtiles, T->d_tcube, T->n_mtiles};
+    if (T->interp && T->n_mtiles > 0) {
+        tc_m2l_kernel<<<T->m2l_grid, kM2lThreads, 0, c->stream>>>(T->d_src, T->d_frm, m, f32_consts(k), T->d_fields,
+                                                                  T->d_ctr + 1, c->d_err, d_skip);
+        count_launch(c);
+        IBIM_CUDA(cudaGetLastError());
+    }
     const int bs = 256;
-    tc_fixup_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(T->d_part, s, N, k.lambda1, k.lambda2, in,
-                                                                          out, d_skip);
+    tc_fixup_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
+        T->d_part, s, N, k.lambda1, k.lambda2, in, out, m, T->d_fields, c->d_geo64, T->interp, d_skip);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -715,23 +989,25 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
 
 }  // namespace ibim
 
-extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau_max)
+extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau_max, int target_interp)
 {
     using namespace ibim;
     if (c == nullptr || !(theta > 0.0 && theta < 1.0) || !(tau_max > 0.0) || !std::isfinite(tau_max))
         return tc_fail(IBIM_ERR_ARG, "need a context, 0 < theta < 1 and a finite tau_max > 0");
     if (c->N <= 0 || c->d_frames == nullptr) return tc_fail(IBIM_ERR_STATE, "the context has no nodes");
-    return tc_setup(c, theta, tau_max);
+    if (target_interp != 0 && target_interp != 1) return tc_fail(IBIM_ERR_ARG, "target_interp must be 0 or 1");
+    return tc_setup(c, theta, tau_max, target_interp);
 }
 
-extern "C" ibim_status ibim_treecode_info(ibim_ctx* c, int64_t* near_steps, int64_t* far_steps, int64_t* clusters,
-                                          int64_t* target_tiles)
+extern "C" ibim_status ibim_treecode_info(ibim_ctx* c, int64_t* near_steps, int64_t* far_steps,
+                                          int64_t* interp_steps, int64_t* clusters, int64_t* target_tiles)
 {
     using namespace ibim;
     if (c == nullptr) return tc_fail(IBIM_ERR_ARG, "need a context");
     if (c->tc == nullptr) return tc_fail(IBIM_ERR_STATE, "no treecode: call ibim_treecode_setup");
     if (near_steps) *near_steps = c->tc->near_steps;
     if (far_steps) *far_steps = c->tc->far_steps;
+    if (interp_steps) *interp_steps = c->tc->interp_steps;
     if (clusters) *clusters = c->tc->n_clusters;
     if (target_tiles) *target_tiles = c->tc->n_t;
     return IBIM_OK;

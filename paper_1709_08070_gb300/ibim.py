@@ -85,8 +85,8 @@ _SIGS = {
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
-    "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double],
-    "ibim_treecode_info": [_V, _I64P, _I64P, _I64P, _I64P],
+    "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+    "ibim_treecode_info": [_V, _I64P, _I64P, _I64P, _I64P, _I64P],
     "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
@@ -374,16 +374,16 @@ def ibim_autotune(ctx, phys):
     return t.value, b.value, ms.value
 
 
-def ibim_treecode_setup(ctx, theta, tau_max):
+def ibim_treecode_setup(ctx, theta, tau_max, target_interp=0):
     """Build the treecode tree and interaction lists (IBIM_F32T operator)."""
-    _check(lib().ibim_treecode_setup(ctx, float(theta), float(tau_max)))
+    _check(lib().ibim_treecode_setup(ctx, float(theta), float(tau_max), int(target_interp)))
 
 
 def ibim_treecode_info(ctx):
-    """{'near_steps', 'far_steps', 'clusters', 'target_tiles'} of the current treecode setup."""
-    v = [ctypes.c_int64(0) for _ in range(4)]
+    """{'near_steps', 'far_steps', 'interp_steps', 'clusters', 'target_tiles'} of the current treecode setup."""
+    v = [ctypes.c_int64(0) for _ in range(5)]
     _check(lib().ibim_treecode_info(ctx, *[ctypes.byref(x) for x in v]))
-    return dict(zip(("near_steps", "far_steps", "clusters", "target_tiles"), (x.value for x in v)))
+    return dict(zip(("near_steps", "far_steps", "interp_steps", "clusters", "target_tiles"), (x.value for x in v)))
 
 
 def ibim_set_f32_variant(ctx, variant, ctas_per_sm=0):
@@ -550,8 +550,8 @@ class Context:
     def set_f32_variant(self, variant, ctas_per_sm=0):
         ibim_set_f32_variant(self.handle, variant, ctas_per_sm)
 
-    def treecode_setup(self, theta, tau_max):
-        ibim_treecode_setup(self.handle, theta, tau_max)
+    def treecode_setup(self, theta, tau_max, target_interp=0):
+        ibim_treecode_setup(self.handle, theta, tau_max, target_interp)
 
     def treecode_info(self):
         return ibim_treecode_info(self.handle)

@@ -28,20 +28,22 @@ def _rel(a, b, N):
     return (np.linalg.norm(a[:N] - b[:N]) / np.linalg.norm(b[:N]), np.linalg.norm(a[N:] - b[N:]) / np.linalg.norm(b[N:]))
 
 
-@pytest.mark.parametrize("theta,n_per", [(0.6, 1000), (0.8, 1500)])
-def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per):
+@pytest.mark.parametrize("theta,n_per,interp", [(0.6, 1000, 0), (0.8, 1500, 0), (0.6, 1000, 1), (0.8, 1500, 1)])
+def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp):
     xs, nr, w = inputs.sphere_cluster_cloud(n_per, CENTRES, radius=5.0, seed=4)
     N = xs.shape[0]
     tau = 0.3
     ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
-    ctx.treecode_setup(theta, tau)
+    ctx.treecode_setup(theta, tau, interp)
     info = ctx.treecode_info()
     tree = tc.TileTree(xs)
-    lists = tree.lists(theta, tau)
-    near, far = tc.list_sizes(lists)
-    assert (info["near_steps"], info["far_steps"]) == (near, far), (info, near, far)
+    lists = tree.lists(theta, tau, bool(interp))
+    sizes = tc.list_sizes(lists)
+    near, far = sizes[0], sizes[1]
+    fint = sizes[2] if interp else 0
+    assert (info["near_steps"], info["far_steps"], info["interp_steps"]) == (near, far, fint), (info, sizes)
     assert info["clusters"] == len(tree.clusters) and info["target_tiles"] == tree.n_t
-    assert far > 0
+    assert far + fint > 0 and (fint > 0 or not interp)
     P = ibim.Phys(2.0, 80.0, 0.1257, tau, 0)
     Po = oracle.Phys(2.0, 80.0, 0.1257, tau)
     p = inputs.random_vector(2 * N, seed=6)
@@ -54,8 +56,8 @@ def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per):
     worst = np.max(np.abs(y - yo)) / np.max(np.abs(yo))
     ye = oracle.matvec(xs, nr, w, Po, p)
     approx = _rel(yo, ye, N)
-    print("theta %.1f N %d steps near %d far %d: GPU vs oracle treecode %.2e %.2e (worst %.2e); "
-          "oracle treecode vs direct %.2e %.2e" % (theta, N, near, far, *r, worst, *approx))
+    print("theta %.1f interp %d N %d steps near %d far %d interp %d: GPU vs oracle treecode %.2e %.2e (worst %.2e); "
+          "oracle treecode vs direct %.2e %.2e" % (theta, interp, N, near, far, fint, *r, worst, *approx))
     assert max(r) < 1e-6 and worst < 1e-5
     ctx.close()
 
@@ -78,24 +80,25 @@ def test_treecode_without_far_clusters_is_the_fp32_operator():
     ctx.close()
 
 
-def test_treecode_on_built_sphere_operator_and_solve():
+@pytest.mark.parametrize("interp", [0, 1])
+def test_treecode_on_built_sphere_operator_and_solve(interp):
     R, h = 20.0, 0.5
     ctx = ibim.Context.sphere(R, h=h, band_eps=2 * h)
     N = ctx.N
     z, q = inputs.kirkwood_charges(50, 16.0)
     ctx.set_charges(z, q)
     P = ibim.Phys(2.0, 80.0, 0.1257, h, 0)
-    ctx.treecode_setup(0.7, h)
+    ctx.treecode_setup(0.7, h, interp)
     info = ctx.treecode_info()
-    assert info["far_steps"] > 0
+    assert info["far_steps"] + info["interp_steps"] > 0 and (info["interp_steps"] > 0 or not interp)
     d_in = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
     yt, y64 = torch.empty_like(d_in), torch.empty_like(d_in)
     ctx.matvec(P, d_in, yt, precision=ibim.IBIM_F32T)
     ctx.matvec(P, d_in, y64, precision=ibim.IBIM_F64)
     r = _rel(yt.cpu().numpy(), y64.cpu().numpy(), N)
     direct_steps = info["target_tiles"] * (-(-N // 256))
-    print("Kirkwood sphere N %d: steps near %d + far %d of %d direct; treecode vs FP64 %.2e %.2e"
-          % (N, info["near_steps"], info["far_steps"], direct_steps, *r))
+    print("Kirkwood sphere N %d interp %d: steps near %d + far %d + interp %d of %d direct; treecode vs FP64 %.2e %.2e"
+          % (N, interp, info["near_steps"], info["far_steps"], info["interp_steps"], direct_steps, *r))
     assert max(r) < 1e-6
     d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
     opts = dict(tol=1e-7, restart=64, maxit=400)
@@ -114,9 +117,9 @@ def test_treecode_misuse_is_reported():
     with pytest.raises(ibim.IbimError) as e:
         ctx.matvec(ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0), d_in, y, precision=ibim.IBIM_F32T)
     assert e.value.status == 7  # IBIM_ERR_STATE: no setup
-    for theta, tau_max in ((0.0, 0.3), (1.0, 0.3), (0.5, 0.0), (0.5, float("inf"))):
+    for theta, tau_max, ti in ((0.0, 0.3, 0), (1.0, 0.3, 0), (0.5, 0.0, 0), (0.5, float("inf"), 0), (0.5, 0.3, 2)):
         with pytest.raises(ibim.IbimError) as e:
-            ctx.treecode_setup(theta, tau_max)
+            ctx.treecode_setup(theta, tau_max, ti)
         assert e.value.status == 1  # IBIM_ERR_ARG
     ctx.treecode_setup(0.5, 0.3)
     for P in (ibim.Phys(2.0, 80.0, 0.1257, 0.4, 0), ibim.Phys(2.0, 80.0, 0.1257, 0.3, 1)):
