@@ -62,6 +62,10 @@ struct TcCube {  // proxy cube of a cluster: centre and half side
     double x, y, z, w;
 };
 
+struct TcItem {  // m2l work item: entries [e0, e1) of target tile t's interpolated list
+    int64_t t, e0, e1;
+};
+
 struct TcClusters {  // device arrays, one entry per cluster
     const int64_t* j0;
     const int64_t* j1;
@@ -91,11 +95,11 @@ struct TreeCode {
     unsigned long long* d_ctr = nullptr;  // [0] list-kernel segments, [1] m2l tiles (reset by the leaf upward launch)
     // target-side interpolation
     int interp = 0;
-    int64_t interp_steps = 0, n_mtiles = 0;
+    int64_t interp_steps = 0, n_items = 0;
     int m2l_grid = 0;
     int64_t* d_irow = nullptr;     // n_t + 1: interpolated far clusters of tile t = isrc[irow[t] .. irow[t + 1])
     int32_t* d_isrc = nullptr;     // their proxy tiles
-    int32_t* d_mtiles = nullptr;   // target tiles with at least one such cluster
+    TcItem* d_items = nullptr;     // m2l work items
     TcCube* d_tcube = nullptr;     // target proxy cube of each tile
     double* d_fields = nullptr;    // n_t x 216 x (y1, Vx, Vy, Vz) at the target proxies
 };
@@ -116,7 +120,7 @@ void tc_destroy(TreeCode* t)
     cudaFree(t->d_ctr);
     cudaFree(t->d_irow);
     cudaFree(t->d_isrc);
-    cudaFree(t->d_mtiles);
+    cudaFree(t->d_items);
     cudaFree(t->d_tcube);
     cudaFree(t->d_fields);
     delete t;
@@ -489,19 +493,21 @@ __device__ __forceinline__ void pair_field2(float2 Xx, float2 Xy, float2 Xz, con
 }
 
 struct TcM2l {
-    const int64_t* irow;     // n_t + 1
-    const int32_t* isrc;     // proxy tile of each entry
-    const int32_t* mtiles;   // target tiles with entries
-    const TcCube* tcube;     // target proxy cube per tile
-    int64_t n_mtiles;
+    const int64_t* irow;      // n_t + 1
+    const int32_t* isrc;      // proxy tile of each entry
+    const TcItem* items;      // work items
+    const TcCube* tcube;      // target proxy cube per tile
+    int64_t n_items;
 };
 
 constexpr int kM2lThreads = kF32STile;  // one thread per target proxy (216 of 256 active)
 
-// Fields at the target proxies of each listed target tile from the proxy
-// tiles of its interpolated far clusters.  CTA b takes tile mtiles[b] and then
-// tiles from the counter; the source proxy tiles stream through the stage
-// ring as in the list kernel (ring position continued across tiles).
+// Fields at the target proxies of each target tile from the proxy tiles of
+// its interpolated far clusters.  Work items are runs of at least 8 entries of
+// one tile's list: CTA b takes item b and then items from the counter; the
+// source proxy tiles stream through the stage ring as in the list kernel
+// (ring position continued across items), and each item adds its fields to
+// the tile's (zeroed before the launch) with FP64 atomics.
 __global__ void __launch_bounds__(kM2lThreads)
     tc_m2l_kernel(const float4* __restrict__ src, const float4* __restrict__ frames, TcM2l m, F32Consts k,
                   double* __restrict__ fields, unsigned long long* __restrict__ ctr, unsigned* __restrict__ err,
@@ -539,10 +545,11 @@ __global__ void __launch_bounds__(kM2lThreads)
 
     int64_t q = blockIdx.x;
     int sp = 0;
-    while (q < m.n_mtiles) {
-        const int64_t t = m.mtiles[q];
-        const int64_t e0 = m.irow[t];
-        e1 = m.irow[t + 1];
+    while (q < m.n_items) {
+        const TcItem item = m.items[q];
+        const int64_t t = item.t;
+        const int64_t e0 = item.e0;
+        e1 = item.e1;
         off = done - e0;
         if (tid == 0) {
             ptx::fence_proxy_async_smem();
@@ -605,10 +612,10 @@ __global__ void __launch_bounds__(kM2lThreads)
         }
         if (active && !bad) {
             double* f = fields + (t * kProxies + tid) * 4;
-            f[0] = F1;
-            f[1] = FX;
-            f[2] = FY;
-            f[3] = FZ;
+            atomicAdd(f, F1);
+            atomicAdd(f + 1, FX);
+            atomicAdd(f + 2, FY);
+            atomicAdd(f + 3, FZ);
         }
         if (warp == 0) {  // every step of this tile released before the stages are reused
             bool ok = !bad;
@@ -622,7 +629,7 @@ __global__ void __launch_bounds__(kM2lThreads)
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok && !bad) give_up();
-            if (lane == 0) tile_next[sp] = ok ? (int64_t)gridDim.x + (int64_t)atomicAdd(ctr, 1ull) : m.n_mtiles;
+            if (lane == 0) tile_next[sp] = ok ? (int64_t)gridDim.x + (int64_t)atomicAdd(ctr, 1ull) : m.n_items;
         }
         done += e1 - e0;
         __syncthreads();
@@ -804,7 +811,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     const int64_t n_real = padded_nodes(N) / kF32STile;
     const double fd = std::max(2.0 * tau_max, 1.5) * 1.001 + 1e-3;
     std::vector<int64_t> row_ptr(n_t + 1, 0), irow(n_t + 1, 0);
-    std::vector<int32_t> steps, isrc, mtiles;
+    std::vector<int32_t> steps, isrc;
     int64_t near_steps = 0, far_steps = 0;
     std::vector<int> stack;
     for (int64_t t = 0; t < n_t; ++t) {
@@ -835,7 +842,6 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
         }
         row_ptr[t + 1] = (int64_t)steps.size();
         irow[t + 1] = (int64_t)isrc.size();
-        if (irow[t + 1] > irow[t]) mtiles.push_back((int32_t)t);
     }
     if (n_real + nc > INT32_MAX) return tc_fail(IBIM_ERR_ARG, "treecode: too many tiles");
 
@@ -886,7 +892,6 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     T->level_off = level_off;
     T->interp = interp ? 1 : 0;
     T->interp_steps = (int64_t)isrc.size();
-    T->n_mtiles = (int64_t)mtiles.size();
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, 1, kTcThreads>, kTcThreads, 0);
     const int64_t cap = (int64_t)std::max(1, occ) * c->num_sms;
@@ -896,9 +901,18 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     T->Ls = std::max<int64_t>(1, (rest + 16 * g - 1) / (16 * g));
     T->nseg = g + (rest + T->Ls - 1) / T->Ls;
     T->grid = (int)g;
+    // m2l work items: runs of at least 8 entries of one tile's list, about
+    // four per resident CTA
     int occm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, tc_m2l_kernel, kM2lThreads, 0);
-    T->m2l_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, occm) * c->num_sms, T->n_mtiles));
+    const int64_t slots = (int64_t)std::max(1, occm) * c->num_sms;
+    const int64_t run = std::max<int64_t>(8, (T->interp_steps + 4 * slots - 1) / (4 * slots));
+    std::vector<TcItem> items;
+    for (int64_t t = 0; t < n_t; ++t)
+        for (int64_t e = irow[t]; e < irow[t + 1]; e += run)
+            items.push_back(TcItem{t, e, std::min(e + run, irow[t + 1])});
+    T->n_items = (int64_t)items.size();
+    T->m2l_grid = (int)std::max<int64_t>(1, std::min<int64_t>(slots, T->n_items));
 
     ibim_status st = IBIM_OK;
     auto chk = [&](ibim_status s) {
@@ -914,7 +928,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     if (T->interp) {
         chk(upload(&T->d_irow, irow));
         chk(upload(&T->d_isrc, isrc));
-        chk(upload(&T->d_mtiles, mtiles));
+        chk(upload(&T->d_items, items));
         chk(upload(&T->d_tcube, tcube));
     }
     const size_t frm_real = (size_t)n_real * 2 * kChunksPerTile;
@@ -972,8 +986,9 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     IBIM_TRY(timing_end(c, (T->near_steps + T->far_steps) * (int64_t)kTcTTile * kF32STile));
-    const TcM2l m{T->d_irow, T->d_isrc, T->d_mtiles, T->d_tcube, T->n_mtiles};
-    if (T->interp && T->n_mtiles > 0) {
+    const TcM2l m{T->d_irow, T->d_isrc, T->d_items, T->d_tcube, T->n_items};
+    if (T->interp && T->n_items > 0) {
+        IBIM_CUDA(cudaMemsetAsync(T->d_fields, 0, sizeof(double) * (size_t)T->n_t * kProxies * 4, c->stream));
         tc_m2l_kernel<<<T->m2l_grid, kM2lThreads, 0, c->stream>>>(T->d_src, T->d_frm, m, f32_consts(k), T->d_fields,
                                                                   T->d_ctr + 1, c->d_err, d_skip);
         count_launch(c);
