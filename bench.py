@@ -159,6 +159,11 @@ def _kirkwood_inputs():
     return z, q
 
 
+def inputs_random(n, seed=3):
+    from paper_1709_08070_gb300 import inputs
+    return inputs.random_vector(n, seed=seed)
+
+
 def _series_kcal(W):
     """Kirkwood series G_pol (kcal/mol) of a sphere workload, as stored in
     tests/golden/kirkwood_series.json by tests/golden/make_kirkwood_series.py."""
@@ -292,6 +297,31 @@ def run_ours(args):
                     props.multi_processor_count, FP32_LANES_PER_SM, sm_max)}
     if ck.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved_ops / (peak_ops * ck["sm_mhz"] / sm_max)
+    # the other kernel family on the same workload (one-directional when the
+    # autotuner chose the symmetric kernel, and vice versa), three timed
+    # operator applications, for comparison of the two fractions
+    variants = ibim.ibim_f32_variants()
+    alt = [v for v, info in enumerate(variants) if info[:3] == (2, 1, 512) and info[3] != sym]
+    if alt:
+        ctx.set_f32_variant(alt[0], 1)
+        xa = torch.from_numpy(inputs_random(2 * N)).cuda()
+        ya = torch.empty_like(xa)
+        ctx.matvec(P, xa, ya)
+        ctx.timing_enable(True)
+        ctx.timing_reset()
+        for _ in range(3):
+            ctx.matvec(P, xa, ya)
+        torch.cuda.synchronize()
+        ta = ctx.timing()
+        ctx.timing_enable(False)
+        ctx.set_f32_variant(variant, bps)
+        a_ms = ta["pair_ms"] / max(1, ta["pair_launches"])
+        a_ops = F32_OPS_PER_INTERACTION_SYM if variants[alt[0]][3] else F32_OPS_PER_INTERACTION
+        a_ach = a_ops * N * N / (a_ms * 1e-3)
+        roofline["other_kernel"] = {"kernel": "pair_sym_kernel" if variants[alt[0]][3] else "pair_f32_kernel",
+                                    "variant": alt[0], "ops_per_interaction": a_ops, "avg_launch_ms": a_ms,
+                                    "achieved": a_ach / 1e12, "frac": a_ach / peak_ops,
+                                    "interactions_per_s": N * N / (a_ms * 1e-3)}
 
     extra = {}
     if rank == 0:
