@@ -285,8 +285,8 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
  * accelerator is a black-box FMM built on Chebyshev interpolation, Sec. 4).
  * Every kernel of the discrete system (Sec. 2.2) is linear in the source's
  * densities d_j = a_j m_j and b_j (a_j = w_j psi_j, b_j = w_j psin_j), so a
- * cluster of sources far from a target tile is replaced by the 216 proxies
- * (6 Chebyshev points of the second kind per axis) of its bounding cube,
+ * cluster of sources far from a target tile is replaced by the order^3 proxies
+ * (Chebyshev points of the second kind, `order` per axis) of its bounding cube,
  * carrying D_k = sum_j L_k(y_j) d_j and beta_k = sum_j L_k(y_j) b_j (L_k the
  * tensor-product Lagrange basis).  Near sources are summed as in IBIM_F32C,
  * tube rule included.
@@ -304,25 +304,27 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
  *     regularisation tube (Sec. 2.2.1) of any target.
  * theta in (0, 1) (smaller: more accurate and slower; 0.5-0.8 give relative
  * operator errors of about 1e-9 to 1e-7); tau_max > 0 is the largest tau the
- * operator will be applied with.  target_interp (0 or 1): with 1, a far
+ * operator will be applied with.  order: Chebyshev points per axis, 4, 5 or 6
+ * (64, 125 or 216 proxies per cluster; at the same theta 4 is less accurate
+ * and makes far steps 3.5x cheaper than 6).  target_interp (0 or 1): with 1, a far
  * cluster that is also far from the target tile's own Chebyshev cube
  * (r_Tc + r_C <= theta D and D >= the same far distance + r_Tc + r_C + 0.25,
- * r_Tc the cube's half-diagonal) is evaluated at the tile's 216 target proxies,
+ * r_Tc the cube's half-diagonal) is evaluated at the tile's order^3 target proxies,
  * and the fields y1 and V (y2 = n . V) are interpolated to the targets.  Allocates device memory on the context
  * (released by ibim_destroy or a new setup); synchronises the context stream.
  * Caller nodes should be ordered so that runs of consecutive indices are
  * compact (built geometries are).  Applying IBIM_F32T with tau > tau_max or
  * tube_rule 1 returns IBIM_ERR_ARG; before any setup, IBIM_ERR_STATE.
- * Errors: IBIM_ERR_ARG (NULL context, theta or tau_max out of range,
- * target_interp not 0 or 1),
+ * Errors: IBIM_ERR_ARG (NULL context, theta or tau_max out of range, order
+ * not 4, 5 or 6, target_interp not 0 or 1),
  * IBIM_ERR_STATE (no nodes), IBIM_ERR_CUDA.
  *
  * ibim_treecode_info: list sizes of the current setup (outputs may be NULL):
  * near source-tile steps, far cluster steps (each step is 1024 targets x 256
- * sources or proxies), interpolated far cluster steps (216 target proxies x 216
+ * sources or proxies), interpolated far cluster steps (order^3 target proxies x order^3
  * proxies each), clusters, target tiles.  IBIM_ERR_STATE before setup.
  */
-ibim_status ibim_treecode_setup(ibim_ctx* ctx, double theta, double tau_max, int target_interp);
+ibim_status ibim_treecode_setup(ibim_ctx* ctx, double theta, double tau_max, int order, int target_interp);
 ibim_status ibim_treecode_info(ibim_ctx* ctx, int64_t* near_steps, int64_t* far_steps, int64_t* interp_steps,
                                int64_t* clusters, int64_t* target_tiles);
 

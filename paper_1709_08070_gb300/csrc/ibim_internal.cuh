@@ -213,7 +213,7 @@ PairSchedule f32_schedule(ibim_ctx* c);
 ibim_status f32_chunk_frames(ibim_ctx* c);
 ibim_status f32_pack_to(ibim_ctx* c, VecRef in, float4* dst, const int* d_skip);
 // treecode form of the FP32 operator (treecode.cu)
-ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp);
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int interp);
 ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, const int* d_skip);
 void tc_destroy(TreeCode* t);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,

@@ -49,14 +49,20 @@
 
 namespace ibim {
 
-constexpr int kCheb = 6;
-constexpr int kProxies = kCheb * kCheb * kCheb;  // 216 of a 256-node tile
-constexpr int kProxyChunks = (kProxies + kChunk - 1) / kChunk;  // 7 chunks hold them (the 8th is padding)
+// Chebyshev order NC (points per axis, 4, 5 or 6): NC^3 proxies fill the
+// first kChunks chunks of a 256-node proxy tile (the rest is padding).
+template <int NC>
+struct Cheb {
+    static constexpr int kProxies = NC * NC * NC;
+    static constexpr int kChunks = (kProxies + kChunk - 1) / kChunk;
+    static constexpr int kM2lThreads = (kProxies + 31) / 32 * 32;  // one thread per target proxy
+};
+constexpr int kMaxProxies = Cheb<6>::kProxies;  // stride of the per-tile field buffer
 constexpr int kTcTpt = 2, kTcThreads = 512;
 constexpr int kTcTTile = kTcTpt * kTcThreads;  // 1024 targets
 constexpr double kTcMinHalf = 1e-3;            // smallest proxy-cube half side (A)
 constexpr double kTcFarMargin = 0.25;          // extra gap of a far cluster (A)
-static_assert(kProxies <= kF32STile, "proxies of a cluster fit one source tile");
+static_assert(kMaxProxies <= kF32STile, "proxies of a cluster fit one source tile");
 
 struct TcCube {  // proxy cube of a cluster: centre and half side
     double x, y, z, w;
@@ -75,6 +81,7 @@ struct TcClusters {  // device arrays, one entry per cluster
 
 struct TreeCode {
     double theta = 0.0, tau_max = 0.0;
+    int order = 6;             // Chebyshev points per axis (4, 5 or 6)
     int64_t n_real_tiles = 0;  // padded N / 256
     int n_clusters = 0;
     int64_t n_t = 0;           // target tiles
@@ -128,35 +135,46 @@ void tc_destroy(TreeCode* t)
 
 // ------------------------------------------------------------------ device
 
-// The 6 Chebyshev points of the second kind cos(k pi / 5) on [-1, 1].
+// The NC Chebyshev points of the second kind cos(k pi / (NC - 1)) on [-1, 1].
+template <int NC>
 __device__ __forceinline__ double cheb_point(int k)
 {
-    const double c1 = 0.8090169943749475, c2 = 0.30901699437494745;  // cos(pi/5), cos(2 pi/5)
-    return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? c2 : k == 3 ? -c2 : k == 4 ? -c1 : -1.0;
+    static_assert(NC >= 4 && NC <= 6, "Chebyshev order 4, 5 or 6");
+    if (NC == 6) {
+        const double c1 = 0.8090169943749475, c2 = 0.30901699437494745;  // cos(pi/5), cos(2 pi/5)
+        return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? c2 : k == 3 ? -c2 : k == 4 ? -c1 : -1.0;
+    }
+    if (NC == 5) {
+        const double c1 = 0.7071067811865476;  // cos(pi/4)
+        return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? 0.0 : k == 3 ? -c1 : -1.0;
+    }
+    return k == 0 ? 1.0 : k == 1 ? 0.5 : k == 2 ? -0.5 : -1.0;  // cos(k pi / 3)
 }
 
 // Lagrange basis of those points at u in FP32 (barycentric form, weights
 // (-1)^k halved at the ends; u on a point gives the unit vector).
-__device__ __forceinline__ void cheb_basis(float u, float (&l)[kCheb])
+template <int NC>
+__device__ __forceinline__ void cheb_basis(float u, float (&l)[NC])
 {
-    float q[kCheb], s = 0.0f;
+    float q[NC], s = 0.0f;
     int hit = -1;
 #pragma unroll
-    for (int k = 0; k < kCheb; ++k) {
-        const float wk = ((k & 1) ? -1.0f : 1.0f) * ((k == 0 || k == kCheb - 1) ? 0.5f : 1.0f);
-        const float d = u - (float)cheb_point(k);
+    for (int k = 0; k < NC; ++k) {
+        const float wk = ((k & 1) ? -1.0f : 1.0f) * ((k == 0 || k == NC - 1) ? 0.5f : 1.0f);
+        const float d = u - (float)cheb_point<NC>(k);
         if (d == 0.0f) hit = k;
         q[k] = wk / d;
         s += q[k];
     }
     const float rs = 1.0f / s;
 #pragma unroll
-    for (int k = 0; k < kCheb; ++k) l[k] = (hit >= 0) ? (k == hit ? 1.0f : 0.0f) : q[k] * rs;
+    for (int k = 0; k < NC; ++k) l[k] = (hit >= 0) ? (k == hit ? 1.0f : 0.0f) : q[k] * rs;
 }
 
 // Proxies of the clusters ids[0 .. gridDim.x) (one CTA of kF32STile threads
 // each): from the cluster's nodes for a leaf, from its children's proxies
 // otherwise; written as the cluster's proxy tile in the source payload format.
+template <int NC>
 __global__ void __launch_bounds__(kF32STile)
     tc_upward_kernel(TcClusters cl, const int* __restrict__ ids, const double* __restrict__ geo, int64_t N,
                      int64_t n_real_tiles, float4* __restrict__ src, unsigned long long* __restrict__ ctr,
@@ -167,7 +185,7 @@ __global__ void __launch_bounds__(kF32STile)
         ctr[0] = 0ull;
         ctr[1] = 0ull;
     }
-    __shared__ float lw[kF32STile][3 * kCheb];
+    __shared__ float lw[kF32STile][3 * NC];
     __shared__ float4 dens[kF32STile];   // (d.x, d.y, d.z, b) of each source of the pass
     __shared__ float4 outp[kF32STile];   // (rel.x, rel.y, rel.z, b) of each proxy
     __shared__ float4 outd[kF32STile];   // (D.x, D.y, D.z, 0)
@@ -176,14 +194,14 @@ __global__ void __launch_bounds__(kF32STile)
     const TcCube cube = cl.cube[ci];
     const double inv = 1.0 / cube.w;
     const int2 ch = cl.child[ci];
-    const int kx = tid / (kCheb * kCheb), ky = (tid / kCheb) % kCheb, kz = tid % kCheb;
+    const int kx = tid / (NC * NC), ky = (tid / NC) % NC, kz = tid % NC;
     float ax = 0.0f, ay = 0.0f, az = 0.0f, ab = 0.0f;
 
     auto accumulate = [&](int count) {
         __syncthreads();
-        if (tid < kProxies)
+        if (tid < Cheb<NC>::kProxies)
             for (int s = 0; s < count; ++s) {
-                const float wgt = lw[s][kx] * lw[s][kCheb + ky] * lw[s][2 * kCheb + kz];
+                const float wgt = lw[s][kx] * lw[s][NC + ky] * lw[s][2 * NC + kz];
                 const float4 d = dens[s];
                 ax = fmaf(wgt, d.x, ax);
                 ay = fmaf(wgt, d.y, ay);
@@ -193,16 +211,16 @@ __global__ void __launch_bounds__(kF32STile)
         __syncthreads();
     };
     auto set_source = [&](double x, double y, double z, float4 d) {
-        float l[kCheb];
-        cheb_basis((float)((x - cube.x) * inv), l);
+        float l[NC];
+        cheb_basis<NC>((float)((x - cube.x) * inv), l);
 #pragma unroll
-        for (int k = 0; k < kCheb; ++k) lw[tid][k] = l[k];
-        cheb_basis((float)((y - cube.y) * inv), l);
+        for (int k = 0; k < NC; ++k) lw[tid][k] = l[k];
+        cheb_basis<NC>((float)((y - cube.y) * inv), l);
 #pragma unroll
-        for (int k = 0; k < kCheb; ++k) lw[tid][kCheb + k] = l[k];
-        cheb_basis((float)((z - cube.z) * inv), l);
+        for (int k = 0; k < NC; ++k) lw[tid][NC + k] = l[k];
+        cheb_basis<NC>((float)((z - cube.z) * inv), l);
 #pragma unroll
-        for (int k = 0; k < kCheb; ++k) lw[tid][2 * kCheb + k] = l[k];
+        for (int k = 0; k < NC; ++k) lw[tid][2 * NC + k] = l[k];
         dens[tid] = d;
     };
 
@@ -226,22 +244,22 @@ __global__ void __launch_bounds__(kF32STile)
         for (int side = 0; side < 2; ++side) {
             const int cc = side ? ch.y : ch.x;
             const TcCube cb = cl.cube[cc];
-            if (tid < kProxies) {
-                const int qx = tid / (kCheb * kCheb), qy = (tid / kCheb) % kCheb, qz = tid % kCheb;
+            if (tid < Cheb<NC>::kProxies) {
+                const int qx = tid / (NC * NC), qy = (tid / NC) % NC, qz = tid % NC;
                 const float4* pr = src + (n_real_tiles + cc) * (kF32STile / 2) * kPairF4 + kPairF4 * (tid >> 1);
                 const float4 B = pr[1], C = pr[2], D = pr[3];
                 const bool odd = tid & 1;
                 const float4 d = odd ? make_float4(C.y, C.w, D.y, B.w) : make_float4(C.x, C.z, D.x, B.z);
-                set_source(cb.x + cb.w * cheb_point(qx), cb.y + cb.w * cheb_point(qy), cb.z + cb.w * cheb_point(qz), d);
+                set_source(cb.x + cb.w * cheb_point<NC>(qx), cb.y + cb.w * cheb_point<NC>(qy), cb.z + cb.w * cheb_point<NC>(qz), d);
             }
-            accumulate(kProxies);
+            accumulate(Cheb<NC>::kProxies);
         }
     }
 
     // proxy tile: positions relative to the cube centre (the tile's chunk frame)
-    if (tid < kProxies) {
-        outp[tid] = make_float4((float)(cube.w * cheb_point(kx)), (float)(cube.w * cheb_point(ky)),
-                                (float)(cube.w * cheb_point(kz)), ab);
+    if (tid < Cheb<NC>::kProxies) {
+        outp[tid] = make_float4((float)(cube.w * cheb_point<NC>(kx)), (float)(cube.w * cheb_point<NC>(ky)),
+                                (float)(cube.w * cheb_point<NC>(kz)), ab);
         outd[tid] = make_float4(ax, ay, az, 0.0f);
     } else {
         outp[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -264,6 +282,7 @@ struct TcSchedule {
     const int32_t* step_src;  // source tile of each step (>= n_real_tiles: a proxy tile)
     int64_t n_t, total, n_real_tiles;
     int64_t Lb, nbig, Ls, nseg;  // segments: nbig of Lb steps, then small ones of Ls steps
+    int proxy_chunks;            // chunks of a proxy tile that hold proxies
 };
 
 // First step of segment q (total for q = nseg) and the segment of step u.
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             if (!idle)
                 tile_sums<TPT, true>(T, &tfrm[warp][0], true, stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2,
                                      g64, gi0, THREADS, st * kF32STile, N, st >= s.n_real_tiles,
-                                     st >= s.n_real_tiles ? kProxyChunks : kChunksPerTile);
+                                     st >= s.n_real_tiles ? s.proxy_chunks : kChunksPerTile);
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 D1[q] += (double)S1[q] - (double)C1[q];
@@ -500,20 +519,19 @@ struct TcM2l {
     int64_t n_items;
 };
 
-constexpr int kM2lThreads = kF32STile;  // one thread per target proxy (216 of 256 active)
-
 // Fields at the target proxies of each target tile from the proxy tiles of
 // its interpolated far clusters.  Work items are runs of at least 8 entries of
 // one tile's list: CTA b takes item b and then items from the counter; the
 // source proxy tiles stream through the stage ring as in the list kernel
 // (ring position continued across items), and each item adds its fields to
 // the tile's (zeroed before the launch) with FP64 atomics.
-__global__ void __launch_bounds__(kM2lThreads)
+template <int NC>
+__global__ void __launch_bounds__(Cheb<NC>::kM2lThreads)
     tc_m2l_kernel(const float4* __restrict__ src, const float4* __restrict__ frames, TcM2l m, F32Consts k,
                   double* __restrict__ fields, unsigned long long* __restrict__ ctr, unsigned* __restrict__ err,
                   const int* __restrict__ skip)
 {
-    constexpr int NW = kM2lThreads / 32;
+    constexpr int NW = Cheb<NC>::kM2lThreads / 32;
     if (skip != nullptr && *skip) return;
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(8) StagePipe pipe;
@@ -522,8 +540,8 @@ __global__ void __launch_bounds__(kM2lThreads)
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const bool active = tid < kProxies;
-    const int lx = tid / (kCheb * kCheb), ly = (tid / kCheb) % kCheb, lz = tid % kCheb;
+    const bool active = tid < Cheb<NC>::kProxies;
+    const int lx = tid / (NC * NC), ly = (tid / NC) % NC, lz = tid % NC;
     if (tid == 0) {
         pipe_init(pipe, NW);
         abort_sh = 0;
@@ -557,8 +575,8 @@ __global__ void __launch_bounds__(kM2lThreads)
         }
         const TcCube cube = m.tcube[t];
         // target proxy relative to the cube centre; the centre as hi + lo floats
-        const float3 X0 = make_float3((float)(cube.w * cheb_point(lx)), (float)(cube.w * cheb_point(ly)),
-                                      (float)(cube.w * cheb_point(lz)));
+        const float3 X0 = make_float3((float)(cube.w * cheb_point<NC>(lx)), (float)(cube.w * cheb_point<NC>(ly)),
+                                      (float)(cube.w * cheb_point<NC>(lz)));
         const float hx = (float)cube.x, hy = (float)cube.y, hz = (float)cube.z;
         const float3 lo = make_float3((float)(cube.x - (double)hx), (float)(cube.y - (double)hy),
                                       (float)(cube.z - (double)hz));
@@ -580,7 +598,7 @@ __global__ void __launch_bounds__(kM2lThreads)
                 float2 f1 = make_float2(0.0f, 0.0f), vx = f1, vy = f1, vz = f1;
                 const float4* cb = stg[stage].buf;
 #pragma unroll 4
-                for (int pr = 0; pr < kProxyChunks * kPairsPerChunk; ++pr) {
+                for (int pr = 0; pr < Cheb<NC>::kChunks * kPairsPerChunk; ++pr) {
                     const float4 A = cb[kPairF4 * pr], B = cb[kPairF4 * pr + 1];
                     const float4 C = cb[kPairF4 * pr + 2], D = cb[kPairF4 * pr + 3];
                     pair_field2(Xx, Xy, Xz, A, B, C, D, fc, f1, vx, vy, vz);
@@ -611,7 +629,7 @@ __global__ void __launch_bounds__(kM2lThreads)
             }
         }
         if (active && !bad) {
-            double* f = fields + (t * kProxies + tid) * 4;
+            double* f = fields + (t * kMaxProxies + tid) * 4;
             atomicAdd(f, F1);
             atomicAdd(f + 1, FX);
             atomicAdd(f + 2, FY);
@@ -642,6 +660,7 @@ __global__ void __launch_bounds__(kM2lThreads)
 // y = Lambda p + (1/(4 pi)) (partials of the segments that covered the row
 // + the interpolated far fields of the row's target proxies, when it has any).
 // One 256-thread block lies inside one 1024-node target tile.
+template <int NC>
 __global__ void __launch_bounds__(256)
     tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, int64_t N, double lambda1, double lambda2,
                     VecRef in, OutRef out, TcM2l m, const double* __restrict__ fields,
@@ -649,12 +668,13 @@ __global__ void __launch_bounds__(256)
 {
     static_assert(kTcTTile % 256 == 0, "a fixup block lies in one target tile");
     if (skip != nullptr && *skip) return;
-    __shared__ float fl[kProxies][4];
+    constexpr int NP = Cheb<NC>::kProxies;
+    __shared__ float fl[NP][4];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x) / kTcTTile;
     const bool has = interp && m.irow[t + 1] > m.irow[t];
     if (has)
-        for (int q = threadIdx.x; q < kProxies * 4; q += blockDim.x) (&fl[0][0])[q] = (float)fields[t * kProxies * 4 + q];
+        for (int q = threadIdx.x; q < NP * 4; q += blockDim.x) (&fl[0][0])[q] = (float)fields[t * kMaxProxies * 4 + q];
     __syncthreads();
     if (i >= N) return;
     const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
@@ -671,18 +691,18 @@ __global__ void __launch_bounds__(256)
     if (has) {  // L2P: the tile's fields at this target
         const TcCube cube = m.tcube[t];
         const double inv = 1.0 / cube.w;
-        float wx[kCheb], wy[kCheb], wz[kCheb];
-        cheb_basis((float)((geo[i] - cube.x) * inv), wx);
-        cheb_basis((float)((geo[N + i] - cube.y) * inv), wy);
-        cheb_basis((float)((geo[2 * N + i] - cube.z) * inv), wz);
+        float wx[NC], wy[NC], wz[NC];
+        cheb_basis<NC>((float)((geo[i] - cube.x) * inv), wx);
+        cheb_basis<NC>((float)((geo[N + i] - cube.y) * inv), wy);
+        cheb_basis<NC>((float)((geo[2 * N + i] - cube.z) * inv), wz);
         float F1 = 0.0f, FX = 0.0f, FY = 0.0f, FZ = 0.0f;
-        for (int ax = 0; ax < kCheb; ++ax)
-            for (int ay = 0; ay < kCheb; ++ay) {
+        for (int ax = 0; ax < NC; ++ax)
+            for (int ay = 0; ay < NC; ++ay) {
                 const float wxy = wx[ax] * wy[ay];
 #pragma unroll
-                for (int az = 0; az < kCheb; ++az) {
+                for (int az = 0; az < NC; ++az) {
                     const float wgt = wxy * wz[az];
-                    const float* f = fl[(ax * kCheb + ay) * kCheb + az];
+                    const float* f = fl[(ax * NC + ay) * NC + az];
                     F1 = fmaf(wgt, f[0], F1);
                     FX = fmaf(wgt, f[1], FX);
                     FY = fmaf(wgt, f[2], FY);
@@ -780,7 +800,15 @@ ibim_status upload(T** dst, const std::vector<T>& v)
 
 }  // namespace
 
-ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
+template <int NC>
+static int m2l_occupancy()
+{
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_m2l_kernel<NC>, Cheb<NC>::kM2lThreads, 0);
+    return occ < 1 ? 1 : occ;
+}
+
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int interp)
 {
     const int64_t N = c->N;
     std::vector<double> xs(3 * (size_t)N);
@@ -883,6 +911,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     TreeCode* T = new TreeCode();
     T->theta = theta;
     T->tau_max = tau_max;
+    T->order = order;
     T->n_real_tiles = n_real;
     T->n_clusters = nc;
     T->n_t = n_t;
@@ -903,9 +932,8 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     T->grid = (int)g;
     // m2l work items: runs of at least 8 entries of one tile's list, about
     // four per resident CTA
-    int occm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, tc_m2l_kernel, kM2lThreads, 0);
-    const int64_t slots = (int64_t)std::max(1, occm) * c->num_sms;
+    const int occm = order == 4 ? m2l_occupancy<4>() : order == 5 ? m2l_occupancy<5>() : m2l_occupancy<6>();
+    const int64_t slots = (int64_t)occm * c->num_sms;
     const int64_t run = std::max<int64_t>(8, (T->interp_steps + 4 * slots - 1) / (4 * slots));
     std::vector<TcItem> items;
     for (int64_t t = 0; t < n_t; ++t)
@@ -939,7 +967,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
             e = cudaMalloc((void**)&T->d_part, sizeof(double) * (size_t)(T->nseg + n_t) * 2 * kTcTTile);
         if (e == cudaSuccess) e = cudaMalloc((void**)&T->d_ctr, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess && T->interp)
-            e = cudaMalloc((void**)&T->d_fields, sizeof(double) * (size_t)n_t * kProxies * 4);
+            e = cudaMalloc((void**)&T->d_fields, sizeof(double) * (size_t)n_t * kMaxProxies * 4);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(T->d_frm, c->d_frames, sizeof(float4) * frm_real, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess)
@@ -958,6 +986,47 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int interp)
     return IBIM_OK;
 }
 
+template <int NC>
+static ibim_status tc_apply_order(ibim_ctx* c, TreeCode* T, const PairConsts& k, VecRef in, OutRef out,
+                                  const int* d_skip)
+{
+    const int64_t N = c->N;
+    IBIM_TRY(f32_pack_to(c, in, T->d_src, d_skip));
+    const TcClusters cl{T->d_j0, T->d_j1, T->d_child, T->d_cube};
+    for (size_t h = 0; h + 1 < T->level_off.size(); ++h) {
+        const int n = T->level_off[h + 1] - T->level_off[h];
+        if (n == 0) continue;
+        tc_upward_kernel<NC><<<n, kF32STile, 0, c->stream>>>(cl, T->d_ids + T->level_off[h], c->d_geo64, N,
+                                                             T->n_real_tiles, T->d_src, h == 0 ? T->d_ctr : nullptr,
+                                                             d_skip);
+        count_launch(c);
+        IBIM_CUDA(cudaGetLastError());
+    }
+    const TcSchedule s{T->d_row_ptr, T->d_step_src, T->n_t, T->total, T->n_real_tiles,
+                       T->Lb, (int64_t)T->grid, T->Ls, T->nseg, Cheb<NC>::kChunks};
+    const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * N, 1, N};
+    IBIM_TRY(timing_begin(c));
+    tc_pair_kernel<kTcTpt, 1, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
+        c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, T->d_ctr, c->d_err, d_skip, g64);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    IBIM_TRY(timing_end(c, (T->near_steps * kF32STile + T->far_steps * Cheb<NC>::kChunks * kChunk) * (int64_t)kTcTTile));
+    const TcM2l m{T->d_irow, T->d_isrc, T->d_items, T->d_tcube, T->n_items};
+    if (T->interp && T->n_items > 0) {
+        IBIM_CUDA(cudaMemsetAsync(T->d_fields, 0, sizeof(double) * (size_t)T->n_t * kMaxProxies * 4, c->stream));
+        tc_m2l_kernel<NC><<<T->m2l_grid, Cheb<NC>::kM2lThreads, 0, c->stream>>>(
+            T->d_src, T->d_frm, m, f32_consts(k), T->d_fields, T->d_ctr + 1, c->d_err, d_skip);
+        count_launch(c);
+        IBIM_CUDA(cudaGetLastError());
+    }
+    const int bs = 256;
+    tc_fixup_kernel<NC><<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
+        T->d_part, s, N, k.lambda1, k.lambda2, in, out, m, T->d_fields, c->d_geo64, T->interp, d_skip);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
 ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, const int* d_skip)
 {
     TreeCode* T = c->tc;
@@ -965,53 +1034,22 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
     if (!(k.four_tau2 < 3.0e38)) return tc_fail(IBIM_ERR_ARG, "the treecode operator needs tube rule 0");
     if (std::sqrt(k.tau2) > T->tau_max * (1.0 + 1e-12))
         return tc_fail(IBIM_ERR_ARG, "tau exceeds the tau_max the treecode lists were built for");
-    const int64_t N = c->N;
-    IBIM_TRY(f32_pack_to(c, in, T->d_src, d_skip));
-    const TcClusters cl{T->d_j0, T->d_j1, T->d_child, T->d_cube};
-    for (size_t h = 0; h + 1 < T->level_off.size(); ++h) {
-        const int n = T->level_off[h + 1] - T->level_off[h];
-        if (n == 0) continue;
-        tc_upward_kernel<<<n, kF32STile, 0, c->stream>>>(cl, T->d_ids + T->level_off[h], c->d_geo64, N,
-                                                         T->n_real_tiles, T->d_src, h == 0 ? T->d_ctr : nullptr,
-                                                         d_skip);
-        count_launch(c);
-        IBIM_CUDA(cudaGetLastError());
-    }
-    const TcSchedule s{T->d_row_ptr, T->d_step_src, T->n_t, T->total, T->n_real_tiles,
-                       T->Lb, (int64_t)T->grid, T->Ls, T->nseg};
-    const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * N, 1, N};
-    IBIM_TRY(timing_begin(c));
-    tc_pair_kernel<kTcTpt, 1, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
-        c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, T->d_ctr, c->d_err, d_skip, g64);
-    count_launch(c);
-    IBIM_CUDA(cudaGetLastError());
-    IBIM_TRY(timing_end(c, (T->near_steps + T->far_steps) * (int64_t)kTcTTile * kF32STile));
-    const TcM2l m{T->d_irow, T->d_isrc, T->d_items, T->d_tcube, T->n_items};
-    if (T->interp && T->n_items > 0) {
-        IBIM_CUDA(cudaMemsetAsync(T->d_fields, 0, sizeof(double) * (size_t)T->n_t * kProxies * 4, c->stream));
-        tc_m2l_kernel<<<T->m2l_grid, kM2lThreads, 0, c->stream>>>(T->d_src, T->d_frm, m, f32_consts(k), T->d_fields,
-                                                                  T->d_ctr + 1, c->d_err, d_skip);
-        count_launch(c);
-        IBIM_CUDA(cudaGetLastError());
-    }
-    const int bs = 256;
-    tc_fixup_kernel<<<(unsigned)((N + bs - 1) / bs), bs, 0, c->stream>>>(
-        T->d_part, s, N, k.lambda1, k.lambda2, in, out, m, T->d_fields, c->d_geo64, T->interp, d_skip);
-    count_launch(c);
-    IBIM_CUDA(cudaGetLastError());
-    return IBIM_OK;
+    if (T->order == 4) return tc_apply_order<4>(c, T, k, in, out, d_skip);
+    if (T->order == 5) return tc_apply_order<5>(c, T, k, in, out, d_skip);
+    return tc_apply_order<6>(c, T, k, in, out, d_skip);
 }
 
 }  // namespace ibim
 
-extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau_max, int target_interp)
+extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau_max, int order, int target_interp)
 {
     using namespace ibim;
     if (c == nullptr || !(theta > 0.0 && theta < 1.0) || !(tau_max > 0.0) || !std::isfinite(tau_max))
         return tc_fail(IBIM_ERR_ARG, "need a context, 0 < theta < 1 and a finite tau_max > 0");
     if (c->N <= 0 || c->d_frames == nullptr) return tc_fail(IBIM_ERR_STATE, "the context has no nodes");
     if (target_interp != 0 && target_interp != 1) return tc_fail(IBIM_ERR_ARG, "target_interp must be 0 or 1");
-    return tc_setup(c, theta, tau_max, target_interp);
+    if (order < 4 || order > 6) return tc_fail(IBIM_ERR_ARG, "the Chebyshev order must be 4, 5 or 6");
+    return tc_setup(c, theta, tau_max, order, target_interp);
 }
 
 extern "C" ibim_status ibim_treecode_info(ibim_ctx* c, int64_t* near_steps, int64_t* far_steps,

@@ -85,7 +85,7 @@ _SIGS = {
     "ibim_matvec_noalloc": [ctypes.c_int64, _V, _V, _V, ctypes.POINTER(Phys), _V, _V, _V],
     "ibim_autotune": [_V, ctypes.POINTER(Phys), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
-    "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+    "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int],
     "ibim_treecode_info": [_V, _I64P, _I64P, _I64P, _I64P, _I64P],
     "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -374,9 +374,9 @@ def ibim_autotune(ctx, phys):
     return t.value, b.value, ms.value
 
 
-def ibim_treecode_setup(ctx, theta, tau_max, target_interp=0):
+def ibim_treecode_setup(ctx, theta, tau_max, target_interp=0, order=6):
     """Build the treecode tree and interaction lists (IBIM_F32T operator)."""
-    _check(lib().ibim_treecode_setup(ctx, float(theta), float(tau_max), int(target_interp)))
+    _check(lib().ibim_treecode_setup(ctx, float(theta), float(tau_max), int(order), int(target_interp)))
 
 
 def ibim_treecode_info(ctx):
@@ -550,8 +550,8 @@ class Context:
     def set_f32_variant(self, variant, ctas_per_sm=0):
         ibim_set_f32_variant(self.handle, variant, ctas_per_sm)
 
-    def treecode_setup(self, theta, tau_max, target_interp=0):
-        ibim_treecode_setup(self.handle, theta, tau_max, target_interp)
+    def treecode_setup(self, theta, tau_max, target_interp=0, order=6):
+        ibim_treecode_setup(self.handle, theta, tau_max, target_interp, order)
 
     def treecode_info(self):
         return ibim_treecode_info(self.handle)

@@ -28,13 +28,14 @@ def _rel(a, b, N):
     return (np.linalg.norm(a[:N] - b[:N]) / np.linalg.norm(b[:N]), np.linalg.norm(a[N:] - b[N:]) / np.linalg.norm(b[N:]))
 
 
-@pytest.mark.parametrize("theta,n_per,interp", [(0.6, 1000, 0), (0.8, 1500, 0), (0.6, 1000, 1), (0.8, 1500, 1)])
-def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp):
+@pytest.mark.parametrize("theta,n_per,interp,order", [(0.6, 1000, 0, 6), (0.8, 1500, 0, 6), (0.6, 1000, 1, 6),
+                                                      (0.8, 1500, 1, 6), (0.8, 1500, 1, 4), (0.7, 1000, 0, 5)])
+def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp, order):
     xs, nr, w = inputs.sphere_cluster_cloud(n_per, CENTRES, radius=5.0, seed=4)
     N = xs.shape[0]
     tau = 0.3
     ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
-    ctx.treecode_setup(theta, tau, interp)
+    ctx.treecode_setup(theta, tau, interp, order)
     info = ctx.treecode_info()
     tree = tc.TileTree(xs)
     lists = tree.lists(theta, tau, bool(interp))
@@ -47,7 +48,7 @@ def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp):
     P = ibim.Phys(2.0, 80.0, 0.1257, tau, 0)
     Po = oracle.Phys(2.0, 80.0, 0.1257, tau)
     p = inputs.random_vector(2 * N, seed=6)
-    yo = tc.treecode_matvec(xs, nr, w, Po, p, tree=tree, lists=lists)
+    yo = tc.treecode_matvec(xs, nr, w, Po, p, n=order, tree=tree, lists=lists)
     d_in = torch.from_numpy(p).cuda()
     y = torch.empty_like(d_in)
     ctx.matvec(P, d_in, y, precision=ibim.IBIM_F32T)
@@ -56,8 +57,9 @@ def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp):
     worst = np.max(np.abs(y - yo)) / np.max(np.abs(yo))
     ye = oracle.matvec(xs, nr, w, Po, p)
     approx = _rel(yo, ye, N)
-    print("theta %.1f interp %d N %d steps near %d far %d interp %d: GPU vs oracle treecode %.2e %.2e (worst %.2e); "
-          "oracle treecode vs direct %.2e %.2e" % (theta, interp, N, near, far, fint, *r, worst, *approx))
+    print("theta %.1f interp %d order %d N %d steps near %d far %d interp %d: GPU vs oracle treecode %.2e %.2e "
+          "(worst %.2e); oracle treecode vs direct %.2e %.2e" % (theta, interp, order, N, near, far, fint, *r, worst,
+                                                                 *approx))
     assert max(r) < 1e-6 and worst < 1e-5
     ctx.close()
 
@@ -117,9 +119,10 @@ def test_treecode_misuse_is_reported():
     with pytest.raises(ibim.IbimError) as e:
         ctx.matvec(ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0), d_in, y, precision=ibim.IBIM_F32T)
     assert e.value.status == 7  # IBIM_ERR_STATE: no setup
-    for theta, tau_max, ti in ((0.0, 0.3, 0), (1.0, 0.3, 0), (0.5, 0.0, 0), (0.5, float("inf"), 0), (0.5, 0.3, 2)):
+    for theta, tau_max, ti, order in ((0.0, 0.3, 0, 6), (1.0, 0.3, 0, 6), (0.5, 0.0, 0, 6), (0.5, float("inf"), 0, 6),
+                                      (0.5, 0.3, 2, 6), (0.5, 0.3, 0, 3), (0.5, 0.3, 0, 7)):
         with pytest.raises(ibim.IbimError) as e:
-            ctx.treecode_setup(theta, tau_max, ti)
+            ctx.treecode_setup(theta, tau_max, ti, order)
         assert e.value.status == 1  # IBIM_ERR_ARG
     ctx.treecode_setup(0.5, 0.3)
     for P in (ibim.Phys(2.0, 80.0, 0.1257, 0.4, 0), ibim.Phys(2.0, 80.0, 0.1257, 0.3, 1)):
