@@ -329,6 +329,30 @@ ibim_status ibim_treecode_info(ibim_ctx* ctx, int64_t* near_steps, int64_t* far_
                                int64_t* clusters, int64_t* target_tiles);
 
 /*
+ * ibim_treecode_plan: the tree and interaction lists that ibim_treecode_setup
+ * builds, computed on the host only (no context, no device; for inspection
+ * and tests), for N nodes in the given order.
+ *   xyz        host, N x 3 doubles (row-major), the nodes' positions x*.
+ *   theta, tau_max, target_interp: as for ibim_treecode_setup.
+ *   sizes      host, 5 int64 (required): target tiles n_t, clusters,
+ *              list-kernel steps S, interpolated steps I, node tiles n_real.
+ *   row_ptr    host, n_t + 1 int64 or NULL: steps of target tile t are
+ *              steps[row_ptr[t] .. row_ptr[t + 1]).
+ *   steps      host, S int32 or NULL: a value v < n_real is the near source
+ *              tile v (nodes 256 v .. 256 v + 255); v >= n_real is far
+ *              cluster v - n_real (clusters numbered in pre-order from the
+ *              root, node range [0, N)).
+ *   irow, isrc host, n_t + 1 int64 and I int32 or NULL: the interpolated far
+ *              clusters of each tile, numbered as in steps.
+ * Lists are in depth-first order (left child first).  Call once with NULL
+ * arrays to read the sizes, then with arrays of those sizes.  Errors:
+ * IBIM_ERR_ARG (NULL xyz or sizes, N <= 0, parameters out of range),
+ * IBIM_ERR_NONFINITE.
+ */
+ibim_status ibim_treecode_plan(const double* xyz, int64_t N, double theta, double tau_max, int target_interp,
+                               int64_t* sizes, int64_t* row_ptr, int32_t* steps, int64_t* irow, int32_t* isrc);
+
+/*
  * FP32 pair-kernel variants (a GPU tuning device, not part of the paper's
  * method).  The library compiles a small table of variants, each with a fixed
  * number of targets per thread, a register budget (minimum CTAs per SM) and

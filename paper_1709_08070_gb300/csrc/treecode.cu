@@ -808,39 +808,50 @@ static int m2l_occupancy()
     return occ < 1 ? 1 : occ;
 }
 
-ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int interp)
-{
-    const int64_t N = c->N;
-    std::vector<double> xs(3 * (size_t)N);
-    IBIM_CUDA(cudaMemcpyAsync(xs.data(), c->d_geo64, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
-    IBIM_CUDA(cudaStreamSynchronize(c->stream));
-
+// Tree, target tiles and interaction lists of N nodes (coordinates SoA:
+// x[0..N), y[N..2N), z[2N..3N)); host only.
+struct TcPlan {
     std::vector<HostCluster> cl;
+    int64_t n_t = 0, n_real = 0;
+    std::vector<double> tcx, tcy, tcz, thalf;
+    std::vector<int64_t> row_ptr, irow;
+    std::vector<int32_t> steps, isrc;
+    int64_t near_steps = 0, far_steps = 0;
+};
+
+TcPlan tc_plan(const std::vector<double>& xs, int64_t N, double theta, double tau_max, int interp)
+{
+    TcPlan P;
+    std::vector<HostCluster>& cl = P.cl;
     cl.reserve((size_t)(2 * (N / kF32STile) + 4));
     make_cluster(cl, xs, N, 0, N);
-    const int nc = (int)cl.size();
 
     // target tiles
     const int64_t n_t = (N + kTcTTile - 1) / kTcTTile;
-    std::vector<double> tcx(n_t), tcy(n_t), tcz(n_t), trad(n_t), thalf(n_t), tcrad(n_t);
+    P.n_t = n_t;
+    P.tcx.resize(n_t);
+    P.tcy.resize(n_t);
+    P.tcz.resize(n_t);
+    P.thalf.resize(n_t);
+    std::vector<double> trad(n_t), tcrad(n_t);
     for (int64_t t = 0; t < n_t; ++t) {
         double mn[3], mx[3];
         box_of(xs, N, t * kTcTTile, std::min<int64_t>((t + 1) * kTcTTile, N), mn, mx);
-        tcx[t] = 0.5 * (mn[0] + mx[0]);
-        tcy[t] = 0.5 * (mn[1] + mx[1]);
-        tcz[t] = 0.5 * (mn[2] + mx[2]);
+        P.tcx[t] = 0.5 * (mn[0] + mx[0]);
+        P.tcy[t] = 0.5 * (mn[1] + mx[1]);
+        P.tcz[t] = 0.5 * (mn[2] + mx[2]);
         const double e0 = 0.5 * (mx[0] - mn[0]), e1 = 0.5 * (mx[1] - mn[1]), e2 = 0.5 * (mx[2] - mn[2]);
         trad[t] = std::sqrt((e0 * e0 + e1 * e1) + e2 * e2);
-        thalf[t] = std::max(std::max(std::max(e0, e1), e2), kTcMinHalf);  // target proxy cube
-        tcrad[t] = std::sqrt(3.0 * thalf[t] * thalf[t]);
+        P.thalf[t] = std::max(std::max(std::max(e0, e1), e2), kTcMinHalf);  // target proxy cube
+        tcrad[t] = std::sqrt(3.0 * P.thalf[t] * P.thalf[t]);
     }
 
     // lists, depth-first from the root
     const int64_t n_real = padded_nodes(N) / kF32STile;
+    P.n_real = n_real;
     const double fd = std::max(2.0 * tau_max, 1.5) * 1.001 + 1e-3;
-    std::vector<int64_t> row_ptr(n_t + 1, 0), irow(n_t + 1, 0);
-    std::vector<int32_t> steps, isrc;
-    int64_t near_steps = 0, far_steps = 0;
+    P.row_ptr.assign(n_t + 1, 0);
+    P.irow.assign(n_t + 1, 0);
     std::vector<int> stack;
     for (int64_t t = 0; t < n_t; ++t) {
         stack.assign(1, 0);
@@ -848,7 +859,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int i
             const int ci = stack.back();
             stack.pop_back();
             const HostCluster& q = cl[ci];
-            const double dx = tcx[t] - q.cx, dy = tcy[t] - q.cy, dz = tcz[t] - q.cz;
+            const double dx = P.tcx[t] - q.cx, dy = P.tcy[t] - q.cy, dz = P.tcz[t] - q.cz;
             const double D = std::sqrt((dx * dx + dy * dy) + dz * dz);
             const double rT = trad[t];
             const bool far = (rT + q.radius <= theta * D) && (D >= fd + rT + q.radius + kTcFarMargin);
@@ -856,21 +867,38 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int i
             const bool fint =
                 far && interp && (rTc + q.radius <= theta * D) && (D >= fd + rTc + q.radius + kTcFarMargin);
             if (fint) {
-                isrc.push_back((int32_t)(n_real + ci));
+                P.isrc.push_back((int32_t)(n_real + ci));
             } else if (far) {
-                steps.push_back((int32_t)(n_real + ci));
-                ++far_steps;
+                P.steps.push_back((int32_t)(n_real + ci));
+                ++P.far_steps;
             } else if (q.c0 < 0) {
-                steps.push_back((int32_t)(q.j0 / kF32STile));
-                ++near_steps;
+                P.steps.push_back((int32_t)(q.j0 / kF32STile));
+                ++P.near_steps;
             } else {
                 stack.push_back(q.c1);
                 stack.push_back(q.c0);
             }
         }
-        row_ptr[t + 1] = (int64_t)steps.size();
-        irow[t + 1] = (int64_t)isrc.size();
+        P.row_ptr[t + 1] = (int64_t)P.steps.size();
+        P.irow[t + 1] = (int64_t)P.isrc.size();
     }
+    return P;
+}
+
+ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int interp)
+{
+    const int64_t N = c->N;
+    std::vector<double> xs(3 * (size_t)N);
+    IBIM_CUDA(cudaMemcpyAsync(xs.data(), c->d_geo64, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    IBIM_CUDA(cudaStreamSynchronize(c->stream));
+    TcPlan P = tc_plan(xs, N, theta, tau_max, interp);
+    const std::vector<HostCluster>& cl = P.cl;
+    const int nc = (int)cl.size();
+    const int64_t n_t = P.n_t, n_real = P.n_real;
+    const std::vector<double>&tcx = P.tcx, &tcy = P.tcy, &tcz = P.tcz, &thalf = P.thalf;
+    const std::vector<int64_t>&row_ptr = P.row_ptr, &irow = P.irow;
+    const std::vector<int32_t>&steps = P.steps, &isrc = P.isrc;
+    const int64_t near_steps = P.near_steps, far_steps = P.far_steps;
     if (n_real + nc > INT32_MAX) return tc_fail(IBIM_ERR_ARG, "treecode: too many tiles");
 
     // clusters by height (leaves first) for the upward pass
@@ -1050,6 +1078,36 @@ extern "C" ibim_status ibim_treecode_setup(ibim_ctx* c, double theta, double tau
     if (target_interp != 0 && target_interp != 1) return tc_fail(IBIM_ERR_ARG, "target_interp must be 0 or 1");
     if (order < 4 || order > 6) return tc_fail(IBIM_ERR_ARG, "the Chebyshev order must be 4, 5 or 6");
     return tc_setup(c, theta, tau_max, order, target_interp);
+}
+
+extern "C" ibim_status ibim_treecode_plan(const double* xyz, int64_t N, double theta, double tau_max,
+                                          int target_interp, int64_t* sizes, int64_t* row_ptr, int32_t* steps,
+                                          int64_t* irow, int32_t* isrc)
+{
+    using namespace ibim;
+    if (xyz == nullptr || N <= 0 || sizes == nullptr || !(theta > 0.0 && theta < 1.0) || !(tau_max > 0.0) ||
+        !std::isfinite(tau_max) || (target_interp != 0 && target_interp != 1))
+        return tc_fail(IBIM_ERR_ARG, "need N > 0 coordinates, sizes, 0 < theta < 1, a finite tau_max > 0 and "
+                                     "target_interp 0 or 1");
+    std::vector<double> xs(3 * (size_t)N);
+    for (int64_t j = 0; j < N; ++j) {
+        for (int a = 0; a < 3; ++a) {
+            const double v = xyz[3 * j + a];
+            if (!std::isfinite(v)) return tc_fail(IBIM_ERR_NONFINITE, "non-finite coordinate");
+            xs[a * N + j] = v;
+        }
+    }
+    const TcPlan P = tc_plan(xs, N, theta, tau_max, target_interp);
+    sizes[0] = P.n_t;
+    sizes[1] = (int64_t)P.cl.size();
+    sizes[2] = (int64_t)P.steps.size();
+    sizes[3] = (int64_t)P.isrc.size();
+    sizes[4] = P.n_real;
+    if (row_ptr) std::copy(P.row_ptr.begin(), P.row_ptr.end(), row_ptr);
+    if (steps) std::copy(P.steps.begin(), P.steps.end(), steps);
+    if (irow) std::copy(P.irow.begin(), P.irow.end(), irow);
+    if (isrc) std::copy(P.isrc.begin(), P.isrc.end(), isrc);
+    return IBIM_OK;
 }
 
 extern "C" ibim_status ibim_treecode_info(ibim_ctx* c, int64_t* near_steps, int64_t* far_steps,

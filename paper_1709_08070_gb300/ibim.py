@@ -21,7 +21,7 @@ __all__ = [
     "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
     "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian", "ibim_solve_extrapolated",
-    "IBIM_F32T", "ibim_treecode_setup", "ibim_treecode_info",
+    "IBIM_F32T", "ibim_treecode_setup", "ibim_treecode_info", "ibim_treecode_plan",
 ]
 
 IBIM_F64 = 64
@@ -87,6 +87,8 @@ _SIGS = {
     "ibim_set_f32_variant": [_V, ctypes.c_int, ctypes.c_int],
     "ibim_treecode_setup": [_V, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int],
     "ibim_treecode_info": [_V, _I64P, _I64P, _I64P, _I64P, _I64P],
+    "ibim_treecode_plan": [_D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int, _I64P, _I64P,
+                           ctypes.POINTER(ctypes.c_int32), _I64P, ctypes.POINTER(ctypes.c_int32)],
     "ibim_f32_variant_info": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "ibim_build": [_D, _D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _V, _CTXP],
@@ -384,6 +386,26 @@ def ibim_treecode_info(ctx):
     v = [ctypes.c_int64(0) for _ in range(5)]
     _check(lib().ibim_treecode_info(ctx, *[ctypes.byref(x) for x in v]))
     return dict(zip(("near_steps", "far_steps", "interp_steps", "clusters", "target_tiles"), (x.value for x in v)))
+
+
+def ibim_treecode_plan(xyz, theta, tau_max, target_interp=0):
+    """Host-only tree and lists of the treecode for nodes xyz (N x 3):
+    dict(n_t, clusters, n_real, row_ptr, steps, irow, isrc) (numpy arrays)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    N = xyz.shape[0]
+    sizes = np.zeros(5, dtype=np.int64)
+    I64 = ctypes.POINTER(ctypes.c_int64)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    args = (xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), N, float(theta), float(tau_max), int(target_interp))
+    _check(lib().ibim_treecode_plan(*args, sizes.ctypes.data_as(I64), None, None, None, None))
+    n_t, ncl, S, I, n_real = (int(v) for v in sizes)
+    row_ptr = np.zeros(n_t + 1, dtype=np.int64)
+    irow = np.zeros(n_t + 1, dtype=np.int64)
+    steps = np.zeros(max(S, 1), dtype=np.int32)
+    isrc = np.zeros(max(I, 1), dtype=np.int32)
+    _check(lib().ibim_treecode_plan(*args, sizes.ctypes.data_as(I64), row_ptr.ctypes.data_as(I64),
+                                    steps.ctypes.data_as(I32), irow.ctypes.data_as(I64), isrc.ctypes.data_as(I32)))
+    return dict(n_t=n_t, clusters=ncl, n_real=n_real, row_ptr=row_ptr, steps=steps[:S], irow=irow, isrc=isrc[:I])
 
 
 def ibim_set_f32_variant(ctx, variant, ctas_per_sm=0):
