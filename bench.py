@@ -488,10 +488,10 @@ TREECODE = {"workload": "kirkwood_sphere_large", "R": 60.0, "h": 0.5, "band_k": 
 
 
 def _tc_pairs(info, order):
-    """Pair evaluations of one treecode application: near steps 1024 x 256,
-    far steps 1024 x the proxy chunks' nodes, interpolated steps order^3 x those."""
+    """Pair evaluations of one treecode application: near steps 512 x 256,
+    far steps 512 x the proxy chunks' nodes, interpolated steps order^3 x those."""
     pc = -(-order ** 3 // 32) * 32
-    return (info["near_steps"] * 256 + info["far_steps"] * pc) * 1024 + info["interp_steps"] * order ** 3 * pc
+    return (info["near_steps"] * 256 + info["far_steps"] * pc) * 512 + info["interp_steps"] * order ** 3 * pc
 
 
 def run_treecode(args):

@@ -296,7 +296,7 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
  *   - clusters are node ranges split as the coordinate bisection of built
  *     geometries splits them (left part B max(1, round(n / 2B)), B = 1024 for
  *     n >= 2048, 256 otherwise), down to 256-node tiles; target tiles have
- *     1024 nodes;
+ *     512 nodes;
  *   - a cluster is far from a target tile when r_T + r_C <= theta D and
  *     D >= max(2 tau_max, 1.5) 1.001 + 1e-3 + r_T + r_C + 0.25 (Angstrom;
  *     D the distance of the box centres, r_T the tile's box half-diagonal,
@@ -320,7 +320,7 @@ void ibim_wsnet_destroy(ibim_wsnet* net);
  * IBIM_ERR_STATE (no nodes), IBIM_ERR_CUDA.
  *
  * ibim_treecode_info: list sizes of the current setup (outputs may be NULL):
- * near source-tile steps, far cluster steps (each step is 1024 targets x 256
+ * near source-tile steps, far cluster steps (each step is 512 targets x 256
  * sources or proxies), interpolated far cluster steps (order^3 target proxies x order^3
  * proxies each), clusters, target tiles.  IBIM_ERR_STATE before setup.
  */

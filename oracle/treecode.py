@@ -30,7 +30,7 @@ Structure (the tiling is chosen so that a GPU can stream proxies like sources):
     extent (at least kMinHalf) as half side, so every cube lies inside its
     parent's; n^3 Chebyshev points of the second kind, radius = half side x
     sqrt(3);
-  * target tiles of 1024 consecutive nodes, bounding box centre and
+  * target tiles of 512 consecutive nodes, bounding box centre and
     half-diagonal r_T;
   * a cluster is far from a target tile when r_T + r_C <= theta D and
     D >= far_dist + r_T + r_C + kFarMargin (D the distance of the centres,
@@ -127,7 +127,7 @@ def target_cube(centre, half_extent):
 class TileTree:
     """Clusters of source tiles and the target tiles of an ordered node set."""
 
-    stile, ttile = 256, 1024
+    stile, ttile = 256, 512
 
     def __init__(self, xs):
         xs = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, 3)

@@ -19,7 +19,7 @@
 //
 // Tree: clusters are node ranges split as the coordinate bisection of the node
 // order splits them (left part B max(1, round(n / 2B)), B = 1024 for n >= 2048,
-// 256 otherwise) down to 256-node tiles.  Target tiles: 1024 nodes.  A
+// 256 otherwise) down to 256-node tiles.  Target tiles: 512 nodes.  A
 // cluster C is far from a target tile T when r_T + r_C <= theta D and
 // D >= far_dist + r_T + r_C + 0.25 A (D the distance of the box centres, r_T
 // the tile box half-diagonal, r_C the cube half-diagonal, far_dist =
@@ -30,7 +30,7 @@
 // Target-side interpolation (optional): a far cluster that is also far from
 // the target tile's own Chebyshev cube (r_Tc + r_C <= theta D, D >= far_dist +
 // r_Tc + r_C + 0.25 A, r_Tc the cube half-diagonal) is evaluated at the tile's
-// 216 target proxies instead of its 1024 targets (tc_m2l_kernel).  y1 is a
+// 216 target proxies instead of its 512 targets (tc_m2l_kernel).  y1 is a
 // scalar field of the target position and y2 = n_x . V(x) with
 //   V = [g d - (3 - B) (r.d / rho^2) r + (1 - th2 A) b r] / (4 pi rho^3),
 // so the fixup interpolates the four fields (y1, V) to each target.
@@ -58,8 +58,11 @@ struct Cheb {
     static constexpr int kM2lThreads = (kProxies + 31) / 32 * 32;  // one thread per target proxy
 };
 constexpr int kMaxProxies = Cheb<6>::kProxies;  // stride of the per-tile field buffer
-constexpr int kTcTpt = 2, kTcThreads = 512;
-constexpr int kTcTTile = kTcTpt * kTcThreads;  // 1024 targets
+// 512-node target tiles (two targets per thread, 256-thread CTAs, two CTAs
+// per SM): measured against 1024-node tiles, the smaller tiles' near regions
+// cut the list work by a fifth to a third at the same pair rate.
+constexpr int kTcTpt = 2, kTcThreads = 256, kTcMinCtas = 2;
+constexpr int kTcTTile = kTcTpt * kTcThreads;  // 512 targets
 constexpr double kTcMinHalf = 1e-3;            // smallest proxy-cube half side (A)
 constexpr double kTcFarMargin = 0.25;          // extra gap of a far cluster (A)
 static_assert(kMaxProxies <= kF32STile, "proxies of a cluster fit one source tile");
@@ -659,7 +662,7 @@ __global__ void __launch_bounds__(Cheb<NC>::kM2lThreads)
 
 // y = Lambda p + (1/(4 pi)) (partials of the segments that covered the row
 // + the interpolated far fields of the row's target proxies, when it has any).
-// One 256-thread block lies inside one 1024-node target tile.
+// One 256-thread block lies inside one target tile.
 template <int NC>
 __global__ void __launch_bounds__(256)
     tc_fixup_kernel(const double* __restrict__ part, TcSchedule s, int64_t N, double lambda1, double lambda2,
@@ -950,7 +953,7 @@ ibim_status tc_setup(ibim_ctx* c, double theta, double tau_max, int order, int i
     T->interp = interp ? 1 : 0;
     T->interp_steps = (int64_t)isrc.size();
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, 1, kTcThreads>, kTcThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_pair_kernel<kTcTpt, kTcMinCtas, kTcThreads>, kTcThreads, 0);
     const int64_t cap = (int64_t)std::max(1, occ) * c->num_sms;
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>(cap, T->total));
     T->Lb = std::max<int64_t>(1, (9 * T->total) / (10 * g));  // g Lb <= total as g <= total
@@ -1034,7 +1037,7 @@ static ibim_status tc_apply_order(ibim_ctx* c, TreeCode* T, const PairConsts& k,
                        T->Lb, (int64_t)T->grid, T->Ls, T->nseg, Cheb<NC>::kChunks};
     const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * N, 1, N};
     IBIM_TRY(timing_begin(c));
-    tc_pair_kernel<kTcTpt, 1, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
+    tc_pair_kernel<kTcTpt, kTcMinCtas, kTcThreads><<<T->grid, kTcThreads, 0, c->stream>>>(
         c->d_pos32, c->d_nrm32, T->d_src, T->d_frm, N, s, f32_consts(k), T->d_part, T->d_ctr, c->d_err, d_skip, g64);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
