@@ -40,3 +40,26 @@ def test_plan_rejects_bad_input():
     with pytest.raises(ibim.IbimError) as e:
         ibim.ibim_treecode_plan(bad, 0.5, 0.3, 0)
     assert e.value.status == 3
+
+
+@pytest.mark.parametrize("n", [1, 100, 256, 257, 511, 513, 1500, 2049])
+def test_plan_on_tiny_and_ragged_sizes(n):
+    """One node, one partial tile, tile boundaries +-1 and a split right above
+    2048: lists equal the oracle's and every source tile is covered once."""
+    from paper_1709_08070_gb300 import ibim
+    xs, _, _ = inputs.compact_sphere_cloud(n, radius=3.0 + n / 300.0, seed=n)
+    plan = ibim.ibim_treecode_plan(xs, 0.7, 0.3, 1)
+    tree = tc.TileTree(xs)
+    lists = tree.lists(0.7, 0.3, True)
+    n_real = plan["n_real"]
+    assert plan["n_t"] == tree.n_t == -(-n // 512) and plan["clusters"] == len(tree.clusters)
+    for t, (near, far, fint) in enumerate(lists):
+        row = plan["steps"][plan["row_ptr"][t]:plan["row_ptr"][t + 1]]
+        assert [int(v) for v in row if v < n_real] == list(near)
+        assert [int(v) - n_real for v in row if v >= n_real] == list(far)
+        assert [int(v) - n_real for v in plan["isrc"][plan["irow"][t]:plan["irow"][t + 1]]] == list(fint)
+        covered = list(near)
+        for ci in list(far) + list(fint):
+            c = tree.clusters[ci]
+            covered += list(range(c.j0 // 256, -(-c.j1 // 256)))
+        assert sorted(covered) == list(range(-(-n // 256)))
