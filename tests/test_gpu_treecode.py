@@ -130,3 +130,25 @@ def test_treecode_misuse_is_reported():
             ctx.matvec(P, d_in, y, precision=ibim.IBIM_F32T)
         assert e.value.status == 1
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [1, 100, 600])
+def test_treecode_on_tiny_and_ragged_sizes(n):
+    """One node, one partial tile and a ragged second tile: setup, upward
+    pass, list kernel and fixup give the FP32 operator (nothing is far)."""
+    xs, nr, w = inputs.compact_sphere_cloud(n, radius=2.0 + n / 200.0, seed=n)
+    ctx = ibim.Context.from_nodes(xs, nr, w, h=0.3)
+    N = ctx.N
+    for order, interp in ((6, 1), (4, 0)):
+        ctx.treecode_setup(0.7, 0.3, interp, order)
+        info = ctx.treecode_info()
+        assert info["far_steps"] == 0 and info["interp_steps"] == 0 and info["target_tiles"] == -(-N // 512)
+        P = ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0)
+        d_in = torch.from_numpy(inputs.random_vector(2 * N, seed=2)).cuda()
+        yt, y32 = torch.empty_like(d_in), torch.empty_like(d_in)
+        ctx.matvec(P, d_in, yt, precision=ibim.IBIM_F32T)
+        ctx.matvec(P, d_in, y32, precision=ibim.IBIM_F32C)
+        a, b = y32.cpu().numpy(), yt.cpu().numpy()
+        assert np.all(np.isfinite(b))
+        assert np.max(np.abs(b - a)) <= 1e-6 * np.max(np.abs(a)), (n, order)
+    ctx.close()
