@@ -55,6 +55,8 @@ FP32_LANES_PER_SM = 128
 # profiles/pair_sym_kernel_kirkwood80k.md.
 NCU_TRAFFIC_BYTES = {(2, 1, 512, 0): 5.686272e6, (2, 1, 512, 1): 7.012352e6}
 METRIC = "IBIM matvec interactions/s"
+L2_NOTE = ("GPU arm: a 256 MB buffer is written between timed steps (L2 is 129 MB); "
+           "oracle arm: host cores, no GPU cache involved")
 
 
 def reduce_over_ranks(ms, count, device):
@@ -176,35 +178,56 @@ def _series_kcal(W):
     return c["gpol_kcal"] if same else None
 
 
-def cpu_oracle_rate(target_s=10.0, max_rows=None):
+def cpu_oracle_rate(target_s=10.0, max_rows=None, threads=None):
     """FP64 oracle operator rows on the host cores, bounded sample: returns
-    (interactions/s, threads, sample description, elapsed)."""
+    (interactions/s, threads, sample description, elapsed).  threads: OpenMP
+    threads of the oracle (None = all host cores)."""
     import oracle
     from paper_1709_08070_gb300 import inputs
     W = WORKLOAD
-    g = oracle.sphere_nodes(W["R"], h=W["h"], eps=W["band_k"] * W["h"])
-    N = g["w"].size
-    P = oracle.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * W["h"], 0)
-    p = inputs.random_vector(2 * N, seed=3)
-    rows = inputs.random_rows(N, 256, seed=4)
-    t0 = time.perf_counter()
-    oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
-    dt = time.perf_counter() - t0
-    nrows = int(min(N, max(256, 256 * target_s / max(dt, 1e-3))))
-    if max_rows:
-        nrows = min(nrows, max_rows)
-    rows = inputs.random_rows(N, nrows, seed=5)
-    t0 = time.perf_counter()
-    oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
-    dt = time.perf_counter() - t0
-    return nrows * N / dt, oracle.num_threads(), "%d of %d operator rows of the %d-node workload (%d interactions)" % (
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        g = oracle.sphere_nodes(W["R"], h=W["h"], eps=W["band_k"] * W["h"])
+        N = g["w"].size
+        P = oracle.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * W["h"], 0)
+        p = inputs.random_vector(2 * N, seed=3)
+        probe = 256 if not threads or threads > 4 else 32
+        rows = inputs.random_rows(N, probe, seed=4)
+        t0 = time.perf_counter()
+        oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
+        dt = time.perf_counter() - t0
+        nrows = int(min(N, max(probe, probe * target_s / max(dt, 1e-3))))
+        if max_rows:
+            nrows = min(nrows, max_rows)
+        rows = inputs.random_rows(N, nrows, seed=5)
+        t0 = time.perf_counter()
+        oracle.matvec_rows(g["xs"], g["nrm"], g["w"], P, p, rows)
+        dt = time.perf_counter() - t0
+        used = oracle.num_threads()
+    finally:
+        oracle.set_num_threads(all_threads)
+    return nrows * N / dt, used, "%d of %d operator rows of the %d-node workload (%d interactions)" % (
         nrows, N, N, nrows * N), dt
 
 
+def kirkwood_config(N, ws):
+    """The workload as both arms state it in their bench lines."""
+    return dict(WORKLOAD, N=int(N), parallelism="replicas" if ws > 1 else "single", l2=L2_NOTE)
+
+
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle timed on the host cores on bounded
+    row samples of the same workload (rank 0 only; it loads no CUDA code)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
+    from oracle import build as oracle_build
+    oracle_build.build()
+    import oracle
+    W = WORKLOAD
+    N = oracle.sphere_nodes(W["R"], h=W["h"], eps=W["band_k"] * W["h"])["w"].size
     vals = []
     desc, cores = "", 0
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
@@ -217,7 +240,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, l2="n/a (host)"),
+            "config": kirkwood_config(N, ws),
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -255,30 +278,43 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         ctx.solve(P, dp, **opts)
-    ctx.timing_enable(True)
-    ctx.timing_reset()
+
+    def timed_steps(kernel_events):
+        """args.steps solves between barriers, each bracketed by CUDA events on
+        the solver's stream.  kernel_events: the library also brackets every
+        pair-kernel launch with events (GMRES then launches its step kernels
+        directly instead of replaying the captured step graph)."""
+        ctx.timing_enable(kernel_events)
+        ctx.timing_reset()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        out = []
+        barrier()
+        t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("ibim_timed_steps")  # lets a profiler select exactly the timed launches
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            out.append(ctx.solve(P, dp, **opts))
+            ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        wall_s = time.perf_counter() - t0
+        tim_ = ctx.timing()
+        ctx.timing_enable(False)
+        return out, [a.elapsed_time(b) for a, b in ev], tim_, wall_s
+
     clocks = Clocks(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    infos = []
-    barrier()
     clocks.start()
-    t_wall = time.perf_counter()
-    torch.cuda.nvtx.range_push("ibim_timed_steps")  # lets a profiler select exactly the timed launches
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        infos.append(ctx.solve(P, dp, **opts))
-        ev[i][1].record(stream)
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    wall = time.perf_counter() - t_wall
+    # the product path (graph replay): the headline value
+    infos, step_ms, tim_prod, wall = timed_steps(False)
+    # the same steps with the pair-kernel launches timed: the roofline
+    infos_k, step_ms_k, tim, _ = timed_steps(True)
     ck = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tim = ctx.timing()
-    ctx.timing_enable(False)
     interactions = sum(int(i["matvecs_f32"] + i["matvecs_f64"]) for i in infos) * N * N
     total_ms, interactions_all = reduce_over_ranks(float(sum(step_ms)), interactions, "cuda")
     value = interactions_all / (total_ms * 1e-3)
+    inter_k = sum(int(i["matvecs_f32"] + i["matvecs_f64"]) for i in infos_k) * N * N
 
     # ---- dominant kernel roofline (pair_f32_kernel), live CUDA-event timing
     peaks = _peaks()
@@ -293,6 +329,11 @@ def run_ours(args):
                 "frac": achieved_ops / peak_ops, "traffic": NCU_TRAFFIC_BYTES.get((tpt, minb, nthr, sym)),
                 "kernel": "pair_sym_kernel" if sym else "pair_f32_kernel", "ops_per_interaction": ops_per,
                 "interactions_per_launch": per_launch, "avg_launch_ms": avg_pair_ms,
+                "timed_in": "a second pass of the same %d steps with a CUDA event pair around every pair-kernel "
+                            "launch on the solver's stream (%.2f ms per step there, %.2f ms on the graph path; "
+                            "%.4g interactions/s)" % (args.steps, float(np.mean(step_ms_k)),
+                                                      float(np.mean(step_ms)),
+                                                      inter_k / (sum(step_ms_k) * 1e-3)),
                 "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock, measured peaks file)" % (
                     props.multi_processor_count, FP32_LANES_PER_SM, sm_max)}
     if ck.get("sm_mhz"):
@@ -377,19 +418,23 @@ def run_ours(args):
             "iters": ix["iters"], "relres_f64": ix["relres"]}
         if not args.skip_cpu:
             v, cores, desc, _ = cpu_oracle_rate(target_s=args.cpu_seconds)
+            v1, c1, desc1, _ = cpu_oracle_rate(target_s=args.cpu_seconds / 2, threads=1)
             extra["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": cores, "kind": "oracle",
-                                     "sample": desc}
+                                     "sample": desc,
+                                     "single_core": {"value": v1, "unit": "interactions/s", "cores": c1,
+                                                     "sample": desc1}}
+        if not args.skip_protein:
+            extra["protein_globule"] = protein_summary(args)
         extra["e2e"] = e2e
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": dict(WORKLOAD, N=N, parallelism="replicas" if ws > 1 else "single",
-                               l2="256 MB buffer written between timed steps",
-                               f32_variant={"index": variant, "targets_per_thread": tpt, "min_ctas_per_sm": minb,
-                                            "threads_per_cta": nthr, "symmetric": sym, "ctas_per_sm": bps}),
-                "gpu_launches": int(tim["total_launches"]), "clocks": ck, "roofline": roofline,
+                "config": kirkwood_config(N, ws),
+                "f32_variant": {"index": variant, "targets_per_thread": tpt, "min_ctas_per_sm": minb,
+                                "threads_per_cta": nthr, "symmetric": sym, "ctas_per_sm": bps},
+                "gpu_launches": int(tim_prod["total_launches"]), "clocks": ck, "roofline": roofline,
                 "wall_s_timed": wall}
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -419,6 +464,54 @@ def _globule(n_atoms, seed, h=0.5, probe=1.4):
     from paper_1709_08070_gb300 import ibim, inputs
     z, r, q = inputs.globule_atoms(int(n_atoms), seed=int(seed))
     return ibim.Context.molecule(z, r, q, probe=probe, h=h)
+
+
+def protein_summary(args, steps=3):
+    """The 2,000-atom globule (level-set SES, N about 211k) as an extra key of
+    the default line: geometry build time, FP32 operator interactions/s over
+    `steps` timed applications (L2 flushed between them), and one certified
+    FP32 solve to 1e-6 from the zero start."""
+    import torch
+
+    from paper_1709_08070_gb300 import ibim, inputs
+
+    W = PROTEIN
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = _globule(W["atoms"], inputs.SEED_PROTEIN, W["h"], W["probe"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    try:
+        N = ctx.N
+        P = ibim.Phys(W["eps_in"], W["eps_out"], W["kappa"], W["tau_k"] * W["h"], 0)
+        variant, bps, _ = ctx.autotune(P)
+        stream = torch.cuda.current_stream()
+        x = torch.from_numpy(inputs.random_vector(2 * N, seed=3)).cuda()
+        y = torch.empty_like(x)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        ctx.matvec(P, x, y)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            ctx.matvec(P, x, y)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=W["tol"], restart=W["restart"], maxit=2000, certify=1)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+        return {"config": dict(W, N=N), "geometry_build_s": build_s, "f32_variant": variant,
+                "operator_interactions_per_s": N * N / (float(np.mean(ms)) * 1e-3),
+                "operator_ms": float(np.mean(ms)),
+                "solve_f32_certified": {"s": solve_s, "iters": info["iters"], "relres_f64": info["relres"],
+                                        "converged": info["converged"], "gpol_kcal": info["gpol_kcal"],
+                                        "area": info["area"], "matvecs_f32": info["matvecs_f32"],
+                                        "matvecs_f64": info["matvecs_f64"]}}
+    finally:
+        ctx.close()
 
 
 def run_protein(args):
@@ -838,6 +931,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-protein", action="store_true",
+                    help="leave the 2,000-atom globule summary out of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--profile", action="store_true",
                     help="operator applications only (for profiler captures); prints no bench line")
@@ -865,11 +960,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    import __graft_entry__
-    __graft_entry__.build()
     if args.impl == "reference":
         run_reference(args)
-    elif args.profile:
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.profile:
         run_profile(args)
     elif args.workload == "treecode":
         run_treecode(args)

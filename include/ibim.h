@@ -371,7 +371,8 @@ ibim_status ibim_f32_variant_info(int v, int* targets_per_thread, int* min_ctas_
 /*
  * Autotuner: times every variant on this context's geometry with CUDA events,
  * keeps the fastest for this context and caches it for contexts built later
- * in the process with N in the same power-of-two bucket.  Returns the chosen
+ * in the process of the same geometry kind (analytic sphere, level-set
+ * surface or caller-given nodes) with N in the same power-of-two bucket.  Returns the chosen
  * variant, its resident CTAs per SM and its time per application (outputs
  * may be NULL).  Synchronises; call it outside any stream capture.
  */
@@ -392,20 +393,24 @@ ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int variant, int ctas_per_sm);
  * IBIM_F32C, without a context, from caller-owned device arrays:
  *   d_xstar, d_normal : N x 3 row-major FP64 projections x* and unit normals,
  *   d_w               : N FP64 weights w_j = J delta_eps(d_j) h^3,
- *   d_in, d_out       : 2N FP64 vectors [psi; psin] (must not overlap),
+ *   d_in, d_out       : 2N FP64 vectors [psi; psin]; the byte ranges of the two
+ *                       2N-vectors must not overlap (IBIM_ERR_ARG otherwise),
  *   stream            : cudaStream_t (NULL = legacy default stream).
- * Working memory (FP32 node copies, packed sources, partial sums, an error
- * word) comes from one fixed-size static device array, about 16.8 MB, that
- * every GPU loading this library holds until the process exits.  The call
- * allocates and frees nothing.  Limits: 1 <= N <= IBIM_NOALLOC_MAX_NODES;
- * larger N returns IBIM_ERR_ARG.
+ * The nodes keep the caller's order; as for ibim_build_from_nodes the product
+ * is fastest when every aligned block of 32 consecutive nodes is compact.
+ * Working memory (FP32 node copies in the frames of their aligned 32-node
+ * blocks, the frames, packed sources, partial sums, an error word) comes from
+ * one fixed-size static device array, about 16.9 MB, that every GPU loading
+ * this library holds until the process exits.  The call allocates and frees
+ * nothing.  Limits: 1 <= N <= IBIM_NOALLOC_MAX_NODES; larger N returns
+ * IBIM_ERR_ARG.
  * The first call on each device looks up that device's address of the array
- * (with the device current); make that first call before any stream capture.
- * All calls share the one array and it keeps the last call's contents: calls
- * that overlap on the GPU (on different streams, or from different host
- * threads) race on it and must be serialised by the caller.  The call
- * synchronises `stream` before returning and reports IBIM_ERR_DEVICE_TIMEOUT
- * when a bounded device wait gave up.
+ * (with the device current).  Every call reads the device error word back
+ * and synchronises `stream` before returning, so no call may be made inside
+ * a stream capture.  All calls share the one array and it keeps the last
+ * call's contents: calls that overlap on the GPU (on different streams, or
+ * from different host threads) race on it and must be serialised by the
+ * caller.  Returns IBIM_ERR_DEVICE_TIMEOUT when a bounded device wait gave up.
  */
 #define IBIM_NOALLOC_MAX_NODES 131072
 ibim_status ibim_matvec_noalloc(int64_t N, const double* d_xstar, const double* d_normal, const double* d_w,
@@ -459,6 +464,21 @@ ibim_status ibim_timing_enable(ibim_ctx* ctx, int enable);
 ibim_status ibim_timing_reset(ibim_ctx* ctx);
 ibim_status ibim_timing_get(ibim_ctx* ctx, double* pair_ms, int64_t* pair_launches,
                             int64_t* pair_interactions, int64_t* total_launches);
+
+/*
+ * Test hook of the failure path (not part of the paper's method).  A kernel
+ * whose bounded device wait gives up records IBIM_ERR_DEVICE_TIMEOUT in the
+ * context's device error word and returns; the host reads the word at the
+ * next synchronising call (ibim_matvec_host, ibim_energy, ibim_solve,
+ * ibim_solve_host, ibim_solve_extrapolated, ibim_solve_batch), which then
+ * returns IBIM_ERR_DEVICE_TIMEOUT and clears the word, so the context stays
+ * usable.  This call sets the same bit from one device thread on the context
+ * stream, after the work already queued there, so that this path can be
+ * exercised without making any wait give up.
+ *   status: IBIM_ERR_DEVICE_TIMEOUT (anything else is IBIM_ERR_ARG).
+ * Asynchronous.
+ */
+ibim_status ibim_debug_raise_device_error(ibim_ctx* ctx, int status);
 
 const char* ibim_last_error(void);
 void ibim_destroy(ibim_ctx* ctx);

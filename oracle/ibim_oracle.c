@@ -432,3 +432,15 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Set the number of OpenMP threads of later oracle calls (n >= 1; no effect
+ * when built without OpenMP).  Used to time the oracle on one host core. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "Phys", "lib", "num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
+    "Phys", "lib", "num_threads", "set_num_threads", "delta_eps", "pair_kernels", "matvec", "matvec_rows", "dense",
     "rhs", "psi_rxn", "gpol", "area", "sphere_nodes", "gmres", "KCAL_PER_E2_A",
     "ls_grid", "make_grid", "grid_coords", "ls_ses", "ls_steps", "ls_band", "ses_nodes", "jacobian",
     "jacobian_weights", "solve_energy", "extrapolated_energy",
@@ -80,6 +80,8 @@ def lib():
                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -97,6 +99,11 @@ def _f64(a, shape=None):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of later oracle calls (OpenMP over independent rows)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def delta_eps(eta, eps):

@@ -246,6 +246,20 @@ extern "C" {
 
 const char* ibim_last_error(void) { return g_err.c_str(); }
 
+// One thread sets bits of the device error word, as a kernel whose bounded
+// wait gave up does (the failure-path test hook below).
+__global__ void raise_device_error_kernel(unsigned* __restrict__ err, unsigned bits) { atomicOr(err, bits); }
+
+ibim_status ibim_debug_raise_device_error(ibim_ctx* c, int status)
+{
+    if (c == nullptr) return fail(IBIM_ERR_ARG, "ctx is NULL");
+    if (status != IBIM_ERR_DEVICE_TIMEOUT) return fail(IBIM_ERR_ARG, "only IBIM_ERR_DEVICE_TIMEOUT can be raised");
+    raise_device_error_kernel<<<1, 1, 0, c->stream>>>(c->d_err, kDevErrTimeout);
+    count_launch(c);
+    IBIM_CUDA(cudaGetLastError());
+    return IBIM_OK;
+}
+
 void ibim_destroy(ibim_ctx* c)
 {
     if (c == nullptr) return;

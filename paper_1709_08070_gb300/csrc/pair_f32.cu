@@ -427,8 +427,8 @@ ibim_status f32_pack_to(ibim_ctx* c, VecRef in, float4* dst, const int* d_skip)
 }
 
 // Launchers on caller-supplied buffers (used by the allocation-free entry
-// point): variant (kF32Tpt, 1), no chunk frames (positions relative to one
-// common origin), arrays padded as above.
+// point): variant (kF32Tpt, 1), chunk frames and positions in them as a
+// context's, arrays padded as above.
 int f32_occupancy_per_sm()
 {
     int occ = 0;
@@ -436,11 +436,11 @@ int f32_occupancy_per_sm()
     return occ < 1 ? 1 : occ;
 }
 
-cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, int64_t N,
-                                const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
+cudaError_t launch_pair_f32_raw(const float4* tpos, const float4* tnrm, const float4* src, const float4* frames,
+                                int64_t N, const PairSchedule& s, const PairConsts& k, double* part, unsigned* err,
                                 cudaStream_t stream, const double* xs_aos, const double* nrm_aos)
 {
-    const PairArgs a{tpos, tnrm, src, nullptr, N, s, f32_consts(k), part, err, nullptr, Geo64{xs_aos, nrm_aos, 3, 1}};
+    const PairArgs a{tpos, tnrm, src, frames, N, s, f32_consts(k), part, err, nullptr, Geo64{xs_aos, nrm_aos, 3, 1}};
     launch_variant<kF32Tpt, 1, kF32Threads>(a, stream);
     return cudaGetLastError();
 }

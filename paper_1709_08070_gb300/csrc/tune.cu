@@ -1,7 +1,9 @@
 // Autotuner of the FP32 pair-sum kernel: measures each variant (targets per
 // thread x CTAs per SM) on a context's own geometry with CUDA events and keeps
-// the fastest, cached per problem-size bucket (floor(log2 N)) for contexts
-// built later in the process.
+// the fastest, cached per (geometry kind, problem-size bucket floor(log2 N))
+// for contexts built later in the process: an analytic sphere, a level-set
+// surface and a caller's node cloud of the same size have different near-field
+// shares, so one kind's choice is not applied to another.
 #include <map>
 #include <mutex>
 #include <vector>
@@ -12,7 +14,7 @@ namespace ibim {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<int, std::pair<int, int>> g_tune_cache;  // bucket -> (variant, CTAs per SM)
+std::map<std::pair<int, int>, std::pair<int, int>> g_tune_cache;  // (kind, bucket) -> (variant, CTAs per SM)
 
 int size_bucket(int64_t N)
 {
@@ -20,6 +22,15 @@ int size_bucket(int64_t N)
     while ((int64_t)1 << (b + 1) <= N) ++b;
     return b;
 }
+
+// 0: caller-given nodes, 1: analytic sphere, 2: level-set surface of atoms.
+int geometry_kind(const ibim_ctx* c)
+{
+    if (c->d_phi != nullptr) return 2;
+    return c->band_eps > 0.0 ? 1 : 0;
+}
+
+std::pair<int, int> cache_key(const ibim_ctx* c) { return {geometry_kind(c), size_bucket(c->N)}; }
 
 __global__ void fill_kernel(double* __restrict__ p, int64_t n)
 {
@@ -31,7 +42,7 @@ __global__ void fill_kernel(double* __restrict__ p, int64_t n)
 void apply_cached_tuning(ibim_ctx* c)
 {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune_cache.find(size_bucket(c->N));
+    auto it = g_tune_cache.find(cache_key(c));
     if (it != g_tune_cache.end()) {
         c->f32_variant = it->second.first;
         c->f32_bps = it->second.second;
@@ -118,7 +129,7 @@ extern "C" ibim_status ibim_autotune(ibim_ctx* c, const ibim_phys* phys, int* va
     c->tuned = 1;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[size_bucket(N)] = pick;
+        g_tune_cache[cache_key(c)] = pick;
     }
     if (variant_out) *variant_out = pick.first;
     if (ctas_per_sm_out) *ctas_per_sm_out = f32_max_bps(pick.first);

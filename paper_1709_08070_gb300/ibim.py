@@ -108,6 +108,7 @@ _SIGS = {
     "ibim_wsnet_gradient": [_V, ctypes.c_int64, ctypes.c_int64, _D, ctypes.POINTER(ctypes.c_float)],
     "ibim_wsnet_train": [_V, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D],
     "ibim_wsnet_predict": [_V, _V, ctypes.POINTER(Phys), _V],
+    "ibim_debug_raise_device_error": [_V, ctypes.c_int],
 }
 
 _lib = None
@@ -346,6 +347,11 @@ def ibim_timing_get(ctx):
     _check(lib().ibim_timing_get(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(inter), ctypes.byref(tot)))
     return {"pair_ms": ms.value, "pair_launches": n.value, "pair_interactions": inter.value,
             "total_launches": tot.value}
+
+
+def ibim_debug_raise_device_error(ctx, status=6):
+    """Sets the device-timeout bit of the context's error word (failure-path test hook)."""
+    _check(lib().ibim_debug_raise_device_error(ctx, int(status)))
 
 
 def ibim_matvec_noalloc(N, d_xstar, d_normal, d_w, phys, d_in, d_out, stream=None):

@@ -72,32 +72,69 @@ def test_cavity_shell_matches_oracle():
     ctx.close()
 
 
+def _rows_every_variant(ctx, bo, inv, rows, h, seed, variants, with_f64=True):
+    """Oracle rows `rows` (oracle numbering) of the operator on the shared node
+    set against the library's, element by element per output block, for the
+    FP64 path (1e-10) and each FP32 variant in `variants` at its occupancy-limited
+    grid (1e-5)."""
+    N = ctx.N
+    P = ibim.Phys(1.0, 80.0, 0.1257, h, 0)
+    Po = oracle.Phys(1.0, 80.0, 0.1257, h, 0)
+    p_orc = inputs.random_vector(2 * N, seed=seed)
+    p_gpu = np.empty(2 * N)
+    p_gpu[inv] = p_orc[:N]
+    p_gpu[N + inv] = p_orc[N:]
+    y1o, y2o = oracle.matvec_rows(bo["xs"], bo["nrm"], bo["w"], Po, p_orc, rows)
+    din = torch.from_numpy(p_gpu).cuda()
+    dout = torch.empty_like(din)
+    configs = ([(ibim.IBIM_F64, None, 1e-10)] if with_f64 else []) + [(ibim.IBIM_F32C, v, 1e-5) for v in variants]
+    for prec, v, tol in configs:
+        if v is not None:
+            ctx.set_f32_variant(v, 0)
+        ctx.matvec(P, din, dout, precision=prec)
+        y = dout.cpu().numpy()
+        errs = []
+        for got, ref in ((y[:N][inv[rows]], y1o), (y[N:][inv[rows]], y2o)):
+            errs += [np.linalg.norm(got - ref) / np.linalg.norm(ref), np.max(np.abs(got - ref)) / np.max(np.abs(ref))]
+        print("globule N=%d prec=%d variant %s: block 1 rel %.2e worst %.2e | block 2 rel %.2e worst %.2e"
+              % (N, prec, v, *errs))
+        assert max(errs) < tol, (prec, v, errs)
+
+
 def test_globule_operator_on_gpu_geometry():
     """2,000-atom seeded globule, probe 1.4, h = 0.5, eps = 2h: geometry parity,
-    then operator rows on the shared nodes (FP64 1e-10, FP32 1e-5)."""
+    then 2,048 operator rows on the shared nodes, element by element, for the
+    FP64 path (1e-10) and every FP32 variant (1e-5)."""
     z, r, q = inputs.globule_atoms(2000)
     h = 0.5
     ctx, bo, bg, jg, jo = _compare(z, r, 1.4, h, 2 * h)
     N = ctx.N
     assert N > 50000
     assert len(jg) == N == len(bo["w"])  # identical node sets on this input
-    P = ibim.Phys(1.0, 80.0, 0.1257, h, 0)
-    Po = oracle.Phys(1.0, 80.0, 0.1257, h, 0)
     inv = np.empty(N, dtype=np.int64)
     inv[jo] = jg  # oracle node -> gpu node
-    p_orc = inputs.random_vector(2 * N, seed=41)
-    p_gpu = np.empty(2 * N)
-    p_gpu[inv] = p_orc[:N]
-    p_gpu[N + inv] = p_orc[N:]
-    rows = inputs.random_rows(N, 1024, seed=42)  # oracle rows
-    y1o, y2o = oracle.matvec_rows(bo["xs"], bo["nrm"], bo["w"], Po, p_orc, rows)
-    din = torch.from_numpy(p_gpu).cuda()
-    dout = torch.empty_like(din)
-    for prec, tol in ((ibim.IBIM_F64, 1e-10), (ibim.IBIM_F32C, 1e-5)):
-        ctx.matvec(P, din, dout, precision=prec)
-        y = dout.cpu().numpy()
-        e1 = np.linalg.norm(y[:N][inv[rows]] - y1o) / np.linalg.norm(y1o)
-        e2 = np.linalg.norm(y[N:][inv[rows]] - y2o) / np.linalg.norm(y2o)
-        print("globule N=%d prec=%d rel err %.3e %.3e" % (N, prec, e1, e2))
-        assert max(e1, e2) < tol, (prec, e1, e2)
+    rows = inputs.random_rows(N, 2048, seed=42)  # oracle rows
+    _rows_every_variant(ctx, bo, inv, rows, h, 41, range(len(ibim.ibim_f32_variants())))
+    ctx.close()
+
+
+def test_ten_thousand_atom_globule_operator_rows():
+    """A 10,000-atom globule of the learned-start evaluation size (about 740k
+    nodes): geometry parity with the oracle's level set, then 1,024 seeded
+    oracle rows of the FP32 operator (the autotuner's choice and both
+    symmetric variants), element by element (1e-5).  The FP64 operator is
+    left out at this size (about a minute per application)."""
+    z, r, q = inputs.globule_atoms(10000, seed=inputs.SEED_LEARNED + 10000)
+    h = 0.5
+    ctx, bo, bg, jg, jo = _compare(z, r, 1.4, h, 2 * h)
+    N = ctx.N
+    assert N > 500000
+    assert len(jg) == N == len(bo["w"])
+    inv = np.empty(N, dtype=np.int64)
+    inv[jo] = jg
+    P = ibim.Phys(1.0, 80.0, 0.1257, h, 0)
+    tuned, _, _ = ctx.autotune(P)
+    sym = [v for v, info in enumerate(ibim.ibim_f32_variants()) if info[3]]
+    rows = inputs.random_rows(N, 1024, seed=43)
+    _rows_every_variant(ctx, bo, inv, rows, h, 44, [tuned] + [v for v in sym if v != tuned], with_f64=False)
     ctx.close()

@@ -1,0 +1,143 @@
+"""Every FP32 pair-kernel variant and the FP64 path against the FP64 oracle,
+element by element.
+
+The operator is the discrete system of Sec. 2.2 with the regularisation of
+Sec. 2.2.1 (final linear system of Sec. 3.3).  Each side builds its own
+geometry from the same parameters and nodes are matched through their grid
+coordinates.  Besides the relative 2-norm over each output block, every
+element is checked:
+    max_i |y_i - y_i^oracle| / max_i |y_i^oracle|  (per block)
+must stay below 1e-5 for the FP32 compensated operator (each compiled
+variant, one-directional and symmetric, at its occupancy-limited grid -- the
+launch configuration the benchmark times -- and at one CTA per SM) and below
+1e-10 for the FP64 operator.  A few rows decided wrongly at the tube
+boundary would pass a 2-norm over tens of thousands of rows but not this.
+
+Cases: every row of the Born sphere (R = 2, h = 0.25, band 3h) and of a
+small level-set globule (14 atoms, about 4.5k nodes) at kappa = 0.1257 and
+kappa = 0; 2,048 seeded rows of the 80k-node Kirkwood sphere.  (The
+2,000-atom and 10,000-atom globules are in test_gpu_levelset.py.)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1709_08070_gb300 import ibim  # noqa: E402
+
+TOL = {ibim.IBIM_F64: 1e-10, ibim.IBIM_F32C: 1e-5}
+
+
+def _match(gpu_ijk, orc_ijk):
+    """perm with gpu node j == oracle node perm[j] (same grid nodes on both sides)."""
+    ko = {tuple(v): i for i, v in enumerate(orc_ijk)}
+    perm = np.array([ko[tuple(v)] for v in gpu_ijk], dtype=np.int64)
+    assert np.unique(perm).size == perm.size == len(orc_ijk)
+    return perm
+
+
+def _to_gpu(v, perm, N):
+    """oracle-ordered 2N vector -> library order."""
+    return np.concatenate([v[:N][perm], v[N:][perm]])
+
+
+def _errors(y, yo):
+    return (float(np.linalg.norm(y - yo) / np.linalg.norm(yo)), float(np.max(np.abs(y - yo)) / np.max(np.abs(yo))))
+
+
+def _assert_blocks(y1, y2, y1o, y2o, tol, what):
+    e1, e2 = _errors(y1, y1o), _errors(y2, y2o)
+    print("%s: block 1 rel %.2e worst %.2e | block 2 rel %.2e worst %.2e" % (what, *e1, *e2))
+    assert max(e1 + e2) < tol, (what, e1, e2)
+
+
+def _configs():
+    """(precision, variant, ctas_per_sm) of every operator configuration."""
+    out = [(ibim.IBIM_F64, None, 0)]
+    for v in range(len(ibim.ibim_f32_variants())):
+        for bps in (0, 1):
+            out.append((ibim.IBIM_F32C, v, bps))
+    return out
+
+
+def _run_all(ctx, P, p_gpu, check):
+    """Applies every configuration to p_gpu and hands the result to check."""
+    din = torch.from_numpy(np.ascontiguousarray(p_gpu)).cuda()
+    dout = torch.empty_like(din)
+    for prec, v, bps in _configs():
+        if v is not None:
+            ctx.set_f32_variant(v, bps)
+        dout.fill_(float("nan"))
+        ctx.matvec(P, din, dout, precision=prec)
+        y = dout.cpu().numpy()
+        assert np.all(np.isfinite(y)), (prec, v, bps)
+        check(y, prec, "prec %d variant %s ctas/SM %d" % (prec, v, bps))
+
+
+def _all_rows(ctx, xs, nrm, w, perm, kappa, eps_in, tau, seed):
+    N = ctx.N
+    P = ibim.Phys(eps_in, 80.0, kappa, tau, 0)
+    Po = oracle.Phys(eps_in, 80.0, kappa, tau, 0)
+    p = inputs.random_vector(2 * N, seed=seed)
+    yo = oracle.matvec(xs, nrm, w, Po, p)
+    yo_g = _to_gpu(yo, perm, N)
+
+    def check(y, prec, what):
+        _assert_blocks(y[:N], y[N:], yo_g[:N], yo_g[N:], TOL[prec], "N %d kappa %g %s" % (N, kappa, what))
+
+    _run_all(ctx, P, _to_gpu(p, perm, N), check)
+
+
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_born_sphere_every_row_every_variant(kappa):
+    R, h = 2.0, 0.25
+    ctx = ibim.Context.sphere(R, h=h, band_eps=3 * h)
+    try:
+        g = oracle.sphere_nodes(R, h=h, eps=3 * h)
+        perm = _match(ctx.nodes()["ijk"], g["ijk"])
+        _all_rows(ctx, g["xs"], g["nrm"], g["w"], perm, kappa, 1.0, h, seed=51)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_small_levelset_globule_every_row_every_variant(kappa):
+    z, r, q = inputs.globule_atoms(14, seed=21)
+    h = 0.5
+    ctx = ibim.Context.molecule(z, r, None, probe=1.4, h=h, band_eps=2 * h)
+    try:
+        b = oracle.ses_nodes(z, r, 1.4, h, 2 * h)
+        assert 3000 < b["w"].size <= 5000
+        perm = _match(ctx.nodes()["ijk"], b["ijk"])
+        _all_rows(ctx, b["xs"], b["nrm"], b["w"], perm, kappa, 1.0, h, seed=52)
+    finally:
+        ctx.close()
+
+
+def test_kirkwood_sphere_sampled_rows_every_variant():
+    R, h = 20.0, 0.5
+    ctx = ibim.Context.sphere(R, h=h, band_eps=2 * h)
+    try:
+        N = ctx.N
+        assert N > 70000
+        g = oracle.sphere_nodes(R, h=h, eps=2 * h)
+        perm = _match(ctx.nodes()["ijk"], g["ijk"])
+        P = ibim.Phys(2.0, 80.0, 0.1257, h, 0)
+        Po = oracle.Phys(2.0, 80.0, 0.1257, h, 0)
+        p = inputs.random_vector(2 * N, seed=53)
+        rows = inputs.random_rows(N, 2048, seed=54)  # library rows
+        y1o, y2o = oracle.matvec_rows(g["xs"], g["nrm"], g["w"], Po, p, perm[rows])
+
+        def check(y, prec, what):
+            _assert_blocks(y[:N][rows], y[N:][rows], y1o, y2o, TOL[prec], "kirkwood %s" % what)
+
+        _run_all(ctx, P, _to_gpu(p, perm, N), check)
+    finally:
+        ctx.close()

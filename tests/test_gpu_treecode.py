@@ -23,6 +23,22 @@ from paper_1709_08070_gb300 import ibim  # noqa: E402
 
 CENTRES = [(28.0 * i, 28.0 * j, 0.0) for i in range(3) for j in range(3)]
 
+# Documented approximation bound of the treecode against the direct operator
+# at theta <= 0.8, by Chebyshev points per axis: relative 2-norm per output
+# block and worst element / max |y| per block.  It is a statement about the
+# far-field interpolation alone, so both the oracle's treecode and the GPU's
+# are held to it against the direct FP64 oracle (the GPU with 1e-6 more for
+# its FP32 arithmetic), whatever tiles either side uses.
+TC_BOUND = {6: 5e-7, 5: 5e-7, 4: 1e-5}
+
+
+def _rel_worst(a, b, N):
+    out = []
+    for blk in (slice(0, N), slice(N, 2 * N)):
+        out += [np.linalg.norm(a[blk] - b[blk]) / np.linalg.norm(b[blk]),
+                np.max(np.abs(a[blk] - b[blk])) / np.max(np.abs(b[blk]))]
+    return out
+
 
 def _rel(a, b, N):
     return (np.linalg.norm(a[:N] - b[:N]) / np.linalg.norm(b[:N]), np.linalg.norm(a[N:] - b[N:]) / np.linalg.norm(b[N:]))
@@ -61,6 +77,14 @@ def test_treecode_matches_oracle_treecode_on_caller_cloud(theta, n_per, interp, 
           "(worst %.2e); oracle treecode vs direct %.2e %.2e" % (theta, interp, order, N, near, far, fint, *r, worst,
                                                                  *approx))
     assert max(r) < 1e-6 and worst < 1e-5
+    # both treecodes against the direct oracle, at the order's bound
+    assert theta <= 0.8
+    e_orc = _rel_worst(yo, ye, N)
+    e_gpu = _rel_worst(y, ye, N)
+    print("  vs direct oracle: oracle treecode %s, GPU treecode %s (bound %.0e)"
+          % (" ".join("%.2e" % v for v in e_orc), " ".join("%.2e" % v for v in e_gpu), TC_BOUND[order]))
+    assert max(e_orc) < TC_BOUND[order], e_orc
+    assert max(e_gpu) < TC_BOUND[order] + 1e-6, e_gpu
     ctx.close()
 
 

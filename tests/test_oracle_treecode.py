@@ -199,3 +199,24 @@ def test_target_interpolation_clears_the_tube_and_stays_accurate():
     print("target interpolation, theta 0.8, lists %s: error n = 4, 6: %s (source side only: %.2e)"
           % (sizes, ["%.2e" % e for e in errs], e0))
     assert errs[0] > errs[1] and errs[1] < 5.0 * e0 + 1e-9 and errs[1] < 1e-6
+
+
+@pytest.mark.parametrize("theta,n_per,interp,order,bound", [(0.6, 1000, 1, 6, 5e-7), (0.7, 1000, 0, 5, 5e-7),
+                                                            (0.8, 1500, 1, 4, 1e-5)])
+def test_error_within_the_documented_bound(theta, n_per, interp, order, bound):
+    """The approximation bound the GPU tests hold both treecodes to (relative
+    2-norm and worst element / max |y| per output block against the direct
+    operator, theta <= 0.8): 5e-7 with 5 or 6 Chebyshev points per axis,
+    1e-5 with 4.  It depends on the interpolation order and the separation
+    only, not on how nodes are grouped into tiles."""
+    xs, nr, w = _cloud(n_per)
+    N = xs.shape[0]
+    P = oracle.Phys(2.0, 80.0, 0.1257, 0.3)
+    p = inputs.random_vector(2 * N, seed=6)
+    tree = tc.TileTree(xs)
+    lists = tree.lists(theta, 0.3, bool(interp))
+    yt = tc.treecode_matvec(xs, nr, w, P, p, n=order, tree=tree, lists=lists)
+    ye = oracle.matvec(xs, nr, w, P, p)
+    for blk in (slice(0, N), slice(N, 2 * N)):
+        assert np.linalg.norm(yt[blk] - ye[blk]) / np.linalg.norm(ye[blk]) < bound
+        assert np.max(np.abs(yt[blk] - ye[blk])) / np.max(np.abs(ye[blk])) < bound
