@@ -48,6 +48,12 @@ typedef enum {
 /* Arithmetic of the pair sums (the N x N kernel evaluations). */
 typedef enum {
     IBIM_F64 = 64,  /* plain FP64 pair sums */
+    IBIM_FF = 65,   /* float-float ("double-single") pair sums on the FP32 pipe: every
+                       quantity an unevaluated sum of two floats (about 48 bits), exp by a
+                       table-driven reduction, 1/rho by a Newton step, tube ties decided in
+                       FP64; the same operator as IBIM_F64 to within 1e-10 of max |y| per
+                       element, several times faster on a GPU whose FP64 rate is a small
+                       fraction of its FP32 rate */
     IBIM_F32C = 32, /* FP32 pair sums, Kahan-compensated per source tile, tile sums in FP64 */
     IBIM_F32T = 33  /* as IBIM_F32C near each target tile, far clusters through Chebyshev
                        proxies (ibim_treecode_setup first; tube rule 0 only) */
@@ -171,7 +177,7 @@ ibim_status ibim_get_jacobian(const ibim_ctx* ctx, double* J);
  *   y1_i = lambda1 psi_i  + sum_j [K11(i,j) w_j psi_j - K12(i,j) w_j psin_j]
  *   y2_i = lambda2 psin_i + sum_j [K21(i,j) w_j psi_j - K22(i,j) w_j psin_j]
  * d_in, d_out: device, 2N doubles each, must not overlap.  Asynchronous on
- * the context stream.  precision: IBIM_F64, IBIM_F32C or IBIM_F32T.
+ * the context stream.  precision: IBIM_F64, IBIM_FF, IBIM_F32C or IBIM_F32T.
  */
 ibim_status ibim_matvec(ibim_ctx* ctx, const ibim_phys* phys, int precision, const double* d_in,
                         double* d_out);
@@ -199,26 +205,27 @@ ibim_status ibim_area(ibim_ctx* ctx, double* area);
 /* ------------------------------------------------------------------ solve */
 
 typedef struct {
-    int precision;  /* IBIM_F64, IBIM_F32C or IBIM_F32T: operator used inside GMRES  */
+    int precision;  /* IBIM_F64, IBIM_FF, IBIM_F32C or IBIM_F32T: operator used inside GMRES */
     double tol;     /* relative residual ||g - A p||_2 / ||g||_2 target (e.g. 1e-6)      */
     int maxit;      /* maximum Arnoldi steps in total                                    */
     int restart;    /* GMRES restart length m (1..128)                                   */
     int start;      /* 0: p0 = 0; 1: p0 = Lambda^-1 g (Sec. 3.3); 3: caller's d_p on entry */
-    int certify;    /* 1: after convergence recompute the residual with the FP64
-                       operator and restart from the current p while it is above tol
-                       (iterative refinement); 0: residuals use the chosen operator   */
+    int certify;    /* 1: after convergence recompute the residual with an FP64-accurate
+                       operator (IBIM_FF) and restart from the current p while it is
+                       above tol (iterative refinement); 2: the same with the plain FP64
+                       operator (IBIM_F64); 0: residuals use the chosen operator        */
 } ibim_solve_opts;
 
 typedef struct {
     int iters;           /* Arnoldi steps taken (the paper's GMRES iteration count)     */
     int cycles;          /* GMRES cycles (restarts + refinement passes)                 */
     int converged;       /* 1 when the reported residual is below tol                   */
-    double relres;       /* final ||g - A p|| / ||g|| (FP64 operator when certify = 1)  */
+    double relres;       /* final ||g - A p|| / ||g|| (FP64-accurate operator when certify > 0) */
     double gpol;         /* G_pol, e^2/Angstrom                                          */
     double gpol_kcal;    /* G_pol, kcal/mol                                              */
     double area;         /* surface area (Angstrom^2)                                    */
-    int64_t matvecs_f32; /* operator applications by precision                           */
-    int64_t matvecs_f64;
+    int64_t matvecs_f32; /* operator applications by precision: FP32 (IBIM_F32C/F32T)    */
+    int64_t matvecs_f64; /* and FP64-accurate (IBIM_F64 and IBIM_FF)                     */
 } ibim_solve_info;
 
 /*

@@ -163,9 +163,12 @@ ibim_status ensure_operator_workspaces(ibim_ctx* c)
     if (c->ws_sized) return IBIM_OK;
     const int64_t N = c->N;
     IBIM_TRY(ensure(c, &c->d_src, &c->src_bytes,
-                    std::max((size_t)N * 8 * sizeof(double), (size_t)padded_nodes(N) * 2 * sizeof(float4))));
+                    std::max(std::max((size_t)N * 8 * sizeof(double), (size_t)padded_nodes(N) * 2 * sizeof(float4)),
+                             ff_src_bytes(N))));
+    IBIM_TRY(ff_prepare_context(c));
     const PairSchedule s64 = make_schedule(N, kF64TTile, N, kF64STile, f64_grid_cap(c));
     size_t need = (size_t)s64.grid * s64.max_segs * 2 * kF64TTile * sizeof(double);
+    need = std::max(need, ff_part_doubles(c) * sizeof(double));
     const int keep = c->f32_variant, keep_bps = c->f32_bps;
     c->f32_bps = 0;
     for (int v = 0; v < f32_variant_count(); ++v) {
@@ -203,8 +206,18 @@ ibim_status apply_operator(ibim_ctx* c, const PairConsts& k, int precision, VecR
         IBIM_TRY(timing_end(c, N * N));
         return f64_fixup(c, k, s, in, out, d_skip);
     }
-    return fail(IBIM_ERR_ARG, "precision must be IBIM_F64 (64), IBIM_F32C (32) or IBIM_F32T (33)");
+    if (precision == IBIM_FF) {
+        const PairSchedule s = ff_schedule(c);
+        IBIM_TRY(ff_pack(c, in, d_skip));
+        IBIM_TRY(timing_begin(c));
+        IBIM_TRY(ff_pairs(c, k, s, d_skip));
+        IBIM_TRY(timing_end(c, N * N));
+        return ff_fixup(c, k, s, in, out, d_skip);
+    }
+    return fail(IBIM_ERR_ARG, "precision must be IBIM_F64 (64), IBIM_FF (65), IBIM_F32C (32) or IBIM_F32T (33)");
 }
+
+static bool valid_precision(int p) { return p == IBIM_F64 || p == IBIM_FF || p == IBIM_F32C || p == IBIM_F32T; }
 
 // Reads the device error word after a synchronisation point.
 static ibim_status check_device_error(ibim_ctx* c)
@@ -284,6 +297,7 @@ void ibim_destroy(ibim_ctx* c)
     cudaFree(c->d_io);
     cudaFree(c->d_aux);
     cudaFree(c->d_yrev);
+    cudaFree(c->d_fftab);
     ibim::tc_destroy(c->tc);
     cudaFree(c->d_phi);
     delete c;
@@ -577,7 +591,7 @@ ibim_status ibim_energy(ibim_ctx* c, const ibim_phys* phys, int precision, const
 {
     if (c == nullptr || d_p == nullptr || gpol == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (precision != IBIM_F64 && precision != IBIM_F32C && precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
+    if (!valid_precision(precision)) return fail(IBIM_ERR_ARG, "bad precision");
     if (c->Nc <= 0) return fail(IBIM_ERR_STATE, "no charges set");
     IBIM_TRY(energy_launch(c, *phys, d_p, d_psi_rxn, gpol));
     return check_device_error(c);
@@ -594,7 +608,8 @@ ibim_status ibim_solve(ibim_ctx* c, const ibim_phys* phys, const ibim_solve_opts
 {
     if (c == nullptr || o == nullptr || d_p == nullptr || info == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C && o->precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
+    if (!valid_precision(o->precision)) return fail(IBIM_ERR_ARG, "bad precision");
+    if (o->certify < 0 || o->certify > 2) return fail(IBIM_ERR_ARG, "certify must be 0, 1 or 2");
     if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
         return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
     if (o->start != 0 && o->start != 1 && o->start != 3) return fail(IBIM_ERR_ARG, "start must be 0, 1 or 3");
@@ -620,7 +635,8 @@ ibim_status ibim_solve_extrapolated(ibim_ctx* c, const ibim_phys* phys, const ib
 {
     if (c == nullptr || o == nullptr || d_p == nullptr || info == nullptr) return fail(IBIM_ERR_ARG, "NULL argument");
     IBIM_TRY(check_phys(phys));
-    if (o->precision != IBIM_F64 && o->precision != IBIM_F32C && o->precision != IBIM_F32T) return fail(IBIM_ERR_ARG, "bad precision");
+    if (!valid_precision(o->precision)) return fail(IBIM_ERR_ARG, "bad precision");
+    if (o->certify < 0 || o->certify > 2) return fail(IBIM_ERR_ARG, "certify must be 0, 1 or 2");
     if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128)
         return fail(IBIM_ERR_ARG, "need tol > 0, maxit >= 1, 1 <= restart <= 128");
     if (o->start != 0 && o->start != 1 && o->start != 3) return fail(IBIM_ERR_ARG, "start must be 0, 1 or 3");

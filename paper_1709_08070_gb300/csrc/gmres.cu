@@ -465,7 +465,9 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
     const int64_t len = w->len, N = c->N;
     const PairConsts k = make_consts(p);
     const int prec_in = o.precision;
-    const int prec_out = o.certify ? IBIM_F64 : o.precision;
+    // certification operator: 1 = float-float pair sums (FP64-accurate on the
+    // FP32 pipe), 2 = plain FP64 pair sums
+    const int prec_out = o.certify == 2 ? IBIM_F64 : (o.certify ? IBIM_FF : o.precision);
 
     // Work on the solver's own stream (graph capture needs a non-legacy
     // stream), ordered after everything already queued on the caller's.
@@ -520,7 +522,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         converged = true;
     }
     // Restart residuals use the iteration's operator; with certification the
-    // residual is recomputed with the FP64 operator once the iteration's
+    // residual is recomputed with the FP64-accurate operator once the iteration's
     // residual meets the inner target (or the iteration budget is spent), and
     // a failed check restarts from that FP64 residual (iterative refinement).
     bool check = false;
@@ -549,7 +551,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         iters += steps;
         ++cycles;
         info->matvecs_f32 += (prec_in == IBIM_F32C || prec_in == IBIM_F32T) ? steps : 0;
-        info->matvecs_f64 += (prec_in == IBIM_F64) ? steps : 0;
+        info->matvecs_f64 += (prec_in == IBIM_F64 || prec_in == IBIM_FF) ? steps : 0;
         if (steps > 0) {
             trisolve_kernel<<<1, 1, 0, c->stream>>>(w->st);
             xupdate_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->x, w->V, len, w->st);

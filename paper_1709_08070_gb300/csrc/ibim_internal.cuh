@@ -146,6 +146,8 @@ struct ibim_ctx {
     size_t aux_bytes = 0;
     double* d_yrev = nullptr;  // reverse sums of the symmetric FP32 kernel (2 x padded N) + segment counter
     size_t yrev_bytes = 0;
+    float2* d_fftab = nullptr;   // float-float table of 2^(i/256) (IBIM_FF), made on first use
+    double ff_grid_scale = 0.0;  // 2^q: grid of the hi parts of float-float coordinates
     ibim::GmresWork* gm = nullptr;
     ibim::TreeCode* tc = nullptr;  // treecode tree, lists and proxy buffers (ibim_treecode_setup)
     ibim::Timing timing;
@@ -218,6 +220,15 @@ ibim_status tc_apply(ibim_ctx* c, const PairConsts& k, VecRef in, OutRef out, co
 void tc_destroy(TreeCode* t);
 ibim_status fixup_launch(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, int ttile, VecRef in,
                          OutRef out, const int* d_skip);
+// float-float path (pair_ff.cu)
+PairSchedule ff_schedule(ibim_ctx* c);
+size_t ff_part_doubles(ibim_ctx* c);
+size_t ff_src_bytes(int64_t N);
+ibim_status ff_pack(ibim_ctx* c, VecRef in, const int* d_skip);
+ibim_status ff_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, const int* d_skip);
+ibim_status ff_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, VecRef in, OutRef out,
+                     const int* d_skip);
+ibim_status ff_prepare_context(ibim_ctx* c);
 // FP64 path pieces (pair_f64.cu)
 ibim_status f64_pack(ibim_ctx* c, VecRef in, const int* d_skip);
 ibim_status f64_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, const int* d_skip);

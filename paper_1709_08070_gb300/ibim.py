@@ -21,10 +21,11 @@ __all__ = [
     "ibim_matvec_noalloc", "IBIM_NOALLOC_MAX_NODES", "ibim_autotune", "ibim_set_f32_variant", "ibim_f32_variants",
     "IBIM_F64", "IBIM_F32C", "Context", "KCAL_PER_E2_A", "WarmStartNet", "IBIM_WS_NPARAMS",
     "ibim_get_curvature", "ibim_set_jacobian", "ibim_get_jacobian", "ibim_solve_extrapolated",
-    "IBIM_F32T", "ibim_treecode_setup", "ibim_treecode_info", "ibim_treecode_plan",
+    "IBIM_F32T", "IBIM_FF", "ibim_treecode_setup", "ibim_treecode_info", "ibim_treecode_plan",
 ]
 
 IBIM_F64 = 64
+IBIM_FF = 65
 IBIM_F32C = 32
 IBIM_F32T = 33
 IBIM_NOALLOC_MAX_NODES = 131072

@@ -75,8 +75,8 @@ def test_cavity_shell_matches_oracle():
 def _rows_every_variant(ctx, bo, inv, rows, h, seed, variants, with_f64=True):
     """Oracle rows `rows` (oracle numbering) of the operator on the shared node
     set against the library's, element by element per output block, for the
-    FP64 path (1e-10) and each FP32 variant in `variants` at its occupancy-limited
-    grid (1e-5)."""
+    FP64 path and the float-float path (1e-10) and each FP32 variant in
+    `variants` at its occupancy-limited grid (1e-5)."""
     N = ctx.N
     P = ibim.Phys(1.0, 80.0, 0.1257, h, 0)
     Po = oracle.Phys(1.0, 80.0, 0.1257, h, 0)
@@ -87,7 +87,8 @@ def _rows_every_variant(ctx, bo, inv, rows, h, seed, variants, with_f64=True):
     y1o, y2o = oracle.matvec_rows(bo["xs"], bo["nrm"], bo["w"], Po, p_orc, rows)
     din = torch.from_numpy(p_gpu).cuda()
     dout = torch.empty_like(din)
-    configs = ([(ibim.IBIM_F64, None, 1e-10)] if with_f64 else []) + [(ibim.IBIM_F32C, v, 1e-5) for v in variants]
+    configs = ([(ibim.IBIM_F64, None, 1e-10)] if with_f64 else []) + [(ibim.IBIM_FF, None, 1e-10)] + \
+        [(ibim.IBIM_F32C, v, 1e-5) for v in variants]
     for prec, v, tol in configs:
         if v is not None:
             ctx.set_f32_variant(v, 0)
@@ -122,8 +123,9 @@ def test_ten_thousand_atom_globule_operator_rows():
     """A 10,000-atom globule of the learned-start evaluation size (about 740k
     nodes): geometry parity with the oracle's level set, then 1,024 seeded
     oracle rows of the FP32 operator (the autotuner's choice and both
-    symmetric variants), element by element (1e-5).  The FP64 operator is
-    left out at this size (about a minute per application)."""
+    symmetric variants; 1e-5) and of the float-float operator (1e-10), element
+    by element.  The plain FP64 operator is left out at this size (about a
+    minute per application)."""
     z, r, q = inputs.globule_atoms(10000, seed=inputs.SEED_LEARNED + 10000)
     h = 0.5
     ctx, bo, bg, jg, jo = _compare(z, r, 1.4, h, 2 * h)
