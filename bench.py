@@ -48,6 +48,13 @@ F32_OPS_PER_INTERACTION = 36
 # products, rho^-3, theta terms, hi, qf) is 28 lane-operations and each
 # direction's two sums 10 more, 48 for two interactions.
 F32_OPS_PER_INTERACTION_SYM = 24
+# The float-float operator (IBIM_FF, pair_ff_kernel), counted from ff_pair's
+# far branch: r 6, |r|^2 31, s_x, s_y and n.m 31 each, 1/rho 11, rho, kappa rho
+# and the exponent argument 4 each, exp 25, E x 4, 1 - E 4, g 11, 1 - th A
+# 15 twice, 3 - B 18, rho^-2 and rho^-3 8, the y1 term 31, the y2 term 54 and
+# the two float-float accumulations 22 FP32-pipe operations per interaction
+# (plus one MUFU, about six integer operations and five shared loads).
+FF_OPS_PER_INTERACTION = 366
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this
 # workload, by variant (targets/thread, min CTAs/SM, threads/CTA, symmetric), from the ncu
@@ -381,11 +388,37 @@ def run_ours(args):
         e2e = {"value": e2e_inter / (sum(e2e_ms) * 1e-3), "unit": "interactions/s",
                "h2d_bytes_per_step": int(zp.numel() * 8 + qp.numel() * 8),
                "d2h_bytes_per_step": int(hp.numel() * 8 + 8)}
-        # ---- time to 1e-6 residual: certified FP32 path vs plain FP64 GPU solve
+        # ---- time to 1e-6 residual: certified FP32 path vs plain FP64 GPU solve.
+        # certify=1 checks the residual with the float-float operator (FP64
+        # accuracy on the FP32 pipe), certify=2 with the plain FP64 operator.
+        ctx.solve(P, dp, **dict(opts, certify=1))  # first use builds the float-float table
         t0 = time.perf_counter()
         icert = ctx.solve(P, dp, **dict(opts, certify=1))
         torch.cuda.synchronize()
         cert_ms = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        icert2 = ctx.solve(P, dp, **dict(opts, certify=2))
+        torch.cuda.synchronize()
+        cert2_ms = (time.perf_counter() - t0) * 1e3
+        # the two FP64-accurate operators alone (CUDA events around the pair launches)
+        xa = torch.from_numpy(inputs_random(2 * N)).cuda()
+        ya = torch.empty_like(xa)
+        acc = {}
+        for name, prec, reps in (("ff", ibim.IBIM_FF, 3), ("f64", ibim.IBIM_F64, 1)):
+            ctx.matvec(P, xa, ya, precision=prec)
+            ctx.timing_enable(True)
+            ctx.timing_reset()
+            for _ in range(reps):
+                ctx.matvec(P, xa, ya, precision=prec)
+            torch.cuda.synchronize()
+            tk = ctx.timing()
+            ctx.timing_enable(False)
+            acc[name] = tk["pair_ms"] / max(1, tk["pair_launches"])
+        ff_ops = FF_OPS_PER_INTERACTION * N * N / (acc["ff"] * 1e-3)
+        certifier = {"kernel": "pair_ff_kernel", "precision": "float-float (IBIM_FF)", "avg_launch_ms": acc["ff"],
+                     "interactions_per_s": N * N / (acc["ff"] * 1e-3), "ops_per_interaction": FF_OPS_PER_INTERACTION,
+                     "achieved": ff_ops / 1e12, "frac": ff_ops / peak_ops, "unit": "Tops/s",
+                     "f64_kernel_ms": acc["f64"], "speedup_vs_f64_kernel": acc["f64"] / acc["ff"]}
         fp64 = None
         if not args.skip_fp64:
             t0 = time.perf_counter()
@@ -398,14 +431,18 @@ def run_ours(args):
         extra = {"time_to_residual": {
             "tol": W["tol"], "f32_step_ms": total_ms / args.steps, "f32_iters": infos[-1]["iters"],
             "f32_certified_ms": cert_ms, "f32_certified_relres_f64": icert["relres"],
-            "f32_certified_iters": icert["iters"], "f64_plain": fp64,
+            "f32_certified_iters": icert["iters"], "f32_certified_check": "float-float operator (certify=1)",
+            "f32_certified_f64check_ms": cert2_ms, "f32_certified_f64check_relres": icert2["relres"],
+            "f64_plain": fp64,
             "speedup_certified_vs_f64": (fp64["ms"] / cert_ms) if fp64 else None,
+            "speedup_certified_f64check_vs_f64": (fp64["ms"] / cert2_ms) if fp64 else None,
             "speedup_uncertified_vs_f64": (fp64["ms"] / (total_ms / args.steps)) if fp64 else None},
             "energy": {"gpol_kcal_f32": infos[-1]["gpol_kcal"], "gpol_kcal_f64": fp64["gpol_kcal"] if fp64 else None,
                        "kirkwood_series_kcal": Gs,
                        "rel_err_f32_vs_f64": abs(infos[-1]["gpol_kcal"] - fp64["gpol_kcal"]) / abs(fp64["gpol_kcal"])
                        if fp64 else None,
-                       "rel_err_vs_series": abs(infos[-1]["gpol_kcal"] - Gs) / abs(Gs)}}
+                       "rel_err_vs_series": abs(infos[-1]["gpol_kcal"] - Gs) / abs(Gs)},
+            "certifying_operator": certifier}
         # accuracy path: full Jacobian + tube extrapolation (two certified FP32 solves)
         ctx.set_jacobian(1)
         t0 = time.perf_counter()
@@ -902,7 +939,7 @@ def run_profile(args):
         variant, bps = args.variant, args.ctas_per_sm
     else:
         variant, bps, _ = ctx.autotune(P)
-    prec = ibim.IBIM_F32C
+    prec = {"f32c": ibim.IBIM_F32C, "ff": ibim.IBIM_FF, "f64": ibim.IBIM_F64}[args.prec]
     if args.treecode_theta > 0:
         ctx.treecode_setup(args.treecode_theta, W["tau_k"] * h, args.treecode_interp)
         prec = ibim.IBIM_F32T
@@ -918,7 +955,7 @@ def run_profile(args):
     torch.cuda.synchronize()
     tim = ctx.timing()
     ctx.close()
-    print(json.dumps({"mode": "profile", "N": N, "variant": variant, "ctas_per_sm": bps,
+    print(json.dumps({"mode": "profile", "N": N, "variant": variant, "ctas_per_sm": bps, "prec": args.prec,
                       "treecode_theta": args.treecode_theta,
                       "pair_ms": tim["pair_ms"] / max(1, tim["pair_launches"])}), flush=True)
 
@@ -938,6 +975,8 @@ def main():
                     help="operator applications only (for profiler captures); prints no bench line")
     ap.add_argument("--variant", type=int, default=None, help="with --profile: FP32 kernel variant (no autotune)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
+    ap.add_argument("--prec", default="f32c", choices=["f32c", "ff", "f64"],
+                    help="with --profile: operator precision (FP32 compensated, float-float or FP64)")
     ap.add_argument("--treecode-theta", type=float, default=0.0,
                     help="with --profile: apply the treecode operator (IBIM_F32T) with this theta instead")
     ap.add_argument("--treecode-interp", type=int, default=0, choices=[0, 1],
