@@ -367,7 +367,10 @@ ibim_status ibim_treecode_plan(const double* xyz, int64_t N, double theta, doubl
  * pair evaluated once for both ordered pairs; its reverse sums are added with
  * FP32 shared-memory and FP64 global atomics in a varying order, so its
  * result varies from run to run at the FP32 rounding level of one tile's
- * partial sum, a few 1e-10 of max |y|);
+ * partial sum, a few 1e-10 of max |y|).  symmetric: 0 = one-directional,
+ * 1 = symmetric with the reverse sums of each source pair reduced across the
+ * warp, 2 = symmetric with the reverse sums carried from lane to lane as the
+ * source pairs rotate through each half-warp;
  * ibim_f32_variant_info describes entry v of [0, ibim_f32_variant_count())
  * (outputs may be NULL).
  */

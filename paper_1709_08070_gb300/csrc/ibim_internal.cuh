@@ -203,7 +203,7 @@ void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric);
 size_t f32_part_doubles(ibim_ctx* c);  // partial-sum doubles of the current variant and grid
 // symmetric FP32 pair kernel (pair_sym.cu)
 int sym_variant_count();
-void sym_variant_info(int v, int* tpt, int* minb, int* threads);
+void sym_variant_info(int v, int* tpt, int* minb, int* threads, int* scheme);
 int sym_occupancy(int v);
 size_t sym_part_doubles(int64_t N, int ttile, int grid_cap);
 size_t sym_yrev_bytes(int64_t N);

@@ -306,8 +306,7 @@ static bool is_sym(int v) { return v >= kNumVariants; }
 void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric)
 {
     if (is_sym(v)) {
-        sym_variant_info(v - kNumVariants, tpt, minb, threads);
-        *symmetric = 1;
+        sym_variant_info(v - kNumVariants, tpt, minb, threads, symmetric);
         return;
     }
     *tpt = kVariants[v].tpt;

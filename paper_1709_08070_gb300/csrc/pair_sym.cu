@@ -30,11 +30,27 @@
 // reverse partial (a few 1e-10 of max |y| measured), well inside the FP32
 // operator's own error against FP64.
 //
-// Source payload (by node pairs, 64 bytes a pair, placeholders past N):
-//   [0] = (-y0.x, -y1.x, -y0.y, -y1.y)   minus the position in its chunk frame
-//   [1] = (-y0.z, -y1.z,  b0,    b1  )   b = w psin
-//   [2] = (m0.x, m1.x, m0.y, m1.y)       unit normals
-//   [3] = (m0.z, m1.z, a0, a1)            a = w psi
+// Source payload (by node pairs, 64 bytes a pair, placeholders past N), four
+// float4 components per pair:
+//   A = (-y0.x, -y1.x, -y0.y, -y1.y)   minus the position in its chunk frame
+//   B = (-y0.z, -y1.z,  b0,    b1  )   b = w psin
+//   C = (m0.x, m1.x, m0.y, m1.y)       unit normals
+//   D = (m0.z, m1.z, a0, a1)            a = w psi
+// stored per 32-node chunk component by component (the 16 A's of the chunk,
+// then its 16 B's, C's and D's), so that 16 lanes reading 16 different pairs
+// of one chunk touch 256 contiguous bytes.
+//
+// Two schemes for the reverse sums (a variant parameter):
+//   * warp reduction: per payload pair, the warp's reverse contributions are
+//     summed by a transposed 4-value butterfly (warp_sum4_add) and added to
+//     the stage's shared reverse buffer by four lanes;
+//   * rotation (far chunks): each half-warp walks the chunk's 16 payload pairs
+//     in a staggered order, lane l taking pair (l + k) mod 16 at step k, and
+//     the reverse accumulators of a pair move with it from lane to lane (one
+//     shuffle per value and step, the adds folded into the pair formula's
+//     FMAs); after 16 steps each lane holds one pair's sums over its
+//     half-warp, the two halves are added and 16 + 16 lanes add them to the
+//     shared buffer.  Near chunks use the warp reduction in both schemes.
 #include <algorithm>
 
 #include "pair_f32_core.cuh"
@@ -108,13 +124,19 @@ __host__ __device__ __forceinline__ void sym_row_start(const SymSchedule& s, int
     }
 }
 
-__device__ __forceinline__ void write_source_pair_sym(float4* __restrict__ dst, float4 y0, float4 y1, float4 m0,
-                                                      float4 m1, float a0, float a1, float b0, float b1)
+// Float4 offset of component `comp` (0..3 = A..D) of payload pair `pr`.
+__host__ __device__ __forceinline__ int64_t sym_pair_offset(int64_t pr, int comp)
 {
-    dst[0] = make_float4(-y0.x, -y1.x, -y0.y, -y1.y);
-    dst[1] = make_float4(-y0.z, -y1.z, b0, b1);
-    dst[2] = make_float4(m0.x, m1.x, m0.y, m1.y);
-    dst[3] = make_float4(m0.z, m1.z, a0, a1);
+    return (pr / kPairsPerChunk) * (kPairsPerChunk * kPairF4) + comp * kPairsPerChunk + (pr % kPairsPerChunk);
+}
+
+__device__ __forceinline__ void write_source_pair_sym(float4* __restrict__ src, int64_t pr, float4 y0, float4 y1,
+                                                      float4 m0, float4 m1, float a0, float a1, float b0, float b1)
+{
+    src[sym_pair_offset(pr, 0)] = make_float4(-y0.x, -y1.x, -y0.y, -y1.y);
+    src[sym_pair_offset(pr, 1)] = make_float4(-y0.z, -y1.z, b0, b1);
+    src[sym_pair_offset(pr, 2)] = make_float4(m0.x, m1.x, m0.y, m1.y);
+    src[sym_pair_offset(pr, 3)] = make_float4(m0.z, m1.z, a0, a1);
 }
 
 // Per-thread targets with their own weights (the reverse direction's sources).
@@ -180,6 +202,60 @@ __device__ __forceinline__ void pair_far_sym(float2 Xx, float2 Xy, float2 Xz, fl
     nr1 = __ffma2_rn(P, __fmul2_rn(u1, psa), __fmul2_rn(qf, nbi));
     const float2 nv = __ffma2_rn(hi, psa, __fmul2_rn(u2, nbi));
     r2 = __fmul2_rn(P, __ffma2_rn(sy, nv, __fmul2_rn(g, __fmul2_rn(ai, cc))));
+}
+
+// pair_far_sym with the reverse sums accumulated into (nR1, R2) inside its
+// final FMAs (rotation scheme): nR1 -= first reverse sum, R2 += second.
+__device__ __forceinline__ void pair_far_sym_acc(float2 Xx, float2 Xy, float2 Xz, float2 nx, float2 ny, float2 nz,
+                                                 float2 ai, float2 nbi, const float4& A, const float4& B,
+                                                 const float4& C, const float4& D, const FarConsts& c, float2& t1,
+                                                 float2& t2, float2& nR1, float2& R2)
+{
+    const float2 rx = __fadd2_rn(Xx, make_float2(A.x, A.y));
+    const float2 ry = __fadd2_rn(Xy, make_float2(A.z, A.w));
+    const float2 rz = __fadd2_rn(Xz, make_float2(B.x, B.y));
+    const float2 bj = make_float2(B.z, B.w);
+    const float2 mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w), mz = make_float2(D.x, D.y);
+    const float2 aj = make_float2(D.z, D.w);
+    float2 rr = __fmul2_rn(rx, rx);
+    rr = __ffma2_rn(ry, ry, rr);
+    rr = __ffma2_rn(rz, rz, rr);
+    float2 sx = __fmul2_rn(rx, nx);
+    sx = __ffma2_rn(ry, ny, sx);
+    sx = __ffma2_rn(rz, nz, sx);
+    float2 sy = __fmul2_rn(rx, mx);
+    sy = __ffma2_rn(ry, my, sy);
+    sy = __ffma2_rn(rz, mz, sy);
+    float2 cc = __fmul2_rn(nx, mx);
+    cc = __ffma2_rn(ny, my, cc);
+    cc = __ffma2_rn(nz, mz, cc);
+    const float2 inv = make_float2(ptx::rsqrt_approx(rr.x), ptx::rsqrt_approx(rr.y));
+    const float2 rho = __fmul2_rn(rr, inv);
+    const float2 ea = __fmul2_rn(rho, c.kl2e);
+    const float2 xn = __fmul2_rn(rho, c.nkappa);
+    const float2 E = make_float2(ptx::ex2_approx(ea.x), ptx::ex2_approx(ea.y));
+    const float2 En = __fmul2_rn(E, xn);
+    const float2 fn = __fadd2_rn(E, c.neg1);
+    const float2 g = __ffma2_rn(fn, c.neg1, En);
+    const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));
+    const float2 inv2 = make_float2(ptx::rcp_approx(rr.x), ptx::rcp_approx(rr.y));
+    const float2 P = __fmul2_rn(inv2, inv);
+    const float2 u1 = __ffma2_rn(c.th1, g, c.omth1);
+    const float2 u2 = __ffma2_rn(c.th2, g, c.omth2);
+    const float2 hi = __fmul2_rn(hn, inv2);
+    const float2 qf = __fmul2_rn(fn, inv);
+    // forward
+    const float2 sa = __fmul2_rn(aj, sy);
+    const float2 ca = __fmul2_rn(aj, cc);
+    t1 = __ffma2_rn(P, __fmul2_rn(u1, sa), t1);
+    t1 = __ffma2_rn(qf, bj, t1);
+    const float2 v = __ffma2_rn(hi, sa, __fmul2_rn(u2, bj));
+    t2 = __ffma2_rn(P, __ffma2_rn(sx, v, __fmul2_rn(g, ca)), t2);
+    // reverse, accumulated
+    const float2 psa = __fmul2_rn(ai, sx);
+    nR1 = __ffma2_rn(P, __fmul2_rn(u1, psa), __ffma2_rn(qf, nbi, nR1));
+    const float2 nv = __ffma2_rn(hi, psa, __fmul2_rn(u2, nbi));
+    R2 = __ffma2_rn(P, __ffma2_rn(sy, nv, __fmul2_rn(g, __fmul2_rn(ai, cc))), R2);
 }
 
 // One ordered near pair (target <- source), scalar: tube test on the target's
@@ -282,11 +358,13 @@ __device__ __forceinline__ void near_pair_sym(const float3 (&X)[TPT], const SymT
 }
 
 // Shared reverse-sum layout of one stage: the first-block sums at [0, STILE),
-// the second-block sums from kRevOff, two words past a 128-byte multiple so
-// that the four addresses of one warp_sum4_add (2p, 2p + 1 of each block) fall
-// in four different banks.
-constexpr int kRevOff = kF32STile + 2;
-constexpr int kRevRow = kRevOff + kF32STile;
+// the second-block sums from rev_off: two words past a 128-byte multiple in
+// the warp-reduction scheme, so that the four addresses of one warp_sum4_add
+// (2p, 2p + 1 of each block) fall in four different banks; one word past it
+// in the rotation scheme, so that the 16 + 16 lanes adding the first and the
+// second sums of 16 pairs use the even and the odd banks.
+__host__ __device__ constexpr int sym_rev_off(bool rot) { return kF32STile + (rot ? 1 : 2); }
+__host__ __device__ constexpr int sym_rev_row(bool rot) { return sym_rev_off(rot) + kF32STile; }
 
 // Sums of four per-lane values over the warp's 32 lanes, added to four
 // shared-memory addresses: the values are exchanged half by half (lane^16,
@@ -313,14 +391,15 @@ __device__ __forceinline__ void warp_sum4_add(float v0, float v1, float v2, floa
 // Ablk[q]: chunk index of target slot q's block; B0: chunk index of the
 // tile's first chunk.  Forward sums go to the compensated pairs (S, C);
 // reverse sums of every source of the tile go to racc[.] (first block) and
-// racc[kRevOff + .] (second block) by shared-memory atomics.
-template <int TPT>
+// racc[sym_rev_off(ROT) + .] (second block) by shared-memory atomics.
+template <int TPT, bool ROT>
 __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const float4* tfrm, const float4* sb,
                                               const float4* sfrm, const F32Consts& k, float (&S1)[TPT],
                                               float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
                                               const Geo64& g64, int64_t gi0, int qstride, int64_t j0, int64_t N,
                                               const int (&Ablk)[TPT], int64_t B0, float* racc)
 {
+    constexpr int P = kPairsPerChunk;
     const FarConsts fc = far_consts(k);
     const int lane = threadIdx.x & 31;
 #pragma unroll 1
@@ -356,9 +435,9 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
         float2 t1[TPT], t2[TPT];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) t1[q] = t2[q] = make_float2(0.0f, 0.0f);
-        const float4* cb = sb + c * kPairsPerChunk * kPairF4;
+        const float4* cb = sb + c * P * kPairF4;
         float* ra = racc + c * kChunk;
-        float* rb = racc + kRevOff + c * kChunk;
+        float* rb = racc + sym_rev_off(ROT) + c * kChunk;
         if (far) {
             float2 Xx[TPT], Xy[TPT], Xz[TPT];
 #pragma unroll
@@ -367,29 +446,70 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                 Xy[q] = f2(X[q].y);
                 Xz[q] = f2(X[q].z);
             }
-#pragma unroll 8
-            for (int p = 0; p < kPairsPerChunk; ++p) {
-                const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
-                const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
-                float2 s1 = make_float2(0.0f, 0.0f), s2 = make_float2(0.0f, 0.0f);
+            if (ROT) {
+                // slots whose reverse direction does not count here add zeros
+                float2 aq[TPT], nbq[TPT];
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) {
-                    float2 r1, r2;
-                    pair_far_sym(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], T.a[q], T.nb[q], A, B, C, D, fc,
-                                 t1[q], t2[q], r1, r2);
-                    if (rev[q]) {
-                        s1 = __fadd2_rn(s1, r1);
-                        s2 = __fadd2_rn(s2, r2);
+                    aq[q] = rev[q] ? T.a[q] : f2(0.0f);
+                    nbq[q] = rev[q] ? T.nb[q] : f2(0.0f);
+                }
+                const int hl = lane & (P - 1);
+                const int nxt = (hl + 1) & (P - 1);
+                float2 nR1 = make_float2(0.0f, 0.0f), R2 = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+                for (int step = 0; step < P; ++step) {
+                    const int p = (hl + step) & (P - 1);
+                    const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q)
+                        pair_far_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B, C, D,
+                                         fc, t1[q], t2[q], nR1, R2);
+                    // pair p goes to lane hl - 1 at the next step: its sums follow it
+                    nR1.x = __shfl_sync(0xffffffffu, nR1.x, nxt, P);
+                    nR1.y = __shfl_sync(0xffffffffu, nR1.y, nxt, P);
+                    R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
+                    R2.y = __shfl_sync(0xffffffffu, R2.y, nxt, P);
+                }
+                // lane hl holds pair hl's sums over its half-warp; add the other half's
+                nR1.x += __shfl_xor_sync(0xffffffffu, nR1.x, P);
+                nR1.y += __shfl_xor_sync(0xffffffffu, nR1.y, P);
+                R2.x += __shfl_xor_sync(0xffffffffu, R2.x, P);
+                R2.y += __shfl_xor_sync(0xffffffffu, R2.y, P);
+                if (anyrev) {
+                    if (lane < P) {
+                        atomicAdd(ra + 2 * hl, -nR1.x);
+                        atomicAdd(ra + 2 * hl + 1, -nR1.y);
+                    } else {
+                        atomicAdd(rb + 2 * hl, R2.x);
+                        atomicAdd(rb + 2 * hl + 1, R2.y);
                     }
                 }
-                if (anyrev)
-                    warp_sum4_add(s1.x, s1.y, s2.x, s2.y, lane, ra + 2 * p, ra + 2 * p + 1, rb + 2 * p,
-                                  rb + 2 * p + 1);
+            } else {
+#pragma unroll 8
+                for (int p = 0; p < P; ++p) {
+                    const float4 A = cb[p], B = cb[P + p];
+                    const float4 C = cb[2 * P + p], D = cb[3 * P + p];
+                    float2 s1 = make_float2(0.0f, 0.0f), s2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) {
+                        float2 r1, r2;
+                        pair_far_sym(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], T.a[q], T.nb[q], A, B, C, D,
+                                     fc, t1[q], t2[q], r1, r2);
+                        if (rev[q]) {
+                            s1 = __fadd2_rn(s1, r1);
+                            s2 = __fadd2_rn(s2, r2);
+                        }
+                    }
+                    if (anyrev)
+                        warp_sum4_add(s1.x, s1.y, s2.x, s2.y, lane, ra + 2 * p, ra + 2 * p + 1, rb + 2 * p,
+                                      rb + 2 * p + 1);
+                }
             }
         } else {
-            for (int p = 0; p < kPairsPerChunk; ++p) {
-                const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
-                const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
+            for (int p = 0; p < P; ++p) {
+                const float4 A = cb[p], B = cb[P + p];
+                const float4 C = cb[2 * P + p], D = cb[3 * P + p];
                 float2 r1[TPT], r2[TPT];
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) r1[q] = r2[q] = make_float2(0.0f, 0.0f);
@@ -417,7 +537,7 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
     }
 }
 
-template <int TPT, int MINB, int THREADS>
+template <int TPT, int MINB, int THREADS, bool ROT>
 __global__ void __launch_bounds__(THREADS, MINB)
     pair_sym_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm,
                     const float4* __restrict__ src, const float4* __restrict__ frames, int64_t N, int64_t n_pad,
@@ -431,7 +551,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
     __shared__ __align__(128) SourceStage stg[kF32Stages];
     __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
     __shared__ __align__(8) StagePipe pipe;
-    __shared__ float racc[kF32Stages][kRevRow];
+    constexpr int REVOFF = sym_rev_off(ROT);
+    __shared__ float racc[kF32Stages][sym_rev_row(ROT)];
     __shared__ int64_t stage_st[kF32Stages];
 
     __shared__ int64_t seg_next[2];
@@ -442,7 +563,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const int lane = tid & 31;
     unsigned long long* seg_ctr = reinterpret_cast<unsigned long long*>(yrev + 2 * n_pad);
 
-    for (int q = tid; q < kF32Stages * kRevRow; q += THREADS) (&racc[0][0])[q] = 0.0f;
+    for (int q = tid; q < kF32Stages * sym_rev_row(ROT); q += THREADS) (&racc[0][0])[q] = 0.0f;
     if (tid == 0) {
         pipe_init(pipe, NW);
         abort_sh = 0;
@@ -481,8 +602,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
             T.nx[q] = f2(b.x);
             T.ny[q] = f2(b.y);
             T.nz[q] = f2(b.z);
-            const float4 pb = src[kPairF4 * (i >> 1) + 1];
-            const float4 pa = src[kPairF4 * (i >> 1) + 3];
+            const float4 pb = src[sym_pair_offset(i >> 1, 1)];
+            const float4 pa = src[sym_pair_offset(i >> 1, 3)];
             const float ai = (i & 1) ? pa.w : pa.z;
             const float bi = (i & 1) ? pb.w : pb.z;
             T.a[q] = f2(ai);
@@ -504,11 +625,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
         const int sv = (int)((v + off) % kF32Stages);
         const int64_t j0 = stage_st[sv] * kF32STile;
         for (int jj = lane; jj < kF32STile; jj += 32) {
-            const float v1 = racc[sv][jj], v2 = racc[sv][kRevOff + jj];
+            const float v1 = racc[sv][jj], v2 = racc[sv][REVOFF + jj];
             if (v1 != 0.0f) atomicAdd(yrev + j0 + jj, (double)v1);
             if (v2 != 0.0f) atomicAdd(yrev + n_pad + j0 + jj, (double)v2);
             racc[sv][jj] = 0.0f;
-            racc[sv][kRevOff + jj] = 0.0f;
+            racc[sv][REVOFF + jj] = 0.0f;
         }
         __syncwarp();
     };
@@ -559,7 +680,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
             for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
             if (!idle)
-                tile_sums_sym<TPT>(T, &tfrm[warp][0], stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64, gi0,
+                tile_sums_sym<TPT, ROT>(T, &tfrm[warp][0], stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64, gi0,
                                    THREADS, st * kF32STile, N, Ablk, st * kChunksPerTile, &racc[stage][0]);
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -643,7 +764,7 @@ __global__ void pack_sym_kernel(const float4* __restrict__ pos, const float4* __
         yrev[n_pad + j] = 0.0;
     }
     if (pr == 0) *reinterpret_cast<unsigned long long*>(yrev + 2 * n_pad) = 0ull;  // small-segment counter
-    write_source_pair_sym(src + kPairF4 * pr, y[0], y[1], m[0], m[1], a[0], a[1], b[0], b[1]);
+    write_source_pair_sym(src, pr, y[0], y[1], m[0], m[1], a[0], a[1], b[0], b[1]);
 }
 
 // y = Lambda p + (1/(4 pi)) (forward partials of the row + reverse sums).
@@ -684,23 +805,50 @@ __global__ void fixup_sym_kernel(const double* __restrict__ part, SymSchedule s,
 
 // ------------------------------------------------------------------ host side
 
-struct SymVariant {
-    int tpt, minb, threads;
-    const void* fn;
+struct SymArgs {
+    const float4* tpos;
+    const float4* tnrm;
+    const float4* src;
+    const float4* frames;
+    int64_t N, n_pad;
+    SymSchedule s;
+    F32Consts k;
+    double* part;
+    double* yrev;
+    unsigned* err;
+    const int* skip;
+    Geo64 g64;
 };
-#define IBIM_SYM_VARIANT(T, M, W) {T, M, W, (const void*)pair_sym_kernel<T, M, W>}
+
+template <int TPT, int MINB, int THREADS, bool ROT>
+static void launch_sym(const SymArgs& a, cudaStream_t st)
+{
+    pair_sym_kernel<TPT, MINB, THREADS, ROT><<<a.s.grid, THREADS, 0, st>>>(
+        a.tpos, a.tnrm, a.src, a.frames, a.N, a.n_pad, a.s, a.k, a.part, a.yrev, a.err, a.skip, a.g64);
+}
+
+// scheme: 1 = warp reduction of the reverse sums, 2 = rotation (see the file comment)
+struct SymVariant {
+    int tpt, minb, threads, scheme;
+    const void* fn;
+    void (*launch)(const SymArgs&, cudaStream_t);
+};
+#define IBIM_SYM_VARIANT(T, M, W, R) \
+    {T, M, W, (R) ? 2 : 1, (const void*)pair_sym_kernel<T, M, W, R>, launch_sym<T, M, W, R>}
 static const SymVariant kSymVariants[] = {
-    IBIM_SYM_VARIANT(2, 1, 512), IBIM_SYM_VARIANT(1, 1, 512),
+    IBIM_SYM_VARIANT(2, 1, 512, false), IBIM_SYM_VARIANT(1, 1, 512, false),
+    IBIM_SYM_VARIANT(2, 1, 512, true), IBIM_SYM_VARIANT(1, 1, 512, true),
 };
 #undef IBIM_SYM_VARIANT
 constexpr int kNumSymVariants = (int)(sizeof(kSymVariants) / sizeof(kSymVariants[0]));
 
 int sym_variant_count() { return kNumSymVariants; }
-void sym_variant_info(int v, int* tpt, int* minb, int* threads)
+void sym_variant_info(int v, int* tpt, int* minb, int* threads, int* scheme)
 {
     *tpt = kSymVariants[v].tpt;
     *minb = kSymVariants[v].minb;
     *threads = kSymVariants[v].threads;
+    *scheme = kSymVariants[v].scheme;
 }
 int sym_occupancy(int v)
 {
@@ -763,19 +911,9 @@ ibim_status sym_pairs(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, co
     const int64_t n_pad = padded_nodes(c->N);
     const F32Consts kk = f32_consts(k);
     const Geo64 g64{c->d_geo64, c->d_geo64 + 3 * c->N, 1, c->N};
-    const float4* srcp = (const float4*)c->d_src;
-    switch (sv) {
-    case 1:
-        pair_sym_kernel<1, 1, 512><<<s.grid, 512, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                 n_pad, s, kk, c->d_part, c->d_yrev, c->d_err, d_skip,
-                                                                 g64);
-        break;
-    default:
-        pair_sym_kernel<2, 1, 512><<<s.grid, 512, 0, c->stream>>>(c->d_pos32, c->d_nrm32, srcp, c->d_frames, c->N,
-                                                                 n_pad, s, kk, c->d_part, c->d_yrev, c->d_err, d_skip,
-                                                                 g64);
-        break;
-    }
+    const SymArgs a{c->d_pos32, c->d_nrm32, (const float4*)c->d_src, c->d_frames, c->N, n_pad, s, kk, c->d_part,
+                    c->d_yrev, c->d_err, d_skip, g64};
+    v.launch(a, c->stream);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
