@@ -234,6 +234,11 @@ typedef struct {
  * least squares on the device and the operator of opts->precision, then
  * evaluate G_pol (Sec. 3.5) and the area (Sec. 3.4).  Each Arnoldi step runs
  * as one CUDA graph replay with no host synchronisation inside the step.
+ * The symmetric FP32 kernels vary from one application to the next by about
+ * 1e-8 of |A p| (their reverse sums are added in a varying order), which is
+ * the floor of a restart residual computed with them; an IBIM_F32C solve with
+ * tol below 1e-7 therefore runs the one-directional FP32 kernel (the
+ * context's variant is restored afterwards).
  * d_p: device 2N doubles; start vector on entry when opts->start == 3,
  * solution [psi; psin] on exit.  Needs charges.  Returns IBIM_ERR_NOT_CONVERGED
  * (info filled) when maxit is reached above tol.
@@ -448,8 +453,9 @@ ibim_status ibim_solve_extrapolated(ibim_ctx* ctx, const ibim_phys* phys, const 
  * molecules' (target tile, source tile) steps, and a round is one CUDA graph
  * replay.  Molecules drop out of the list as they converge.  The first
  * batched solve of a size class (device, floor(log2 sum N_m^2)) in the process
- * times each compiled variant of the batched pair kernel (target tiles of
- * 512, 256 and 128 nodes) on its first round and keeps the fastest.
+ * times each compiled variant of the batched pair kernel (one-directional with
+ * target tiles of 512, 256 and 128 nodes, and symmetric; the symmetric one only
+ * for tol >= 1e-7, see ibim_solve) on its first round and keeps the fastest.
  *   nmol in [1, 1024]; phys: nmol entries (kappa etc. per molecule); opts must
  *   ask for IBIM_F32C and certify 0, with start 0 (zero start) or 3 (each
  *   d_p[m] holds the starting vector, e.g. an ibim_wsnet_predict result);
@@ -460,6 +466,24 @@ ibim_status ibim_solve_extrapolated(ibim_ctx* ctx, const ibim_phys* phys, const 
  */
 ibim_status ibim_solve_batch(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts* opts,
                              double* const* d_p, ibim_solve_info* infos);
+
+/*
+ * Batched pair-kernel variants (tuning, not part of the paper's method):
+ * one-directional kernels with one target per thread in CTAs of 512, 256 or
+ * 128 threads, and a symmetric kernel (each unordered node pair of a molecule
+ * evaluated once for both directions, reverse sums carried by rotating
+ * accumulators as in the single-molecule symmetric kernel).  By default the
+ * first batched solve of a size class times every variant on its first round
+ * and keeps the fastest; ibim_set_batch_variant(v) forces variant v for later
+ * batched solves in the process (-1 restores the measured choice).
+ * ibim_batch_variant_info describes variant v (outputs may be NULL) and
+ * returns in last_used the variant the calling thread's last batched solve
+ * ran (-1 before any).
+ */
+int ibim_batch_variant_count(void);
+ibim_status ibim_batch_variant_info(int v, int* targets_per_thread, int* threads_per_cta, int* symmetric,
+                                    int* last_used);
+ibim_status ibim_set_batch_variant(int v);
 
 /* ----------------------------------------------------------- diagnostics */
 

@@ -25,10 +25,11 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "gmres_internal.cuh"
-#include "pair_f32_core.cuh"
+#include "pair_sym_core.cuh"
 
 namespace ibim {
 
@@ -76,9 +77,17 @@ __device__ __forceinline__ double* batch_out(const BatchMol& M, int mode)
     return mode == 0 ? M.V + (int64_t)(M.st->k + 1) * 2 * M.N : M.t;
 }
 
+// Steps of one molecule: every (target tile, source tile) pair, or with R > 0
+// (symmetric kernel, R = target tile / source tile) the upper triangle: row t
+// holds the source tiles R t .. n_s - 1.
+__host__ __device__ __forceinline__ int64_t batch_mol_steps(int64_t N, int64_t ttile, int64_t n_s, int64_t R)
+{
+    const int64_t n_t = (N + ttile - 1) / ttile;
+    return R > 0 ? n_t * n_s - R * n_t * (n_t - 1) / 2 : n_t * n_s;
+}
+
 __global__ void batch_plan_kernel(const BatchMol* __restrict__ mols, int nmol, int mode, const int* __restrict__ want,
-                                  int64_t ttile,
-                                  int grid, BatchPlan* __restrict__ plan)
+                                  int64_t ttile, int64_t sym_R, int grid, BatchPlan* __restrict__ plan)
 {
     if (threadIdx.x != 0) return;
     int a = 0;
@@ -88,7 +97,7 @@ __global__ void batch_plan_kernel(const BatchMol* __restrict__ mols, int nmol, i
         if (!active) continue;
         plan->mol[a] = m;
         plan->off[a] = total;
-        total += (mols[m].N + ttile - 1) / ttile * mols[m].n_stiles;
+        total += batch_mol_steps(mols[m].N, ttile, mols[m].n_stiles, sym_R);
         ++a;
     }
     plan->off[a] = total;
@@ -130,6 +139,257 @@ __global__ void batch_pack_kernel(const BatchMol* __restrict__ mols, const Batch
         }
         write_source_pair(M.src + kPairF4 * pr, q[0], q[1], n[0], n[1], av[0], av[1], bv[0], bv[1]);
     }
+}
+
+// As batch_pack_kernel, with the symmetric kernel's payload layout.
+__global__ void batch_sym_pack_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode)
+{
+    const int a = blockIdx.y;
+    if (a >= plan->nactive) return;
+    const BatchMol& M = mols[plan->mol[a]];
+    const double* p = batch_in(M, mode);
+    double* y = batch_out(M, mode);
+    const int64_t N = M.N;
+    const int64_t n_pairs = padded_nodes(N) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pr < n_pairs;
+         pr += (int64_t)gridDim.x * blockDim.x) {
+        float4 q[2], n[2];
+        float av[2], bv[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t j = 2 * pr + e;
+            if (j < N) {
+                q[e] = M.pos[j];
+                n[e] = M.nrm[j];
+                const double wj = M.w[j];
+                const double pj = p[j], pn = p[N + j];
+                av[e] = (float)(wj * pj);
+                bv[e] = (float)(wj * pn);
+                y[j] = M.lambda1 * pj;
+                y[N + j] = M.lambda2 * pn;
+            } else {
+                q[e] = pad_source_pos();
+                n[e] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+                av[e] = bv[e] = 0.0f;
+            }
+        }
+        write_source_pair_sym(M.src, pr, q[0], q[1], n[0], n[1], av[0], av[1], bv[0], bv[1]);
+    }
+}
+
+// Symmetric batched pair sums (rotation scheme of pair_sym.cu): stream-K over
+// the concatenated upper triangles of the active molecules' (target tile,
+// source tile) steps.  Forward sums of a row are added to the molecule's
+// output with FP64 atomics when the row (or the CTA's range) ends; the
+// reverse sums of a staged source tile are collected in shared memory and
+// added to the output with FP64 atomics once every warp has released the
+// stage (warp 0, before it refills the stage).
+template <int TPT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    batch_sym_kernel(const BatchMol* __restrict__ mols, const BatchPlan* __restrict__ plan, int mode,
+                     unsigned* __restrict__ err)
+{
+    constexpr int TTILE = TPT * THREADS;
+    constexpr int NW = THREADS / 32;
+    constexpr int64_t R = TTILE / kF32STile;
+    constexpr int REVOFF = sym_rev_off(true);
+    static_assert(TTILE <= kF32MaxTTile && TTILE % kF32STile == 0, "target tile");
+    __shared__ __align__(128) SourceStage stg[kF32Stages];
+    __shared__ __align__(16) float4 tfrm[NW][2 * TPT];
+    __shared__ __align__(8) StagePipe pipe;
+    __shared__ float racc[kF32Stages][sym_rev_row(true)];
+    __shared__ int stage_mol[kF32Stages];
+    __shared__ int64_t stage_st[kF32Stages];
+    // constants of the molecule of each staged tile (written with the stage's
+    // copy, read by the warps that consume the stage)
+    __shared__ F32Consts stage_k[kF32Stages];
+    __shared__ Geo64 stage_g[kF32Stages];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int64_t total = plan->total;
+    const int64_t per_cta = plan->per_cta;
+    const int64_t s0 = (int64_t)blockIdx.x * per_cta;
+    const int64_t s1 = (s0 + per_cta < total) ? s0 + per_cta : total;
+    if (s0 >= s1) return;
+    const int nact = plan->nactive;
+    const int* __restrict__ s_mol = plan->mol;
+    const int64_t* __restrict__ s_off = plan->off;
+    for (int q = tid; q < kF32Stages * sym_rev_row(true); q += THREADS) (&racc[0][0])[q] = 0.0f;
+    if (tid == 0) pipe_init(pipe, NW);
+    __syncthreads();
+
+    // step u -> active index a, row t and position in the row
+    auto locate = [&](int64_t u, int& a, int64_t& t, int64_t& pos) {
+        int lo = 0, hi = nact - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        a = lo;
+        const BatchMol& M = mols[s_mol[a]];
+        const int64_t v = u - s_off[a];
+        const int64_t n_s = M.n_stiles, n_t = (M.N + TTILE - 1) / TTILE;
+        // rows before t hold t n_s - R t (t - 1) / 2 steps (increasing in t)
+        int64_t tl = 0, th = n_t - 1;
+        while (tl < th) {
+            const int64_t mid = (tl + th + 1) >> 1;
+            if (mid * n_s - R * mid * (mid - 1) / 2 <= v) tl = mid;
+            else th = mid - 1;
+        }
+        t = tl;
+        pos = v - (tl * n_s - R * tl * (tl - 1) / 2);
+    };
+    auto issue = [&](int64_t u) {
+        int a;
+        int64_t t, pos;
+        locate(u, a, t, pos);
+        const BatchMol& M = mols[s_mol[a]];
+        const int64_t st = R * t + pos;
+        const int stage = (int)((u - s0) % kF32Stages);
+        stage_mol[stage] = s_mol[a];
+        stage_st[stage] = st;
+        stage_k[stage] = M.k;
+        stage_g[stage] = M.g64;
+        pipe_issue(pipe, stg[stage], stage, M.src + st * (kF32STile / 2) * kPairF4, M.frames + st * 2 * kChunksPerTile);
+    };
+    if (tid == 0)
+        for (int q = 0; q < kF32Stages && s0 + q < s1; ++q) issue(s0 + q);
+
+    int a;
+    int64_t t, pos;
+    locate(s0, a, t, pos);
+    const BatchMol* M = &mols[s_mol[a]];
+    SymTargets<TPT> T;
+    int64_t gi0 = 0;
+    int Ablk[TPT];
+    bool idle = false;
+    double D1[TPT], D2[TPT];
+
+    auto load_targets = [&]() {
+        gi0 = t * TTILE + tid;
+        idle = t * TTILE + warp * 32 >= M->N;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t i = gi0 + (int64_t)q * THREADS;  // < padded N
+            const float4 p4 = M->pos[i];
+            const float4 n4 = M->nrm[i];
+            T.x[q] = make_float3(p4.x, p4.y, p4.z);
+            T.nx[q] = f2(n4.x);
+            T.ny[q] = f2(n4.y);
+            T.nz[q] = f2(n4.z);
+            const float4 pb = M->src[sym_pair_offset(i >> 1, 1)];
+            const float4 pa = M->src[sym_pair_offset(i >> 1, 3)];
+            T.a[q] = f2((i & 1) ? pa.w : pa.z);
+            T.nb[q] = f2(-((i & 1) ? pb.w : pb.z));
+            Ablk[q] = (int)((t * TTILE + (int64_t)q * THREADS + warp * 32) / kChunk);
+            D1[q] = 0.0;
+            D2[q] = 0.0;
+        }
+        __syncwarp();
+        if (lane < 2 * TPT) {
+            const int64_t blk0 = t * TTILE + (int64_t)(lane >> 1) * THREADS + warp * 32;
+            tfrm[warp][lane] = M->frames[2 * (blk0 / kChunk) + (lane & 1)];
+        }
+        __syncwarp();
+    };
+    // forward sums of the current row into the molecule's output
+    auto flush_rows = [&]() {
+        double* y = batch_out(*M, mode);
+        const int64_t N = M->N;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t i = gi0 + (int64_t)q * THREADS;
+            if (i < N) {
+                atomicAdd(y + i, kInv4Pi * D1[q]);
+                atomicAdd(y + N + i, kInv4Pi * D2[q]);
+            }
+        }
+    };
+    // warp 0: reverse sums of the tile staged for step v into its molecule's output
+    auto flush_rev = [&](int64_t v) {
+        const int sv = (int)((v - s0) % kF32Stages);
+        const BatchMol& S = mols[stage_mol[sv]];
+        double* y = batch_out(S, mode);
+        const int64_t N = S.N;
+        const int64_t j0 = stage_st[sv] * kF32STile;
+        for (int jj = lane; jj < kF32STile; jj += 32) {
+            const float v1 = racc[sv][jj], v2 = racc[sv][REVOFF + jj];
+            if (j0 + jj < N) {
+                if (v1 != 0.0f) atomicAdd(y + j0 + jj, kInv4Pi * (double)v1);
+                if (v2 != 0.0f) atomicAdd(y + N + j0 + jj, kInv4Pi * (double)v2);
+            }
+            racc[sv][jj] = 0.0f;
+            racc[sv][REVOFF + jj] = 0.0f;
+        }
+        __syncwarp();
+    };
+    // warp 0: wait until every warp is past step v
+    auto wait_empty = [&](int64_t v) -> bool {
+        bool ok = true;
+        const int64_t w = v - s0;
+        if (lane == 0)
+            ok = ptx::mbar_wait_bounded(&pipe.empty[(int)(w % kF32Stages)], (uint32_t)((w / kF32Stages) & 1),
+                                        kWaitLimitNs);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok && lane == 0) atomicOr(err, kDevErrTimeout);
+        return ok;
+    };
+    load_targets();
+
+    for (int64_t u = s0; u < s1; ++u) {
+        const int stage = (int)((u - s0) % kF32Stages);
+        const uint32_t parity = (uint32_t)(((u - s0) / kF32Stages) & 1);
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&pipe.full[stage], parity, kWaitLimitNs))) {
+            if (lane == 0) atomicOr(err, kDevErrTimeout);
+            return;
+        }
+        const int64_t st = R * t + pos;
+        float S1[TPT], C1[TPT], S2[TPT], C2[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
+        if (!idle)
+            tile_sums_sym<TPT, true>(T, &tfrm[warp][0], stg[stage].buf, stg[stage].frm, stage_k[stage], S1, C1, S2, C2,
+                                     stage_g[stage], gi0, THREADS, st * kF32STile, M->N, Ablk, st * kChunksPerTile,
+                                     &racc[stage][0]);
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            D1[q] += (double)S1[q] - (double)C1[q];
+            D2[q] += (double)S2[q] - (double)C2[q];
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&pipe.empty[stage]);
+        if (warp == 0 && u > s0) {
+            if (!wait_empty(u - 1)) return;
+            flush_rev(u - 1);
+            if (lane == 0 && u - 1 + kF32Stages < s1) {
+                ptx::fence_proxy_async_smem();
+                issue(u - 1 + kF32Stages);
+            }
+            __syncwarp();
+        }
+        // advance to step u + 1
+        const int64_t row_len = M->n_stiles - R * t;
+        const bool row_ends = (pos + 1 == row_len);
+        if (row_ends || u + 1 == s1) flush_rows();
+        if (u + 1 == s1) break;
+        if (!row_ends) {
+            ++pos;
+        } else {
+            pos = 0;
+            if (t + 1 < (M->N + TTILE - 1) / TTILE) {
+                ++t;
+            } else {
+                ++a;
+                M = &mols[s_mol[a]];
+                t = 0;
+            }
+            load_targets();
+        }
+    }
+    if (warp == 0 && wait_empty(s1 - 1)) flush_rev(s1 - 1);
 }
 
 template <int TPT, int THREADS, int MINB>
@@ -287,14 +547,30 @@ __global__ void __launch_bounds__(THREADS, MINB)
 }
 
 struct BatchVariant {
-    int tpt, threads, minb;
+    int tpt, threads, minb, sym;
     const void* fn;
+    void (*launch)(int grid, cudaStream_t st, const BatchMol* mols, const BatchPlan* plan, int mode, unsigned* err);
 };
-#define IBIM_BATCH_VARIANT(T, W, M) {T, W, M, (const void*)batch_pair_kernel<T, W, M>}
+template <int T, int W, int M>
+static void launch_batch_pair(int grid, cudaStream_t st, const BatchMol* mols, const BatchPlan* plan, int mode,
+                              unsigned* err)
+{
+    batch_pair_kernel<T, W, M><<<grid, W, 0, st>>>(mols, plan, mode, err);
+}
+template <int T, int W>
+static void launch_batch_sym(int grid, cudaStream_t st, const BatchMol* mols, const BatchPlan* plan, int mode,
+                             unsigned* err)
+{
+    batch_sym_kernel<T, W><<<grid, W, 0, st>>>(mols, plan, mode, err);
+}
+#define IBIM_BATCH_VARIANT(T, W, M) {T, W, M, 0, (const void*)batch_pair_kernel<T, W, M>, launch_batch_pair<T, W, M>}
+#define IBIM_BATCH_SYM_VARIANT(T, W) {T, W, 1, 1, (const void*)batch_sym_kernel<T, W>, launch_batch_sym<T, W>}
 static const BatchVariant kBatchVariants[] = {
     IBIM_BATCH_VARIANT(1, 512, 1), IBIM_BATCH_VARIANT(1, 256, 2), IBIM_BATCH_VARIANT(1, 128, 4),
+    IBIM_BATCH_SYM_VARIANT(1, 512),
 };
 #undef IBIM_BATCH_VARIANT
+#undef IBIM_BATCH_SYM_VARIANT
 constexpr int kNumBatchVariants = (int)(sizeof(kBatchVariants) / sizeof(kBatchVariants[0]));
 
 // ------------------------------------------------------------------ host side
@@ -330,33 +606,29 @@ struct BatchRun {
 };
 
 std::mutex g_batch_tune_mu;
-std::map<std::pair<int, int>, int> g_batch_tune;  // (device, floor(log2 sum N^2)) -> variant
+// (device, floor(log2 sum N^2), tolerance below kSymTolFloor) -> variant
+std::map<std::tuple<int, int, int>, int> g_batch_tune;
+int g_batch_forced = -1;                           // ibim_set_batch_variant (-1: measured choice)
 
 }  // namespace
 
 static ibim_status batch_operator(ibim_ctx* c0, BatchRun& R, int mode)
 {
     const BatchVariant& v = kBatchVariants[R.variant];
-    batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, (int64_t)v.tpt * v.threads, R.grid,
-                                          R.d_plan);
-    batch_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
-    switch (R.variant) {
-    case 1:
-        batch_pair_kernel<1, 256, 2><<<R.grid, 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
-        break;
-    case 2:
-        batch_pair_kernel<1, 128, 4><<<R.grid, 128, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
-        break;
-    default:
-        batch_pair_kernel<1, 512, 1><<<R.grid, 512, 0, R.bs>>>(R.d_mols, R.d_plan, mode, c0->d_err);
-        break;
-    }
+    const int64_t ttile = (int64_t)v.tpt * v.threads;
+    batch_plan_kernel<<<1, 32, 0, R.bs>>>(R.d_mols, R.nmol, mode, R.d_want, ttile, v.sym ? ttile / kF32STile : 0,
+                                          R.grid, R.d_plan);
+    if (v.sym)
+        batch_sym_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
+    else
+        batch_pack_kernel<<<dim3(R.pack_blocks, R.nmol), 256, 0, R.bs>>>(R.d_mols, R.d_plan, mode);
+    v.launch(R.grid, R.bs, R.d_mols, R.d_plan, mode, c0->d_err);
     count_launch(c0, 3);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
 }
 
-static ibim_status tune_batch_variant(ibim_ctx* c0, BatchRun& R)
+static ibim_status tune_batch_variant(ibim_ctx* c0, BatchRun& R, double tol)
 {
     cudaEvent_t e0, e1;
     IBIM_CUDA(cudaEventCreate(&e0));
@@ -365,6 +637,7 @@ static ibim_status tune_batch_variant(ibim_ctx* c0, BatchRun& R)
     int pick = R.variant;
     ibim_status st = IBIM_OK;
     for (int v = 0; v < kNumBatchVariants && st == IBIM_OK; ++v) {
+        if (kBatchVariants[v].sym && tol < kSymTolFloor) continue;  // see kSymTolFloor
         R.set_variant(v);
         cudaEventRecord(e0, R.bs);
         st = batch_operator(c0, R, 0);
@@ -383,6 +656,22 @@ static ibim_status tune_batch_variant(ibim_ctx* c0, BatchRun& R)
     R.set_variant(pick);
     return st;
 }
+
+static thread_local int batch_last_variant = -1;
+
+int batch_variant_count() { return kNumBatchVariants; }
+void batch_variant_info(int v, int* tpt, int* threads, int* symmetric)
+{
+    *tpt = kBatchVariants[v].tpt;
+    *threads = kBatchVariants[v].threads;
+    *symmetric = kBatchVariants[v].sym;
+}
+void batch_force_variant(int v)
+{
+    std::lock_guard<std::mutex> lock(g_batch_tune_mu);
+    g_batch_forced = v;
+}
+int batch_last_variant_used() { return batch_last_variant; }
 
 ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts& o,
                         double* const* d_p, ibim_solve_info* infos)
@@ -459,8 +748,9 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
     int cached = -1;
     {
         std::lock_guard<std::mutex> lock(g_batch_tune_mu);
-        auto it = g_batch_tune.find({ctxs[0]->device, bucket});
+        auto it = g_batch_tune.find({ctxs[0]->device, bucket, o.tol < kSymTolFloor ? 1 : 0});
         if (it != g_batch_tune.end()) cached = it->second;
+        if (g_batch_forced >= 0) cached = g_batch_forced;
     }
     R.set_variant(cached >= 0 ? cached : 0);
     R.pack_blocks = (int)std::min<int64_t>(256, (maxN + 255) / 256);
@@ -517,11 +807,12 @@ ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, 
         // this round (plan + pack + pairs recompute V_{k+1} from scratch, so
         // repeating them is harmless) and keep the fastest.
         if (cached < 0) {
-            IBIM_TRY(tune_batch_variant(ctxs[0], R));
+            IBIM_TRY(tune_batch_variant(ctxs[0], R, o.tol));
             cached = R.variant;
             std::lock_guard<std::mutex> lock(g_batch_tune_mu);
-            g_batch_tune[{ctxs[0]->device, bucket}] = cached;
+            g_batch_tune[{ctxs[0]->device, bucket, o.tol < kSymTolFloor ? 1 : 0}] = cached;
         }
+        batch_last_variant = R.variant;
         // one graph per solve: plan + pack + batched pairs + every molecule's orthogonalisation
         if (R.exec == nullptr) {
             cudaGraph_t graph = nullptr;

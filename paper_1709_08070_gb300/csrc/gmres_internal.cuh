@@ -43,6 +43,8 @@ struct GmresWork {
     int graph_prec = 0;
     PairConsts graph_k;
     uint64_t graph_generation = 0;  // workspace generation the graph was captured with
+    int graph_variant = -1;         // FP32 pair-kernel variant and CTAs per SM captured in the graph
+    int graph_bps = -1;
     bool graph_valid = false;
 };
 

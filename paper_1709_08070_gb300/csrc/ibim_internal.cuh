@@ -200,6 +200,10 @@ int f32_ttile(const ibim_ctx* c);
 int f32_max_bps(int variant);
 int f32_variant_count();
 void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric);
+bool f32_variant_symmetric(int v);
+int f32_deterministic_variant();  // the one-directional variant used below kSymTolFloor
+// Smallest GMRES tolerance solved with a symmetric FP32 kernel (see gmres_solve).
+constexpr double kSymTolFloor = 1e-7;
 size_t f32_part_doubles(ibim_ctx* c);  // partial-sum doubles of the current variant and grid
 // symmetric FP32 pair kernel (pair_sym.cu)
 int sym_variant_count();
@@ -259,5 +263,9 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
 void gmres_free(ibim_ctx* c);
 ibim_status batch_solve(int nmol, ibim_ctx* const* ctxs, const ibim_phys* phys, const ibim_solve_opts& o,
                         double* const* d_p, ibim_solve_info* infos);
+int batch_variant_count();
+void batch_variant_info(int v, int* tpt, int* threads, int* symmetric);
+void batch_force_variant(int v);
+int batch_last_variant_used();
 
 }  // namespace ibim

@@ -302,6 +302,9 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // Variants kNumVariants.. are the symmetric kernel's (pair_sym.cu).
 int f32_variant_count() { return kNumVariants + sym_variant_count(); }
 static bool is_sym(int v) { return v >= kNumVariants; }
+bool f32_variant_symmetric(int v) { return is_sym(v); }
+int f32_deterministic_variant() { return 5; }  // (2 targets/thread, 1 CTA/SM, 512 threads)
+static_assert(5 < kNumVariants, "deterministic variant");
 
 void f32_variant_info(int v, int* tpt, int* minb, int* threads, int* symmetric)
 {

@@ -147,3 +147,31 @@ extern "C" ibim_status ibim_set_f32_variant(ibim_ctx* c, int variant, int ctas_p
     c->f32_bps = ctas_per_sm;
     return IBIM_OK;
 }
+
+extern "C" int ibim_batch_variant_count(void) { return batch_variant_count(); }
+
+extern "C" ibim_status ibim_batch_variant_info(int v, int* targets_per_thread, int* threads_per_cta, int* symmetric,
+                                              int* last_used)
+{
+    if (last_used) *last_used = batch_last_variant_used();
+    if (v < 0 || v >= batch_variant_count()) {
+        set_error("batched variant index out of range");
+        return IBIM_ERR_ARG;
+    }
+    int t = 0, w = 0, y = 0;
+    batch_variant_info(v, &t, &w, &y);
+    if (targets_per_thread) *targets_per_thread = t;
+    if (threads_per_cta) *threads_per_cta = w;
+    if (symmetric) *symmetric = y;
+    return IBIM_OK;
+}
+
+extern "C" ibim_status ibim_set_batch_variant(int v)
+{
+    if (v < -1 || v >= batch_variant_count()) {
+        set_error("batched variant must be -1 (measured choice) or in [0, ibim_batch_variant_count())");
+        return IBIM_ERR_ARG;
+    }
+    batch_force_variant(v);
+    return IBIM_OK;
+}

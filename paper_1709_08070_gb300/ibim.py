@@ -65,6 +65,7 @@ class SolveInfo(ctypes.Structure):
 _V = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _I64P = ctypes.POINTER(ctypes.c_int64)
+_IP = ctypes.POINTER(ctypes.c_int)
 _CTXP = ctypes.POINTER(_V)
 _SIGS = {
     "ibim_build_sphere": [ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_double, _V, _CTXP],
@@ -110,6 +111,8 @@ _SIGS = {
     "ibim_wsnet_train": [_V, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D],
     "ibim_wsnet_predict": [_V, _V, ctypes.POINTER(Phys), _V],
     "ibim_debug_raise_device_error": [_V, ctypes.c_int],
+    "ibim_batch_variant_info": [ctypes.c_int, _IP, _IP, _IP, _IP],
+    "ibim_set_batch_variant": [ctypes.c_int],
 }
 
 _lib = None
@@ -135,6 +138,8 @@ def lib():
         L.ibim_last_error.argtypes = []
         L.ibim_f32_variant_count.restype = ctypes.c_int
         L.ibim_f32_variant_count.argtypes = []
+        L.ibim_batch_variant_count.restype = ctypes.c_int
+        L.ibim_batch_variant_count.argtypes = []
         L.ibim_wsnet_destroy.restype = None
         L.ibim_wsnet_destroy.argtypes = [_V]
         L.ibim_destroy.restype = None
@@ -371,6 +376,22 @@ def ibim_f32_variants():
         _check(lib().ibim_f32_variant_info(v, ctypes.byref(t), ctypes.byref(m), ctypes.byref(w), ctypes.byref(y)))
         out.append((t.value, m.value, w.value, y.value))
     return out
+
+
+def ibim_batch_variants():
+    """([(targets_per_thread, threads_per_cta, symmetric)] of the batched pair-kernel variants,
+    variant run by the last batched solve of this thread or -1)."""
+    out, last = [], ctypes.c_int(-1)
+    for v in range(lib().ibim_batch_variant_count()):
+        t, w, y = (ctypes.c_int(0) for _ in range(3))
+        _check(lib().ibim_batch_variant_info(v, ctypes.byref(t), ctypes.byref(w), ctypes.byref(y), ctypes.byref(last)))
+        out.append((t.value, w.value, y.value))
+    return out, last.value
+
+
+def ibim_set_batch_variant(v):
+    """Force batched variant v for later batched solves (-1: the measured choice)."""
+    _check(lib().ibim_set_batch_variant(int(v)))
 
 
 def ibim_autotune(ctx, phys):

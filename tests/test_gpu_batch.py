@@ -85,42 +85,60 @@ ORACLE_SOLVE_MAX_N = 15000
 
 
 def test_batch_matches_oracle():
-    """Each batched FP32 solution (tol 1e-8) against the oracle: the oracle's
-    FP64 GMRES solution (tol 1e-10) to 1e-5 (relative 2-norm and worst element
-    per block) and its G_pol to 1e-4; for every molecule the oracle's own
-    residual ||g - A p|| / ||g|| of the batched solution stays below 1e-6 and
-    the oracle's G_pol of the batched solution equals the batched G_pol to 1e-6."""
+    """Each batched FP32 solution (tol 1e-7) against the oracle, for every
+    batched pair-kernel variant (one-directional and symmetric, forced one
+    after the other): the oracle's FP64 GMRES solution (tol 1e-10) to 1e-5
+    (relative 2-norm and worst element per block) and its G_pol to 1e-4; for
+    every molecule the oracle's own residual ||g - A p|| / ||g|| of the batched
+    solution stays below 1e-6 and the oracle's G_pol of the batched solution
+    equals the batched G_pol to 1e-6."""
     mols = _molecules(with_oracle=True)
     try:
         ctxs = [m[0] for m in mols]
         physs = [m[1] for m in mols]
-        outs = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in ctxs]
-        infos = ibim.ibim_solve_batch(ctxs, physs, outs, precision=ibim.IBIM_F32C, tol=1e-8, restart=64, maxit=400)
-        for (ctx, P, o), d, info in zip(mols, outs, infos):
-            N = ctx.N
-            x = _to_oracle(d.cpu().numpy(), o["perm"])
-            b = oracle.rhs(o["xs"], o["nrm"], o["z"], o["q"], P.eps_in)
-            r = b - oracle.matvec(o["xs"], o["nrm"], o["w"], o["Po"], x)
-            res = np.linalg.norm(r) / np.linalg.norm(b)
-            G_of_x = oracle.gpol(o["q"], oracle.psi_rxn(o["xs"], o["nrm"], o["w"], o["z"], o["Po"], x))
-            print("batch vs oracle N=%d: oracle residual of the batched solution %.2e, G %.8f vs %.8f"
-                  % (N, res, info["gpol"], G_of_x))
-            assert info["converged"] and res < 1e-6, (N, res)
-            assert abs(info["gpol"] - G_of_x) <= 1e-6 * abs(G_of_x), (N, info["gpol"], G_of_x)
-            if N > ORACLE_SOLVE_MAX_N:
+        ref = {}
+        for mi, (ctx, P, o) in enumerate(mols):
+            if ctx.N > ORACLE_SOLVE_MAX_N:
                 continue
+            b = oracle.rhs(o["xs"], o["nrm"], o["z"], o["q"], P.eps_in)
             xo, it, rr, ok = oracle.gmres(o["xs"], o["nrm"], o["w"], o["Po"], b, tol=1e-10, maxit=1000)
             assert ok
             Go = oracle.gpol(o["q"], oracle.psi_rxn(o["xs"], o["nrm"], o["w"], o["z"], o["Po"], xo))
-            errs = []
-            for blk in (slice(0, N), slice(N, 2 * N)):
-                errs += [np.linalg.norm(x[blk] - xo[blk]) / np.linalg.norm(xo[blk]),
-                         np.max(np.abs(x[blk] - xo[blk])) / np.max(np.abs(xo[blk]))]
-            print("  oracle solve: %d iterations; solution rel/worst %.2e %.2e | %.2e %.2e; G %.8f vs oracle %.8f"
-                  % (it, *errs, info["gpol"], Go))
-            assert max(errs) < 1e-5, (N, errs)
-            assert abs(info["gpol"] - Go) <= 1e-4 * abs(Go), (N, info["gpol"], Go)
+            ref[mi] = (xo, Go, it)
+        variants, _ = ibim.ibim_batch_variants()
+        assert any(v[2] for v in variants)  # a symmetric batched kernel is compiled
+        for var in range(len(variants)):
+            ibim.ibim_set_batch_variant(var)
+            outs = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in ctxs]
+            # 1e-7: the symmetric kernel's reverse sums vary by about 1e-8 of |A p| from one
+            # application to the next, the floor of its restart residuals
+            infos = ibim.ibim_solve_batch(ctxs, physs, outs, precision=ibim.IBIM_F32C, tol=1e-7, restart=64,
+                                          maxit=400)
+            assert ibim.ibim_batch_variants()[1] == var
+            for mi, ((ctx, P, o), d, info) in enumerate(zip(mols, outs, infos)):
+                N = ctx.N
+                x = _to_oracle(d.cpu().numpy(), o["perm"])
+                b = oracle.rhs(o["xs"], o["nrm"], o["z"], o["q"], P.eps_in)
+                r = b - oracle.matvec(o["xs"], o["nrm"], o["w"], o["Po"], x)
+                res = np.linalg.norm(r) / np.linalg.norm(b)
+                G_of_x = oracle.gpol(o["q"], oracle.psi_rxn(o["xs"], o["nrm"], o["w"], o["z"], o["Po"], x))
+                print("variant %d %s N=%d: oracle residual of the batched solution %.2e, G %.8f vs %.8f"
+                      % (var, variants[var], N, res, info["gpol"], G_of_x))
+                assert info["converged"] and res < 1e-6, (var, N, res)
+                assert abs(info["gpol"] - G_of_x) <= 1e-6 * abs(G_of_x), (var, N, info["gpol"], G_of_x)
+                if mi not in ref:
+                    continue
+                xo, Go, it = ref[mi]
+                errs = []
+                for blk in (slice(0, N), slice(N, 2 * N)):
+                    errs += [np.linalg.norm(x[blk] - xo[blk]) / np.linalg.norm(xo[blk]),
+                             np.max(np.abs(x[blk] - xo[blk])) / np.max(np.abs(xo[blk]))]
+                print("  oracle solve: %d iterations; solution rel/worst %.2e %.2e | %.2e %.2e; G %.8f vs oracle %.8f"
+                      % (it, *errs, info["gpol"], Go))
+                assert max(errs) < 1e-5, (var, N, errs)
+                assert abs(info["gpol"] - Go) <= 1e-4 * abs(Go), (var, N, info["gpol"], Go)
     finally:
+        ibim.ibim_set_batch_variant(-1)
         for m in mols:
             m[0].close()
 
@@ -195,3 +213,34 @@ def test_batch_rejects_unsupported_options():
         ibim.ibim_solve_batch([ctx, ctx], [P, P], [d, d])
     assert e.value.status == 1
     ctx.close()
+
+
+def test_tight_tolerance_solves_use_the_deterministic_kernel():
+    """A solve asked for a tolerance below 1e-7 while the context has a
+    symmetric FP32 variant set converges (it runs the one-directional kernel,
+    whose applications repeat exactly); a batched solve below 1e-7 does not
+    pick the symmetric batched kernel."""
+    ctx = ibim.Context.sphere(6.0, h=0.5, band_eps=1.0)
+    try:
+        z, q = inputs.kirkwood_charges(n=3, ball_radius=3.6, seed=60)
+        ctx.set_charges(z, q)
+        P = ibim.Phys(2.0, 80.0, 0.1257, 0.5, 0)
+        sym = [v for v, info in enumerate(ibim.ibim_f32_variants()) if info[3]]
+        d = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
+        for v in sym:
+            ctx.set_f32_variant(v, 0)
+            info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=1e-9, restart=64, maxit=400)
+            assert info["converged"] and info["relres"] < 1e-9
+            x = torch.empty_like(d)
+            y = torch.empty_like(d)
+            ctx.matvec(P, d, x)
+            ctx.matvec(P, d, y)
+            # the context keeps working with its own variant afterwards
+            assert float(torch.max(torch.abs(x - y))) <= 1e-7 * float(torch.max(torch.abs(x)))
+        ibim.ibim_set_batch_variant(-1)
+        d2 = torch.empty_like(d)
+        infos = ibim.ibim_solve_batch([ctx], [P], [d2], precision=ibim.IBIM_F32C, tol=1e-9, restart=64, maxit=400)
+        variants, last = ibim.ibim_batch_variants()
+        assert infos[0]["converged"] and variants[last][2] == 0
+    finally:
+        ctx.close()
