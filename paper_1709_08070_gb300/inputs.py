@@ -167,6 +167,76 @@ def globule_atoms(n_atoms, seed=SEED_PROTEIN, step=3.8, min_dist=3.0, beta=100.0
     return pos - pos.mean(axis=0), radii, q
 
 
+def residue_atoms(n_atoms, seed=SEED_PROTEIN, atoms_per_residue=8, ca_step=3.8, ca_min=4.5, volume_per_residue=130.0,
+                  contact=2.2, radius_range=(1.6, 1.9), charge_range=(-0.8, 0.8)):
+    """Seeded heavy-atom-like cloud at protein packing density: a self-avoiding
+    chain of residue centres (bond `ca_step` A, non-bonded >= `ca_min` A) grown
+    inside a ball of volume n_residues * `volume_per_residue` A^3 (about the
+    volume a residue occupies in a folded protein), then `atoms_per_residue` - 1
+    further atoms per residue placed 1.5-4 A from its centre, each at least
+    `contact` A from every atom placed before it (heavy atoms of real proteins
+    overlap their neighbours' van der Waals spheres in the same way).  Radii
+    uniform in `radius_range`; charges as in globule_atoms.  Returns
+    (centres (n,3) about their mean, radii, charges)."""
+    rng = np.random.default_rng(seed)
+    n_res = max(1, int(round(n_atoms / atoms_per_residue)))
+    R_ball = (3.0 * n_res * volume_per_residue / (4.0 * np.pi)) ** (1.0 / 3.0)
+    ca = np.zeros((n_res, 3))
+    i = 1
+    tries = 0
+    while i < n_res:
+        d = rng.standard_normal((64, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        cand = ca[i - 1] + ca_step * d
+        ok = np.linalg.norm(cand, axis=1) <= R_ball
+        if i > 1:
+            dd = np.linalg.norm(cand[:, None, :] - ca[None, :i - 1, :], axis=2)
+            ok &= (dd >= ca_min).all(axis=1)
+        good = np.nonzero(ok)[0]
+        if good.size == 0:
+            tries += 1
+            back = min(i - 1, 4 + tries // 8)
+            i -= back
+            continue
+        ca[i] = cand[good[rng.integers(good.size)]]
+        i += 1
+    atoms = [c for c in ca]
+    cell = {}
+
+    def key(p):
+        return tuple(np.floor(p / 4.0).astype(int))
+
+    for j, p in enumerate(atoms):
+        cell.setdefault(key(p), []).append(j)
+
+    def clear(p):
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for j in cell.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                        if np.sum((atoms[j] - p) ** 2) < contact * contact:
+                            return False
+        return True
+
+    for r in range(n_res):
+        placed = 0
+        for _ in range(400):
+            if placed == atoms_per_residue - 1 or len(atoms) >= n_atoms:
+                break
+            d = rng.standard_normal(3)
+            p = ca[r] + rng.uniform(1.5, 4.0) * d / np.linalg.norm(d)
+            if clear(p):
+                cell.setdefault(key(p), []).append(len(atoms))
+                atoms.append(p)
+                placed += 1
+    pos = np.array(atoms)
+    radii = rng.uniform(radius_range[0], radius_range[1], size=len(pos))
+    q = rng.uniform(charge_range[0], charge_range[1], size=len(pos))
+    q -= q.mean()
+    return pos - pos.mean(axis=0), radii, q
+
+
 def batch_sizes(n_mol=64, lo=50, hi=3000, seed=SEED_BATCH):
     """Atom counts log-uniform in [lo, hi] and screening constants kappa ~ U[0, 0.2]."""
     rng = np.random.default_rng(seed)
