@@ -55,6 +55,12 @@ F32_OPS_PER_INTERACTION_SYM = 24
 # the two float-float accumulations 22 FP32-pipe operations per interaction
 # (plus one MUFU, about six integer operations and five shared loads).
 FF_OPS_PER_INTERACTION = 366
+# The symmetric float-float kernel (pair_ffs_kernel, the default IBIM_FF kernel),
+# counted from ffs_pair: 296 shared operations per unordered pair (the above up
+# to rho^-3, plus the combination g c - (3 - B) s_x s_y / rho^2 27 and four
+# products with the powers of 1/rho 16) and 68 per direction (the two terms 46,
+# their float-float accumulation 22): 432 per unordered pair, 216 per interaction.
+FFS_OPS_PER_INTERACTION = 216
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this
 # workload, by variant (targets/thread, min CTAs/SM, threads/CTA, symmetric scheme), from
@@ -404,7 +410,9 @@ def run_ours(args):
         xa = torch.from_numpy(inputs_random(2 * N)).cuda()
         ya = torch.empty_like(xa)
         acc = {}
-        for name, prec, reps in (("ff", ibim.IBIM_FF, 3), ("f64", ibim.IBIM_F64, 1)):
+        for name, prec, reps, ffs in (("ffs", ibim.IBIM_FF, 3, 1), ("ff", ibim.IBIM_FF, 3, 0),
+                                      ("f64", ibim.IBIM_F64, 1, 1)):
+            ctx.set_ff_kernel(ffs)
             ctx.matvec(P, xa, ya, precision=prec)
             ctx.timing_enable(True)
             ctx.timing_reset()
@@ -414,11 +422,17 @@ def run_ours(args):
             tk = ctx.timing()
             ctx.timing_enable(False)
             acc[name] = tk["pair_ms"] / max(1, tk["pair_launches"])
+        ctx.set_ff_kernel(1)
+        ffs_ops = FFS_OPS_PER_INTERACTION * N * N / (acc["ffs"] * 1e-3)
         ff_ops = FF_OPS_PER_INTERACTION * N * N / (acc["ff"] * 1e-3)
-        certifier = {"kernel": "pair_ff_kernel", "precision": "float-float (IBIM_FF)", "avg_launch_ms": acc["ff"],
-                     "interactions_per_s": N * N / (acc["ff"] * 1e-3), "ops_per_interaction": FF_OPS_PER_INTERACTION,
-                     "achieved": ff_ops / 1e12, "frac": ff_ops / peak_ops, "unit": "Tops/s",
-                     "f64_kernel_ms": acc["f64"], "speedup_vs_f64_kernel": acc["f64"] / acc["ff"]}
+        certifier = {"kernel": "pair_ffs_kernel", "precision": "float-float (IBIM_FF), symmetric kernel",
+                     "avg_launch_ms": acc["ffs"], "interactions_per_s": N * N / (acc["ffs"] * 1e-3),
+                     "ops_per_interaction": FFS_OPS_PER_INTERACTION, "achieved": ffs_ops / 1e12,
+                     "frac": ffs_ops / peak_ops, "unit": "Tops/s",
+                     "f64_kernel_ms": acc["f64"], "speedup_vs_f64_kernel": acc["f64"] / acc["ffs"],
+                     "one_directional": {"kernel": "pair_ff_kernel", "avg_launch_ms": acc["ff"],
+                                         "ops_per_interaction": FF_OPS_PER_INTERACTION,
+                                         "achieved": ff_ops / 1e12, "frac": ff_ops / peak_ops}}
         fp64 = None
         if not args.skip_fp64:
             t0 = time.perf_counter()
@@ -941,7 +955,8 @@ def run_profile(args):
         variant, bps = args.variant, args.ctas_per_sm
     else:
         variant, bps, _ = ctx.autotune(P)
-    prec = {"f32c": ibim.IBIM_F32C, "ff": ibim.IBIM_FF, "f64": ibim.IBIM_F64}[args.prec]
+    prec = {"f32c": ibim.IBIM_F32C, "ff": ibim.IBIM_FF, "ff1": ibim.IBIM_FF, "f64": ibim.IBIM_F64}[args.prec]
+    ctx.set_ff_kernel(0 if args.prec == "ff1" else 1)
     if args.treecode_theta > 0:
         ctx.treecode_setup(args.treecode_theta, W["tau_k"] * h, args.treecode_interp)
         prec = ibim.IBIM_F32T
@@ -977,8 +992,9 @@ def main():
                     help="operator applications only (for profiler captures); prints no bench line")
     ap.add_argument("--variant", type=int, default=None, help="with --profile: FP32 kernel variant (no autotune)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --variant: CTAs per SM (0 = occupancy)")
-    ap.add_argument("--prec", default="f32c", choices=["f32c", "ff", "f64"],
-                    help="with --profile: operator precision (FP32 compensated, float-float or FP64)")
+    ap.add_argument("--prec", default="f32c", choices=["f32c", "ff", "ff1", "f64"],
+                    help="with --profile: operator precision (FP32 compensated, float-float with the symmetric "
+                         "kernel, float-float with the one-directional kernel, or FP64)")
     ap.add_argument("--treecode-theta", type=float, default=0.0,
                     help="with --profile: apply the treecode operator (IBIM_F32T) with this theta instead")
     ap.add_argument("--treecode-interp", type=int, default=0, choices=[0, 1],

@@ -397,6 +397,14 @@ ibim_status ibim_autotune(ibim_ctx* ctx, const ibim_phys* phys, int* variant, in
  * grid (0 = the occupancy limit; larger values are clamped to it). */
 ibim_status ibim_set_f32_variant(ibim_ctx* ctx, int variant, int ctas_per_sm);
 
+/* Kernel of the float-float operator IBIM_FF on this context: 1 (default) the
+ * symmetric kernel, each unordered node pair evaluated once for both
+ * directions, reverse sums added in FP64 with atomics (so its last bits vary
+ * from run to run, far below its 1e-10 accuracy); 0 the one-directional
+ * kernel (repeatable bit for bit).  Both give the FP64 oracle's operator to
+ * within 1e-10 of max |y| per element. */
+ibim_status ibim_set_ff_kernel(ibim_ctx* ctx, int symmetric);
+
 /* ------------------------------------------------- allocation-free variant */
 
 /*

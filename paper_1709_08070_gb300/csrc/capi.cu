@@ -259,6 +259,13 @@ extern "C" {
 
 const char* ibim_last_error(void) { return g_err.c_str(); }
 
+ibim_status ibim_set_ff_kernel(ibim_ctx* c, int symmetric)
+{
+    if (c == nullptr || (symmetric != 0 && symmetric != 1)) return fail(IBIM_ERR_ARG, "need a context and 0 or 1");
+    c->ff_symmetric = symmetric;
+    return IBIM_OK;
+}
+
 // One thread sets bits of the device error word, as a kernel whose bounded
 // wait gave up does (the failure-path test hook below).
 __global__ void raise_device_error_kernel(unsigned* __restrict__ err, unsigned bits) { atomicOr(err, bits); }

@@ -148,6 +148,7 @@ struct ibim_ctx {
     size_t yrev_bytes = 0;
     float2* d_fftab = nullptr;   // float-float table of 2^(i/256) (IBIM_FF), made on first use
     double ff_grid_scale = 0.0;  // 2^q: grid of the hi parts of float-float coordinates
+    int ff_symmetric = 1;        // IBIM_FF kernel: 1 symmetric (each unordered pair once), 0 one-directional
     ibim::GmresWork* gm = nullptr;
     ibim::TreeCode* tc = nullptr;  // treecode tree, lists and proxy buffers (ibim_treecode_setup)
     ibim::Timing timing;
@@ -215,6 +216,8 @@ ibim_status sym_pack(ibim_ctx* c, VecRef in, const int* d_skip);
 ibim_status sym_pairs(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, const int* d_skip);
 ibim_status sym_fixup(ibim_ctx* c, int sv, int grid_cap, const PairConsts& k, VecRef in, OutRef out,
                       const int* d_skip);
+ibim_status sym_fixup_tiles(ibim_ctx* c, int ttile, int grid_cap, const PairConsts& k, VecRef in, OutRef out,
+                            const int* d_skip);
 PairSchedule f32_schedule(ibim_ctx* c);
 ibim_status f32_chunk_frames(ibim_ctx* c);
 ibim_status f32_pack_to(ibim_ctx* c, VecRef in, float4* dst, const int* d_skip);

@@ -41,8 +41,7 @@
 // thread, 256-source tiles through two shared-memory stages filled by bulk
 // async copies; chunk pairs whose bounding spheres are at least the far
 // distance apart skip the tube test, as in the FP32 kernel.
-#include "ibim_internal.cuh"
-#include "ptx.cuh"
+#include "pair_sym_core.cuh"
 
 namespace ibim {
 
@@ -55,8 +54,15 @@ constexpr int kFFChunksPerTile = kFFSTile / kFFChunk;
 constexpr int kFFTab = 256;      // table of 2^(i/256)
 constexpr uint64_t kFFWaitNs = 2000000000ull;  // 2 s
 static_assert(kPadNodes % kFFSTile == 0 && kPadNodes % kFFTTile == 0, "padding");
-// payload per node: (xh, ah), (xl, al), (nh, bh), (nl, bl)
+// payload per node: (xh, ah), (xl, al), (nh, bh), (nl, bl), stored per aligned
+// 32-node chunk component by component (the chunk's 32 first float4, then its
+// 32 second ones, ...), so that 32 lanes reading 32 different nodes of a chunk
+// touch 512 contiguous bytes
 constexpr int kFFNodeF4 = 4;
+__host__ __device__ __forceinline__ int64_t ff_off(int64_t j, int comp)
+{
+    return (j >> 5) * (32 * kFFNodeF4) + comp * 32 + (j & 31);
+}
 constexpr uint32_t kFFStageBytes = kFFSTile * kFFNodeF4 * sizeof(float4);
 constexpr uint32_t kFFFrameBytes = 2 * kFFChunksPerTile * sizeof(float4);
 constexpr float kFFPad = 1.0e4f;  // placeholder coordinate (sources +, targets -)
@@ -337,8 +343,8 @@ __global__ void __launch_bounds__(kFFThreads, 2)
     auto load_target = [&](int64_t tile) {
         gi = tile * kFFTTile + tid;
         idle = tile * kFFTTile + warp * kFFChunk >= N;
-        const float4 a = src[kFFNodeF4 * gi], b = src[kFFNodeF4 * gi + 1];
-        const float4 c = src[kFFNodeF4 * gi + 2], e = src[kFFNodeF4 * gi + 3];
+        const float4 a = src[ff_off(gi, 0)], b = src[ff_off(gi, 1)];
+        const float4 c = src[ff_off(gi, 2)], e = src[ff_off(gi, 3)];
         const bool pad = gi >= N;  // placeholder targets away from placeholder sources
         T.xh0 = pad ? -kFFPad : a.x;
         T.xh1 = pad ? -kFFPad : a.y;
@@ -387,13 +393,13 @@ __global__ void __launch_bounds__(kFFThreads, 2)
                 if (far) {
 #pragma unroll 2
                     for (int p = 0; p < kFFChunk; ++p)
-                        ff_pair<false>(T, cb[kFFNodeF4 * p], cb[kFFNodeF4 * p + 1], cb[kFFNodeF4 * p + 2],
-                                       cb[kFFNodeF4 * p + 3], k, tab, S1, S2, geo, gi, j0 + p, N);
+                        ff_pair<false>(T, cb[p], cb[32 + p], cb[64 + p], cb[96 + p], k, tab, S1, S2, geo, gi, j0 + p,
+                                       N);
                 } else {
 #pragma unroll 1
                     for (int p = 0; p < kFFChunk; ++p)
-                        ff_pair<true>(T, cb[kFFNodeF4 * p], cb[kFFNodeF4 * p + 1], cb[kFFNodeF4 * p + 2],
-                                      cb[kFFNodeF4 * p + 3], k, tab, S1, S2, geo, gi, j0 + p, N);
+                        ff_pair<true>(T, cb[p], cb[32 + p], cb[64 + p], cb[96 + p], k, tab, S1, S2, geo, gi, j0 + p,
+                                      N);
                 }
             }
             D1 += (double)S1.h + (double)S1.l;
@@ -414,6 +420,285 @@ __global__ void __launch_bounds__(kFFThreads, 2)
                 load_target(t);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------- symmetric
+//
+// The same operator with each unordered node pair evaluated once for both
+// directions (as the symmetric FP32 kernel of pair_sym.cu does): the shared
+// float-float work (r, |r|^2, s_x, s_y, n . m, 1/rho, E, g, 1 - th A, 3 - B,
+// the combination g c - (3 - B) s_x s_y / rho^2 and the powers of 1/rho) is
+// done once, and the reverse direction (target j <- source i) is formed from
+// it with r' = -r, s_x' = -s_y, s_y' = -s_x, c' = c:
+//   forward   y1_i += u1 s_y a_j / rho^3 - (1 - E) b_j / rho
+//             y2_i += [br a_j + u2 s_x b_j] / rho^3
+//   reverse   y1_j += -u1 s_x a_i / rho^3 - (1 - E) b_i / rho
+//             y2_j += [br a_i - u2 s_y b_i] / rho^3
+// with br = g c - (3 - B) s_x s_y / rho^2.  Each direction takes its own tube
+// test (the reverse one on the source's normal, rho_P'^2 = |r|^2 - s_y^2).
+// 432 FP32 operations per unordered pair against 2 x 366.
+//
+// Per warp and source chunk the 32 lanes hold 32 targets and walk the chunk's
+// 32 sources in a staggered order (lane l takes source (l + k) mod 32 at step
+// k); the float-float reverse sums of a source ride along with it from lane to
+// lane (four shuffles a step), so after 32 steps lane l holds source l's
+// reverse sums over the warp's targets and adds them, as doubles, to the
+// reverse vector with FP64 atomics.  Forward sums and the schedule (upper
+// triangle, large and small segments, partials per (segment, row)) are those
+// of the symmetric FP32 kernel, and its fixup adds everything up.
+
+// One unordered pair: forward into (S1, S2), reverse (when rev) into (R1, R2).
+template <bool NEAR>
+__device__ __forceinline__ void ffs_pair(const FFTarget& T, ff ai, ff bi, const float4& F0, const float4& F1,
+                                         const float4& F2, const float4& F3, const FFConsts& k,
+                                         const float2* __restrict__ tab, bool rev, ff& S1, ff& S2, ff& R1, ff& R2,
+                                         const double* __restrict__ geo, int64_t i, int64_t j, int64_t N)
+{
+    const float rh0 = __fsub_rn(T.xh0, F0.x), rh1 = __fsub_rn(T.xh1, F0.y), rh2 = __fsub_rn(T.xh2, F0.z);
+    const float rl0 = __fsub_rn(T.xl0, F1.x), rl1 = __fsub_rn(T.xl1, F1.y), rl2 = __fsub_rn(T.xl2, F1.z);
+    const ff rr = ff_norm2(rh0, rl0, rh1, rl1, rh2, rl2);
+    const ff sx = ff_dot3(rh0, rl0, rh1, rl1, rh2, rl2, T.nh0, T.nl0, T.nh1, T.nl1, T.nh2, T.nl2);
+    const ff sy = ff_dot3(rh0, rl0, rh1, rl1, rh2, rl2, F2.x, F3.x, F2.y, F3.y, F2.z, F3.z);
+    const ff aj = ff{F0.w, F1.w}, bj = ff{F2.w, F3.w};
+    bool tube_f = false, tube_r = false;
+    if (NEAR) {
+        const float d2 = __fadd_rn(__fsub_rn(rr.h, k.four_tau2.x), __fsub_rn(rr.l, k.four_tau2.y));
+        const bool tie2 = fabsf(d2) < 1e-9f * k.four_tau2.x;
+        const ff pf = ff_sub(rr, ff_mul(sx, sx));
+        const float d1f = __fadd_rn(__fsub_rn(pf.h, k.tau2.x), __fsub_rn(pf.l, k.tau2.y));
+        tube_f = (d1f < 0.0f) && (d2 < 0.0f);
+        if ((tie2 || fabsf(d1f) < 1e-9f * k.tau2.x) && i < N && j < N)
+            tube_f = tube_f64_ordered(geo, N, i, j, k.tau2_d, k.four_tau2_d);
+        if (rev) {
+            const ff pr = ff_sub(rr, ff_mul(sy, sy));
+            const float d1r = __fadd_rn(__fsub_rn(pr.h, k.tau2.x), __fsub_rn(pr.l, k.tau2.y));
+            tube_r = (d1r < 0.0f) && (d2 < 0.0f);
+            if ((tie2 || fabsf(d1r) < 1e-9f * k.tau2.x) && i < N && j < N)
+                tube_r = tube_f64_ordered(geo, N, j, i, k.tau2_d, k.four_tau2_d);
+        }
+        if (tube_f && (tube_r || !rev)) {  // both directions regularised (the self pair among them)
+            const ff c = ff_mul(ff_of(k.nk12t), bj);
+            const ff s = two_sum(S1.h, c.h);
+            S1 = fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(S1.l, c.l)));
+            if (rev) {
+                const ff cr = ff_mul(ff_of(k.nk12t), bi);
+                const ff t = two_sum(R1.h, cr.h);
+                R1 = fast_two_sum(t.h, __fadd_rn(t.l, __fadd_rn(R1.l, cr.l)));
+            }
+            return;
+        }
+    }
+    const ff cc = ff_dot3(T.nh0, T.nl0, T.nh1, T.nl1, T.nh2, T.nl2, F2.x, F3.x, F2.y, F3.y, F2.z, F3.z);
+    const float y0 = ptx::rsqrt_approx(rr.h);
+    const ff q = ff_mul(rr, ff{__fmul_rn(y0, y0), __fmaf_rn(y0, y0, -__fmul_rn(y0, y0))});
+    const float d = __fadd_rn(__fsub_rn(q.h, 1.0f), q.l);
+    const ff inv = ff{y0, __fmul_rn(__fmul_rn(y0, d), __fmaf_rn(0.375f, d, -0.5f))};
+    const ff rho = ff_mul(rr, inv);
+    const ff x = ff_mul(ff_of(k.kap), rho);
+    const ff E = ff_exp2(ff_mul(ff_of(k.cz), rho), tab);
+    const ff Ex = ff_mul(E, x);
+    const float fh = __fsub_rn(1.0f, E.h);
+    const ff f = ff{fh, __fsub_rn(__fsub_rn(__fsub_rn(1.0f, fh), E.h), E.l)};
+    const ff g = ff_sub(f, Ex);
+    const ff u1 = ff_add(ff_of(k.om1), ff_mul(ff_of(k.th1), g));
+    const ff u2 = ff_add(ff_of(k.om2), ff_mul(ff_of(k.th2), g));
+    const ff hb = ff_sub(ff_mulf(g, 3.0f), ff_mul(Ex, x));
+    const ff inv2 = ff_mul(inv, inv);
+    const ff inv3 = ff_mul(inv2, inv);
+    const ff br = ff_sub(ff_mul(g, cc), ff_mul(hb, ff_mul(ff_mul(sx, sy), inv2)));
+    const ff P1 = ff_mul(u1, inv3), Q = ff_mul(f, inv), P2 = ff_mul(u2, inv3), B3 = ff_mul(br, inv3);
+    ff c1, c2;
+    if (NEAR && tube_f) {
+        c1 = ff_mul(ff_of(k.nk12t), bj);
+        c2 = ff{0.0f, 0.0f};
+    } else {
+        c1 = ff_sub(ff_mul(P1, ff_mul(sy, aj)), ff_mul(Q, bj));
+        c2 = ff_add(ff_mul(B3, aj), ff_mul(ff_mul(P2, sx), bj));
+    }
+    const ff s1 = two_sum(S1.h, c1.h);
+    S1 = fast_two_sum(s1.h, __fadd_rn(s1.l, __fadd_rn(S1.l, c1.l)));
+    const ff s2 = two_sum(S2.h, c2.h);
+    S2 = fast_two_sum(s2.h, __fadd_rn(s2.l, __fadd_rn(S2.l, c2.l)));
+    if (!rev) return;
+    ff e1, e2;
+    if (NEAR && tube_r) {
+        e1 = ff_mul(ff_of(k.nk12t), bi);
+        e2 = ff{0.0f, 0.0f};
+    } else {
+        const ff m = ff_mul(P1, ff_mul(sx, ai));
+        e1 = ff_sub(ff{-m.h, -m.l}, ff_mul(Q, bi));
+        e2 = ff_sub(ff_mul(B3, ai), ff_mul(ff_mul(P2, sy), bi));
+    }
+    const ff r1 = two_sum(R1.h, e1.h);
+    R1 = fast_two_sum(r1.h, __fadd_rn(r1.l, __fadd_rn(R1.l, e1.l)));
+    const ff r2 = two_sum(R2.h, e2.h);
+    R2 = fast_two_sum(r2.h, __fadd_rn(r2.l, __fadd_rn(R2.l, e2.l)));
+}
+
+constexpr int kFFSThreads = 256;  // one target per thread; target tile = source tile (R = 1)
+
+__global__ void __launch_bounds__(kFFSThreads, 2)
+    pair_ffs_kernel(const float4* __restrict__ src, const float4* __restrict__ frames,
+                    const float2* __restrict__ tab_g, const double* __restrict__ geo, int64_t N, int64_t n_pad,
+                    SymSchedule s, FFConsts k, double* __restrict__ part, double* __restrict__ yrev,
+                    unsigned* __restrict__ err, const int* __restrict__ skip)
+{
+    constexpr int TTILE = kFFSThreads;
+    if (skip != nullptr && *skip) return;
+    __shared__ __align__(128) float4 sbuf[kFFStages][kFFSTile * kFFNodeF4];
+    __shared__ __align__(16) float4 sfrm[kFFStages][2 * kFFChunksPerTile];
+    __shared__ float2 tab[kFFTab];
+    __shared__ __align__(8) uint64_t bars[kFFStages];
+    __shared__ int abort_flag;
+    __shared__ int64_t seg_next;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    unsigned long long* seg_ctr = reinterpret_cast<unsigned long long*>(yrev + 2 * n_pad);
+    for (int q = tid; q < kFFTab; q += kFFSThreads) tab[q] = tab_g[q];
+    if (tid == 0) {
+        for (int q = 0; q < kFFStages; ++q) ptx::mbar_init(&bars[q], 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    // ring position: this CTA's n-th step uses stage n mod kFFStages, phase (n / kFFStages) mod 2
+    int64_t n_done = 0;
+    auto issue = [&](int64_t u, int64_t n) {
+        int64_t t, rho, pos;
+        sym_locate(s, u, t, rho, pos);
+        const int64_t st = s.R * t + pos;
+        const int stage = (int)(n % kFFStages);
+        ptx::mbar_arrive_expect_tx(&bars[stage], kFFStageBytes + kFFFrameBytes);
+        ptx::bulk_g2s(&sbuf[stage][0], src + st * kFFSTile * kFFNodeF4, kFFStageBytes, &bars[stage]);
+        ptx::bulk_g2s(&sfrm[stage][0], frames + st * 2 * kFFChunksPerTile, kFFFrameBytes, &bars[stage]);
+    };
+
+    FFTarget T;
+    ff ai, bi;
+    float4 tfh, tfl;
+    int64_t gi = 0;
+    int Ablk = 0;
+    bool idle = false;
+    double D1 = 0.0, D2 = 0.0;
+    auto load_target = [&](int64_t tile) {
+        gi = tile * TTILE + tid;
+        idle = tile * TTILE + warp * kFFChunk >= N;
+        const float4 a = src[ff_off(gi, 0)], b = src[ff_off(gi, 1)];
+        const float4 c = src[ff_off(gi, 2)], e = src[ff_off(gi, 3)];
+        const bool pad = gi >= N;
+        T.xh0 = pad ? -kFFPad : a.x;
+        T.xh1 = pad ? -kFFPad : a.y;
+        T.xh2 = pad ? -kFFPad : a.z;
+        T.xl0 = pad ? 0.0f : b.x;
+        T.xl1 = pad ? 0.0f : b.y;
+        T.xl2 = pad ? 0.0f : b.z;
+        T.nh0 = c.x;
+        T.nh1 = c.y;
+        T.nh2 = c.z;
+        T.nl0 = e.x;
+        T.nl1 = e.y;
+        T.nl2 = e.z;
+        ai = ff{a.w, b.w};
+        bi = ff{c.w, e.w};
+        Ablk = (int)((tile * TTILE + warp * kFFChunk) / kFFChunk);
+        const int64_t blk = Ablk;
+        tfh = frames[2 * blk];
+        tfl = frames[2 * blk + 1];
+        D1 = D2 = 0.0;
+    };
+
+    int64_t seg = blockIdx.x;
+    while (seg < s.nseg) {
+        const int64_t s0 = sym_seg_start(s, seg), s1 = sym_seg_start(s, seg + 1);
+        if (tid == 0)
+            for (int q = 0; q < kFFStages && s0 + q < s1; ++q) issue(s0 + q, n_done + q);
+        int64_t t, rho, pos;
+        sym_locate(s, s0, t, rho, pos);
+        load_target(t);
+        for (int64_t u = s0; u < s1; ++u) {
+            const int64_t n = n_done + (u - s0);
+            const int stage = (int)(n % kFFStages);
+            if (!ptx::mbar_wait_bounded(&bars[stage], (uint32_t)((n / kFFStages) & 1), kFFWaitNs)) {
+                abort_flag = 1;
+                atomicOr(err, kDevErrTimeout);
+            }
+            __syncthreads();
+            if (abort_flag) return;
+            const int64_t st = s.R * t + pos;
+            if (!idle) {
+                ff S1{0.0f, 0.0f}, S2{0.0f, 0.0f};
+                const float4* sb = &sbuf[stage][0];
+#pragma unroll 1
+                for (int c = 0; c < kFFChunksPerTile; ++c) {
+                    const int64_t Bc = st * kFFChunksPerTile + c;
+                    if (Bc < Ablk) continue;  // the warp holding block Bc covers this block pair
+                    const bool rev = Bc > Ablk;
+                    const float4 mh = sfrm[stage][2 * c], ml = sfrm[stage][2 * c + 1];
+                    const float dx = (tfh.x - mh.x) + (tfl.x - ml.x);
+                    const float dy = (tfh.y - mh.y) + (tfl.y - ml.y);
+                    const float dz = (tfh.z - mh.z) + (tfl.z - ml.z);
+                    const float lim = k.far_dist + tfh.w + mh.w;
+                    const bool far = k.rule0 && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim);
+                    const float4* cb = sb + c * kFFChunk * kFFNodeF4;
+                    const int64_t j0 = Bc * kFFChunk;
+                    ff R1{0.0f, 0.0f}, R2{0.0f, 0.0f};
+                    if (far) {
+#pragma unroll 1
+                        for (int step = 0; step < kFFChunk; ++step) {
+                            const int p = (lane + step) & (kFFChunk - 1);
+                            ffs_pair<false>(T, ai, bi, cb[p], cb[32 + p], cb[64 + p], cb[96 + p], k, tab, rev, S1, S2,
+                                            R1, R2, geo, gi, j0 + p, N);
+                            R1.h = __shfl_sync(0xffffffffu, R1.h, lane + 1);  // source p goes to lane - 1
+                            R1.l = __shfl_sync(0xffffffffu, R1.l, lane + 1);
+                            R2.h = __shfl_sync(0xffffffffu, R2.h, lane + 1);
+                            R2.l = __shfl_sync(0xffffffffu, R2.l, lane + 1);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int step = 0; step < kFFChunk; ++step) {
+                            const int p = (lane + step) & (kFFChunk - 1);
+                            ffs_pair<true>(T, ai, bi, cb[p], cb[32 + p], cb[64 + p], cb[96 + p], k, tab, rev, S1, S2,
+                                           R1, R2, geo, gi, j0 + p, N);
+                            R1.h = __shfl_sync(0xffffffffu, R1.h, lane + 1);
+                            R1.l = __shfl_sync(0xffffffffu, R1.l, lane + 1);
+                            R2.h = __shfl_sync(0xffffffffu, R2.h, lane + 1);
+                            R2.l = __shfl_sync(0xffffffffu, R2.l, lane + 1);
+                        }
+                    }
+                    if (rev) {  // lane l holds source j0 + l's reverse sums over the warp's targets
+                        atomicAdd(yrev + j0 + lane, (double)R1.h + (double)R1.l);
+                        atomicAdd(yrev + n_pad + j0 + lane, (double)R2.h + (double)R2.l);
+                    }
+                }
+                D1 += (double)S1.h + (double)S1.l;
+                D2 += (double)S2.h + (double)S2.l;
+            }
+            __syncthreads();
+            if (tid == 0 && u + kFFStages < s1) {
+                ptx::fence_proxy_async_smem();
+                issue(u + kFFStages, n + kFFStages);
+            }
+            if (pos == sym_row_len(s, t) - 1 || u + 1 == s1) {
+                double* dst = part + (seg + rho) * 2 * TTILE;
+                dst[tid] = D1;
+                dst[TTILE + tid] = D2;
+                if (u + 1 < s1) {
+                    sym_locate(s, u + 1, t, rho, pos);
+                    load_target(t);
+                }
+            } else {
+                ++pos;
+            }
+        }
+        n_done += s1 - s0;
+        if (tid == 0) seg_next = s.nbig + (int64_t)atomicAdd(seg_ctr, 1ull);
+        __syncthreads();
+        seg = seg_next;
+        __syncthreads();
     }
 }
 
@@ -449,17 +734,21 @@ __global__ void ff_extent_kernel(const double* __restrict__ geo, int64_t N, doub
 // normals, a = w psi and b = w psin split into hi + lo.
 __global__ void ff_pack_kernel(const double* __restrict__ geo, int64_t N, int64_t n_pad, double c0, double c1,
                                double c2, double grid_scale, VecRef in, float4* __restrict__ src,
-                               const int* __restrict__ skip)
+                               double* __restrict__ yrev, const int* __restrict__ skip)
 {
     if (skip != nullptr && *skip) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
-    float4* d = src + kFFNodeF4 * j;
+    if (yrev != nullptr) {  // symmetric kernel: clear its reverse sums and its segment counter
+        yrev[j] = 0.0;
+        yrev[n_pad + j] = 0.0;
+        if (j == 0) *reinterpret_cast<unsigned long long*>(yrev + 2 * n_pad) = 0ull;
+    }
     if (j >= N) {
-        d[0] = make_float4(kFFPad, kFFPad, kFFPad, 0.0f);
-        d[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        d[2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-        d[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        src[ff_off(j, 0)] = make_float4(kFFPad, kFFPad, kFFPad, 0.0f);
+        src[ff_off(j, 1)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        src[ff_off(j, 2)] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+        src[ff_off(j, 3)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
     const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
@@ -477,10 +766,10 @@ __global__ void ff_pack_kernel(const double* __restrict__ geo, int64_t N, int64_
     const double w = geo[6 * N + j];
     const double av = w * p[j], bv = w * p[N + j];
     const float ah = (float)av, bh = (float)bv;
-    d[0] = make_float4(xh[0], xh[1], xh[2], ah);
-    d[1] = make_float4(xl[0], xl[1], xl[2], (float)(av - (double)ah));
-    d[2] = make_float4(nh[0], nh[1], nh[2], bh);
-    d[3] = make_float4(nl[0], nl[1], nl[2], (float)(bv - (double)bh));
+    src[ff_off(j, 0)] = make_float4(xh[0], xh[1], xh[2], ah);
+    src[ff_off(j, 1)] = make_float4(xl[0], xl[1], xl[2], (float)(av - (double)ah));
+    src[ff_off(j, 2)] = make_float4(nh[0], nh[1], nh[2], bh);
+    src[ff_off(j, 3)] = make_float4(nl[0], nl[1], nl[2], (float)(bv - (double)bh));
 }
 
 // ------------------------------------------------------------------ host side
@@ -494,10 +783,12 @@ int ff_grid_cap(ibim_ctx* c)
 
 PairSchedule ff_schedule(ibim_ctx* c) { return make_schedule(c->N, kFFTTile, c->N, kFFSTile, ff_grid_cap(c)); }
 
+size_t ffs_part_doubles(ibim_ctx* c);
+
 size_t ff_part_doubles(ibim_ctx* c)
 {
     const PairSchedule s = ff_schedule(c);
-    return (size_t)s.grid * s.max_segs * 2 * kFFTTile;
+    return std::max((size_t)s.grid * s.max_segs * 2 * kFFTTile, ffs_part_doubles(c));
 }
 
 size_t ff_src_bytes(int64_t N) { return (size_t)padded_nodes(N) * kFFNodeF4 * sizeof(float4); }
@@ -527,6 +818,15 @@ static ibim_status ff_prepare(ibim_ctx* c)
 
 ibim_status ff_prepare_context(ibim_ctx* c) { return ff_prepare(c); }
 
+int ffs_grid_cap(ibim_ctx* c)
+{
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_ffs_kernel, kFFSThreads, 0);
+    return (occ < 1 ? 1 : occ) * c->num_sms;
+}
+
+size_t ffs_part_doubles(ibim_ctx* c) { return sym_part_doubles(c->N, kFFSThreads, ffs_grid_cap(c)); }
+
 ibim_status ff_pack(ibim_ctx* c, VecRef in, const int* d_skip)
 {
     IBIM_TRY(ff_prepare(c));
@@ -534,7 +834,7 @@ ibim_status ff_pack(ibim_ctx* c, VecRef in, const int* d_skip)
     const int bs = 256;
     ff_pack_kernel<<<(unsigned)((n_pad + bs - 1) / bs), bs, 0, c->stream>>>(
         c->d_geo64, N, n_pad, c->centroid[0], c->centroid[1], c->centroid[2], c->ff_grid_scale, in,
-        (float4*)c->d_src, d_skip);
+        (float4*)c->d_src, c->ff_symmetric ? c->d_yrev : nullptr, d_skip);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -542,8 +842,16 @@ ibim_status ff_pack(ibim_ctx* c, VecRef in, const int* d_skip)
 
 ibim_status ff_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, const int* d_skip)
 {
-    pair_ff_kernel<<<s.grid, kFFThreads, 0, c->stream>>>((const float4*)c->d_src, c->d_frames, c->d_fftab, c->d_geo64,
-                                                          c->N, s, ff_consts(k), c->d_part, c->d_err, d_skip);
+    if (c->ff_symmetric) {
+        const SymSchedule ss = make_sym_schedule(c->N, kFFSThreads, ffs_grid_cap(c));
+        pair_ffs_kernel<<<ss.grid, kFFSThreads, 0, c->stream>>>(
+            (const float4*)c->d_src, c->d_frames, c->d_fftab, c->d_geo64, c->N, padded_nodes(c->N), ss, ff_consts(k),
+            c->d_part, c->d_yrev, c->d_err, d_skip);
+    } else {
+        pair_ff_kernel<<<s.grid, kFFThreads, 0, c->stream>>>((const float4*)c->d_src, c->d_frames, c->d_fftab,
+                                                              c->d_geo64, c->N, s, ff_consts(k), c->d_part, c->d_err,
+                                                              d_skip);
+    }
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
     return IBIM_OK;
@@ -552,6 +860,7 @@ ibim_status ff_pairs(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, co
 ibim_status ff_fixup(ibim_ctx* c, const PairConsts& k, const PairSchedule& s, VecRef in, OutRef out,
                      const int* d_skip)
 {
+    if (c->ff_symmetric) return sym_fixup_tiles(c, kFFSThreads, ffs_grid_cap(c), k, in, out, d_skip);
     return fixup_launch(c, k, s, kFFTTile, in, out, d_skip);
 }
 

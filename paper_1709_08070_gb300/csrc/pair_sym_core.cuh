@@ -7,6 +7,77 @@
 
 namespace ibim {
 
+// Stream-K schedule of a symmetric launch over the upper triangle of
+// (target tile, source tile) steps (see pair_sym.cu).
+struct SymSchedule {
+    int64_t n_t, n_s, R;  // target tiles, source tiles, source tiles per target tile
+    int64_t npairs;       // row pairs (n_t / 2); an odd row count leaves a middle row at the end
+    int64_t L2;           // steps of a row pair: 2 n_s - R (n_t - 1)
+    int64_t total;        // steps
+    int64_t Lb, nbig;     // large segments: nbig (= grid) of Lb steps, first
+    int64_t Ls, nseg;     // then small segments of Ls steps (the last may be shorter); nseg in all
+    int grid;
+};
+
+// First step of segment q (q <= nseg; total for q = nseg).
+__host__ __device__ __forceinline__ int64_t sym_seg_start(const SymSchedule& s, int64_t q)
+{
+    const int64_t v = q < s.nbig ? q * s.Lb : s.nbig * s.Lb + (q - s.nbig) * s.Ls;
+    return v < s.total ? v : s.total;
+}
+
+// Segment holding step u (u < total).
+__host__ __device__ __forceinline__ int64_t sym_seg_of(const SymSchedule& s, int64_t u)
+{
+    const int64_t big = s.nbig * s.Lb;
+    return u < big ? u / s.Lb : s.nbig + (u - big) / s.Ls;
+}
+
+__host__ __device__ __forceinline__ int64_t sym_row_len(const SymSchedule& s, int64_t t) { return s.n_s - s.R * t; }
+
+// Step u of the sequence -> row t, its sequence index rho and the position in the row.
+__host__ __device__ __forceinline__ void sym_locate(const SymSchedule& s, int64_t u, int64_t& t, int64_t& rho,
+                                                    int64_t& pos)
+{
+    const int64_t p = u / s.L2;
+    if (p < s.npairs) {
+        const int64_t r = u - p * s.L2;
+        const int64_t l0 = sym_row_len(s, p);
+        if (r < l0) {
+            t = p;
+            rho = 2 * p;
+            pos = r;
+        } else {
+            t = s.n_t - 1 - p;
+            rho = 2 * p + 1;
+            pos = r - l0;
+        }
+    } else {
+        t = s.npairs;
+        rho = 2 * s.npairs;
+        pos = u - s.npairs * s.L2;
+    }
+}
+
+// First step of row t in the sequence and its sequence index.
+__host__ __device__ __forceinline__ void sym_row_start(const SymSchedule& s, int64_t t, int64_t& start,
+                                                       int64_t& rho)
+{
+    if (t < s.npairs) {
+        start = t * s.L2;
+        rho = 2 * t;
+    } else if (t >= s.n_t - s.npairs) {
+        const int64_t p = s.n_t - 1 - t;
+        start = p * s.L2 + sym_row_len(s, p);
+        rho = 2 * p + 1;
+    } else {
+        start = s.npairs * s.L2;
+        rho = 2 * s.npairs;
+    }
+}
+
+SymSchedule make_sym_schedule(int64_t N, int ttile, int grid_cap);
+
 // Float4 offset of component `comp` (0..3 = A..D) of payload pair `pr`.
 __host__ __device__ __forceinline__ int64_t sym_pair_offset(int64_t pr, int comp)
 {

@@ -113,6 +113,7 @@ _SIGS = {
     "ibim_debug_raise_device_error": [_V, ctypes.c_int],
     "ibim_batch_variant_info": [ctypes.c_int, _IP, _IP, _IP, _IP],
     "ibim_set_batch_variant": [ctypes.c_int],
+    "ibim_set_ff_kernel": [_V, ctypes.c_int],
 }
 
 _lib = None
@@ -599,6 +600,10 @@ class Context:
 
     def set_f32_variant(self, variant, ctas_per_sm=0):
         ibim_set_f32_variant(self.handle, variant, ctas_per_sm)
+
+    def set_ff_kernel(self, symmetric):
+        """IBIM_FF kernel: 1 symmetric (default), 0 one-directional."""
+        _check(lib().ibim_set_ff_kernel(self.handle, int(symmetric)))
 
     def treecode_setup(self, theta, tau_max, target_interp=0, order=6):
         ibim_treecode_setup(self.handle, theta, tau_max, target_interp, order)

@@ -40,20 +40,53 @@ def _match(gpu_ijk, orc_ijk):
     return np.array([ko[tuple(v)] for v in gpu_ijk], dtype=np.int64)
 
 
-def test_ff_tiny_and_ragged_caller_clouds():
-    for n in (1, 2, 3, 257, 1000, 3001):
+@pytest.mark.parametrize("symmetric", [1, 0])
+def test_ff_tiny_and_ragged_caller_clouds(symmetric):
+    """Both float-float kernels (symmetric, one-directional) on clouds with fewer
+    nodes than a chunk, a ragged last chunk and tile, and several tiles."""
+    for n in (1, 2, 3, 33, 257, 1000, 3001):
         xs, nr, w = inputs.sphere_cloud(n, radius=3.0, seed=100 + n)
         ctx = ibim.Context.from_nodes(xs, nr, w, h=0.25)
         try:
-            P = ibim.Phys(2.0, 80.0, 0.1257, 0.3, 0)
-            Po = oracle.Phys(2.0, 80.0, 0.1257, 0.3, 0)
-            p = inputs.random_vector(2 * n, seed=n)
-            y = ctx.matvec_host(P, p, precision=ibim.IBIM_FF)
-            e = _worst_blocks(y, oracle.matvec(xs, nr, w, Po, p), n)
-            print("ff cloud n=%d: %s" % (n, " ".join("%.1e" % v for v in e)))
-            assert max(e) < TOL, (n, e)
+            ctx.set_ff_kernel(symmetric)
+            for rule in (0, 1):
+                P = ibim.Phys(2.0, 80.0, 0.1257, 0.3, rule)
+                Po = oracle.Phys(2.0, 80.0, 0.1257, 0.3, rule)
+                p = inputs.random_vector(2 * n, seed=n)
+                y = ctx.matvec_host(P, p, precision=ibim.IBIM_FF)
+                e = _worst_blocks(y, oracle.matvec(xs, nr, w, Po, p), n)
+                print("ff (symmetric %d) cloud n=%d rule %d: %s" % (symmetric, n, rule,
+                                                                   " ".join("%.1e" % v for v in e)))
+                assert max(e) < TOL, (n, rule, e)
         finally:
             ctx.close()
+
+
+def test_ff_kernels_on_the_kirkwood_sphere_rows():
+    """The 80k-node sphere: 2,048 oracle rows for both float-float kernels, and
+    the two kernels against each other on every row."""
+    R, h = 20.0, 0.5
+    ctx = ibim.Context.sphere(R, h=h, band_eps=2 * h)
+    try:
+        g = oracle.sphere_nodes(R, h=h, eps=2 * h)
+        perm = _match(ctx.nodes()["ijk"], g["ijk"])
+        N = ctx.N
+        P = ibim.Phys(2.0, 80.0, 0.1257, h, 0)
+        Po = oracle.Phys(2.0, 80.0, 0.1257, h, 0)
+        p = inputs.random_vector(2 * N, seed=64)
+        rows = inputs.random_rows(N, 2048, seed=65)
+        y1o, y2o = oracle.matvec_rows(g["xs"], g["nrm"], g["w"], Po, p, perm[rows])
+        outs = []
+        for symmetric in (1, 0):
+            ctx.set_ff_kernel(symmetric)
+            y = ctx.matvec_host(P, np.concatenate([p[:N][perm], p[N:][perm]]), precision=ibim.IBIM_FF)
+            e = _worst_blocks(np.concatenate([y[:N][rows], y[N:][rows]]), np.concatenate([y1o, y2o]), 2048)
+            print("ff (symmetric %d) kirkwood rows: %s" % (symmetric, " ".join("%.1e" % v for v in e)))
+            assert max(e) < TOL, (symmetric, e)
+            outs.append(y)
+        assert max(_worst_blocks(outs[0], outs[1], N)) < TOL
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("kappa,tau_k,rule,eps_in", [(0.2, 1.0, 1, 2.0), (0.0, 0.5, 0, 1.0), (0.1257, 1.0, 0, 4.0)])
