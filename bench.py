@@ -511,10 +511,22 @@ def _line(args, workload, value, ms, extra):
     print(json.dumps(line), flush=True)
 
 
-def _globule(n_atoms, seed, h=0.5, probe=1.4):
+def _globule(n_atoms, seed, h=0.5, probe=1.4, atoms=None):
+    """Level-set context of a seeded globule (atoms: a precomputed (z, r, q))."""
     from paper_1709_08070_gb300 import ibim, inputs
-    z, r, q = inputs.globule_atoms(int(n_atoms), seed=int(seed))
+    z, r, q = atoms if atoms is not None else inputs.globule_atoms(int(n_atoms), seed=int(seed))
     return ibim.Context.molecule(z, r, q, probe=probe, h=h)
+
+
+def _globule_atoms_parallel(specs):
+    """inputs.globule_atoms for every (n_atoms, seed) of specs on all host cores
+    (a spawned process pool, started before this process uses the GPU)."""
+    import multiprocessing as mp
+
+    from paper_1709_08070_gb300 import inputs
+    specs = [(int(n), int(sd)) for n, sd in specs]
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32))) as pool:
+        return pool.starmap(inputs.globule_atoms, specs, chunksize=4)
 
 
 def protein_summary(args, steps=3):
@@ -831,14 +843,18 @@ def run_learned(args):
     from paper_1709_08070_gb300 import ibim, inputs
 
     rng = np.random.default_rng(inputs.SEED_LEARNED)
-    net = ibim.WarmStartNet(seed=1)
     t0 = time.perf_counter()
     train_atoms = rng.integers(args.learn_train_lo, args.learn_train_hi + 1, size=args.learn_train)
     train_kappa = rng.uniform(0.0, 0.2, size=args.learn_train)
+    # the training globules' atoms on the host cores first (no GPU use before the pool)
+    train_sets = _globule_atoms_parallel([(train_atoms[m], inputs.SEED_LEARNED + 100 + m)
+                                          for m in range(args.learn_train)])
+    atoms_s = time.perf_counter() - t0
+    net = ibim.WarmStartNet(seed=1)
     n_examples = 0
     for b0 in range(0, args.learn_train, 64):
         idx = range(b0, min(args.learn_train, b0 + 64))
-        ctxs = [_globule(train_atoms[m], inputs.SEED_LEARNED + 100 + m) for m in idx]
+        ctxs = [_globule(train_atoms[m], inputs.SEED_LEARNED + 100 + m, atoms=train_sets[m]) for m in idx]
         physs = [ibim.Phys(1.0, 80.0, float(train_kappa[m]), 0.5, 0) for m in idx]
         outs = [torch.empty(2 * c.N, dtype=torch.float64, device="cuda") for c in ctxs]
         infos = ibim.ibim_solve_batch(ctxs, physs, outs, precision=ibim.IBIM_F32C, tol=1e-6, restart=64,
@@ -933,7 +949,8 @@ def run_learned(args):
             "vs_baseline": None, "dtype": "bf16 weights, f32+f64 solve", "data": "synthetic", "config": cfg,
             "zero_start_iters_per_solve": z_it / max(1, len(tests)),
             "iters_saved_frac": (z_it - l_it) / max(1, z_it), "time_saved_frac": (z_s - l_s) / max(1e-9, z_s),
-            "train": {"examples_s": gen_s, "train_s": train_s, "loss_first": loss0, "loss_last": loss},
+            "train": {"examples_s": gen_s, "atoms_on_host_s": atoms_s, "train_s": train_s, "loss_first": loss0,
+                      "loss_last": loss},
             "tests": tests, "batched_warm_started_vs_f64": combined}
     print(json.dumps(line), flush=True)
 
@@ -1007,10 +1024,10 @@ def main():
     ap.add_argument("--batch-rounds", type=int, default=4000,
                     help="with --workload batched: cap on lock-step GMRES rounds (the default lets every molecule "
                          "converge)")
-    ap.add_argument("--learn-train", type=int, default=256)
+    ap.add_argument("--learn-train", type=int, default=2000)
     ap.add_argument("--learn-train-lo", type=int, default=100)
     ap.add_argument("--learn-train-hi", type=int, default=1000)
-    ap.add_argument("--learn-steps", type=int, default=20000)
+    ap.add_argument("--learn-steps", type=int, default=50000)
     ap.add_argument("--learn-test", type=int, default=2)
     ap.add_argument("--learn-test-atoms", type=int, default=10000)
     ap.add_argument("--learn-cmp", type=int, default=8, help="held-out globules of the batched comparison")
