@@ -499,8 +499,13 @@ ibim_status ibim_set_batch_variant(int v);
  * Kernel timing: when enabled, the pair-sum kernel launches of this context
  * are bracketed by CUDA events on the context stream.  ibim_timing_get returns
  * the summed event time (ms), the number of pair-kernel launches, the pair
- * interactions they evaluated and the total number of kernels this context
- * launched since the last reset.  Reading synchronises.
+ * interactions they were launched for (N^2 each) and the total number of
+ * kernels this context launched since the last reset.  Reading synchronises.
+ * GMRES launches its Arnoldi steps in pairs between host polls: when a cycle
+ * converges on the first step of a pair, the second launch finds the solver
+ * done and returns at once, yet counts here as a launch of N^2 interactions.
+ * ibim_solve_info's matvec counts are the applications that ran; divide the
+ * event time by those for the time of one application.
  */
 ibim_status ibim_timing_enable(ibim_ctx* ctx, int enable);
 ibim_status ibim_timing_reset(ibim_ctx* ctx);
