@@ -14,9 +14,12 @@
 //
 // Outer loop: r = g - A_out x, one GMRES cycle on A_in d = r from d = 0,
 // x += d.  Without certification A_out = A_in (plain restarted GMRES).  With
-// certification A_out is the FP64 operator and each cycle works to half the
-// tolerance with A_in (iterative refinement), so the reported residual is the
-// FP64 one.
+// certification A_out is an FP64-accurate operator: restarted GMRES with A_in
+// runs to half the tolerance, then the residual is recomputed with A_out; if
+// it misses the tolerance, the correction equation A e = r_out is solved the
+// same way with A_in from e = 0 (its restart residuals r_out - A_in e) and
+// x += e (iterative refinement).  The reported residual is the FP64-accurate
+// one.
 #include <math.h>
 #include <string.h>
 
@@ -237,6 +240,13 @@ __global__ void cycle_begin_scale_kernel(const double* __restrict__ r, double* _
         V0[i] = r[i] * inv;
 }
 
+// x += y
+__global__ void add_kernel(double* __restrict__ x, const double* __restrict__ y, int64_t len)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += y[i];
+}
+
 // x0 = Lambda^{-1} g (Sec. 3.3 initial guess with D = 0)
 __global__ void lambda_inv_kernel(const double* __restrict__ g, double* __restrict__ x, int64_t N, double l1,
                                   double l2)
@@ -261,6 +271,8 @@ void gmres_free(ibim_ctx* c)
     cudaFree(w->r);
     cudaFree(w->t);
     cudaFree(w->g);
+    cudaFree(w->xb);
+    cudaFree(w->gin);
     cudaFree(w->part);
     cudaFree(w->st);
     cudaFreeHost(w->h_st);
@@ -284,6 +296,8 @@ ibim_status gm_alloc(ibim_ctx* c, int m)
     IBIM_CUDA(cudaMalloc((void**)&w->r, sizeof(double) * len));
     IBIM_CUDA(cudaMalloc((void**)&w->t, sizeof(double) * len));
     IBIM_CUDA(cudaMalloc((void**)&w->g, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->xb, sizeof(double) * len));
+    IBIM_CUDA(cudaMalloc((void**)&w->gin, sizeof(double) * len));
     IBIM_CUDA(cudaMalloc((void**)&w->part, sizeof(double) * (size_t)w->nblk * (kMaxRestart + 1)));
     IBIM_CUDA(cudaMalloc((void**)&w->st, sizeof(GmState)));
     IBIM_CUDA(cudaMallocHost((void**)&w->h_st, sizeof(GmState)));
@@ -367,15 +381,16 @@ ibim_status gm_init(ibim_ctx* c, const ibim_phys& p, int m, double* gnorm)
     return IBIM_OK;
 }
 
-// r = g - A_out x (or r = g when x is known to be zero); starts a cycle on r.
-static ibim_status begin_cycle(ibim_ctx* c, const PairConsts& k, int prec_out, bool x_zero, double target,
-                               int kmax, double* beta_host)
+// r = rhs - A x with the operator of precision `prec` (or r = rhs when x is
+// known to be zero); starts a cycle on r.
+static ibim_status begin_cycle(ibim_ctx* c, const PairConsts& k, int prec, const double* rhs, bool x_zero,
+                               double target, int kmax, double* beta_host)
 {
     GmresWork* w = c->gm;
     const int64_t len = w->len;
     if (!x_zero)
-        IBIM_TRY(apply_operator(c, k, prec_out, VecRef{w->x, nullptr, 0, 0}, OutRef{w->t, nullptr, 0, 0}, nullptr));
-    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->g, x_zero ? nullptr : w->t, w->r, len, w->part);
+        IBIM_TRY(apply_operator(c, k, prec, VecRef{w->x, nullptr, 0, 0}, OutRef{w->t, nullptr, 0, 0}, nullptr));
+    residual_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(rhs, x_zero ? nullptr : w->t, w->r, len, w->part);
     cycle_begin_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, target, kmax);
     cycle_begin_scale_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->r, w->V, len, w->st);
     count_launch(c, 3);
@@ -542,17 +557,28 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
     }
     // Restart residuals use the iteration's operator; with certification the
     // residual is recomputed with the FP64-accurate operator once the iteration's
-    // residual meets the inner target (or the iteration budget is spent), and
-    // a failed check restarts from that FP64 residual (iterative refinement).
-    bool check = false;
+    // residual meets the inner target (or the iteration budget is spent).  A
+    // failed check starts a solve of the correction equation on that residual:
+    // xb keeps the iterate, x the correction from zero, gin the residual, and
+    // restarts compute gin - A_in x until the next check adds xb back.  (Restart
+    // residuals g - A_in x of the whole system would pull the iterate back to
+    // A_in's own solution, which misses the tolerance whenever A_in differs
+    // from A_out by more than the inner target, e.g. a treecode operator.)
+    bool check = false, refining = false;
     while (!converged) {
         const int kmax = std::min(m, o.maxit - iters);
         const int prec_r = (check || kmax <= 0) ? prec_out : prec_in;
+        if (prec_r == prec_out && refining) {
+            add_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->x, w->xb, len);
+            count_launch(c);
+            refining = false;
+        }
         if (!x_zero) {
             if (prec_r == IBIM_F32C || prec_r == IBIM_F32T) info->matvecs_f32 += 1;
             else info->matvecs_f64 += 1;
         }
-        IBIM_TRY(begin_cycle(c, k, prec_r, x_zero, inner_target, std::max(kmax, 0), &beta));
+        IBIM_TRY(begin_cycle(c, k, prec_r, refining ? w->gin : w->g, x_zero, inner_target, std::max(kmax, 0),
+                             &beta));
         x_zero = false;
         if (prec_r == prec_out && beta <= target_abs) {
             converged = true;
@@ -564,6 +590,12 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         }
         check = false;
         if (kmax <= 0) break;
+        if (prec_r != prec_in) {  // failed check: the cycle below starts on r = g - A_out x
+            IBIM_CUDA(cudaMemcpyAsync(w->xb, w->x, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+            IBIM_CUDA(cudaMemcpyAsync(w->gin, w->r, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+            IBIM_CUDA(cudaMemsetAsync(w->x, 0, sizeof(double) * len, c->stream));
+            refining = true;
+        }
         if (use_graph) IBIM_TRY(capture_step(c, k, prec_in));
         int steps = 0, conv = 0;
         IBIM_TRY(run_cycle(c, k, prec_in, use_graph, &steps, &conv));

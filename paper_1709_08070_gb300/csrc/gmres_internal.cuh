@@ -33,6 +33,8 @@ struct GmresWork {
     double* r = nullptr;       // len: residual / scratch
     double* t = nullptr;       // len: operator output scratch
     double* g = nullptr;       // len: right-hand side
+    double* xb = nullptr;      // len: refinement base iterate (x holds the correction to it)
+    double* gin = nullptr;     // len: refinement right-hand side (residual at xb)
     double* part = nullptr;    // per-block partial sums ((m + 1) x nblk)
     int nblk = 0;
     GmState* st = nullptr;     // device state

@@ -132,6 +132,24 @@ def test_treecode_on_built_sphere_operator_and_solve(interp):
     i32 = ctx.solve(P, d, precision=ibim.IBIM_F32C, certify=0, **opts)
     print("G_pol treecode %.10f direct %.10f (iterations %d, %d)" % (it["gpol"], i32["gpol"], it["iters"], i32["iters"]))
     assert it["converged"] and abs(it["gpol"] - i32["gpol"]) < 1e-6 * abs(i32["gpol"])
+    # Certified treecode solves: the treecode's approximation error (about
+    # 5e-7 here) is close to the inner target, so the refinement must solve the
+    # correction equation and not fall back to the treecode's own solution.
+    # The reported residual is checked against g - A x with the direct FP64
+    # operator.
+    g = torch.empty_like(d)
+    ctx.rhs(P.eps_in, g)
+    gn = float(torch.linalg.norm(g))
+    for certify in (1, 2):
+        ic = ctx.solve(P, d, precision=ibim.IBIM_F32T, certify=certify, tol=1e-6, restart=64, maxit=400)
+        ctx.matvec(P, d, y64, precision=ibim.IBIM_F64)
+        res = float(torch.linalg.norm(g - y64)) / gn
+        print("certified treecode solve (certify %d): iterations %d, cycles %d, FP64-accurate applications %d, "
+              "reported %.6e, direct FP64 %.6e" % (certify, ic["iters"], ic["cycles"], ic["matvecs_f64"],
+                                                     ic["relres"], res))
+        assert ic["converged"] and res < 1e-6 and abs(ic["relres"] - res) <= 1e-9
+        assert ic["matvecs_f64"] <= 4 and ic["iters"] <= 3 * it["iters"]
+        assert abs(ic["gpol"] - i32["gpol"]) < 2e-6 * abs(i32["gpol"])
     ctx.close()
 
 
