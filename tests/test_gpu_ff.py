@@ -170,3 +170,37 @@ def test_certified_solve_reports_the_oracle_residual():
         assert np.max(np.abs(sols[0] - sols[1])) <= 1e-6 * np.max(np.abs(sols[1]))
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10])
+def test_certified_solve_below_the_fp32_accuracy(tol):
+    """Born sphere, FP32 GMRES certified to tolerances at and below the FP32
+    operator's own accuracy (about 1e-8 of |A p|): the refinement on the
+    correction equation reaches them, and the reported residual is the
+    oracle's residual of the returned vector."""
+    R, h = 2.0, 0.25
+    ctx = ibim.Context.sphere(R, h=h, band_eps=3 * h)
+    try:
+        g = oracle.sphere_nodes(R, h=h, eps=3 * h)
+        perm = _match(ctx.nodes()["ijk"], g["ijk"])
+        N = ctx.N
+        z, q = np.array([[0.2, -0.1, 0.3]]), np.array([1.0])
+        ctx.set_charges(z, q)
+        P = ibim.Phys(1.0, 80.0, 0.1257, h, 0)
+        Po = oracle.Phys(1.0, 80.0, 0.1257, h, 0)
+        b = oracle.rhs(g["xs"], g["nrm"], z, q, 1.0)
+        d = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        info = ctx.solve(P, d, precision=ibim.IBIM_F32C, tol=tol, restart=64, maxit=400, certify=1)
+        x = d.cpu().numpy()
+        xo = np.empty_like(x)
+        xo[:N][perm] = x[:N]
+        xo[N:][perm] = x[N:]
+        r = b - oracle.matvec(g["xs"], g["nrm"], g["w"], Po, xo)
+        res = np.linalg.norm(r) / np.linalg.norm(b)
+        print("tol %g: iterations %d, cycles %d, FP64-accurate applications %d, reported %.6e, oracle %.6e"
+              % (tol, info["iters"], info["cycles"], info["matvecs_f64"], info["relres"], res))
+        assert info["converged"] and res < tol
+        assert abs(info["relres"] - res) <= 1e-11
+        assert info["iters"] <= 150 and info["matvecs_f64"] <= 6
+    finally:
+        ctx.close()
