@@ -236,9 +236,15 @@ typedef struct {
  * as one CUDA graph replay with no host synchronisation inside the step.
  * The symmetric FP32 kernels vary from one application to the next by about
  * 1e-8 of |A p| (their reverse sums are added in a varying order), which is
- * the floor of a restart residual computed with them; an IBIM_F32C solve with
- * tol below 1e-7 therefore runs the one-directional FP32 kernel (the
- * context's variant is restored afterwards).
+ * the floor of a restart residual computed with them; an uncertified
+ * IBIM_F32C solve with tol below 1e-7 therefore runs the one-directional FP32
+ * kernel (the context's variant is restored afterwards).  Certified solves
+ * (opts->certify > 0) keep the context's variant at any tol: after the first
+ * FP64-accurate residual misses tol, the iteration solves the correction
+ * equation A e = r from e = 0 (restart residuals r - A e, noise relative to
+ * |r|) and adds e before the next check (iterative refinement).  A cycle that
+ * converges by its own estimate while the restart residual does not (the FP32
+ * operator's accuracy, about 1e-8 of |A p|) leads to the check at once.
  * d_p: device 2N doubles; start vector on entry when opts->start == 3,
  * solution [psi; psin] on exit.  Needs charges.  Returns IBIM_ERR_NOT_CONVERGED
  * (info filled) when maxit is reached above tol.

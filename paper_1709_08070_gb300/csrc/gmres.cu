@@ -484,8 +484,11 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
     const int prec_in = o.precision;
     // The symmetric FP32 kernels add their reverse sums in a varying order, so
     // two applications to the same vector differ by about 1e-8 of |A p|; a
-    // restart residual then cannot settle below that.  Solves asked for a
-    // tighter tolerance run the one-directional kernel instead (restored on exit).
+    // restart residual then cannot settle below that.  Uncertified solves asked
+    // for a tighter tolerance run the one-directional kernel instead (restored
+    // on exit).  Certified solves keep the symmetric kernel: once the first
+    // check fails, the inner solves work on the correction equation, whose
+    // right-hand side is the current residual, so the noise scales with it.
     struct KeepVariant {
         ibim_ctx* c;
         int v, b;
@@ -495,7 +498,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
             c->f32_bps = b;
         }
     } keep_variant{c, c->f32_variant, c->f32_bps};
-    if (prec_in == IBIM_F32C && o.tol < kSymTolFloor && f32_variant_symmetric(c->f32_variant)) {
+    if (prec_in == IBIM_F32C && o.certify == 0 && o.tol < kSymTolFloor && f32_variant_symmetric(c->f32_variant)) {
         c->f32_variant = f32_deterministic_variant();
         c->f32_bps = 0;
     }
