@@ -57,16 +57,23 @@ __global__ void __launch_bounds__(kVecThreads)
     }
 }
 
-// coef[j] = sum_b part[b][j]; hcol[j] (+)= coef[j]  (pass 0 sets, pass 1 adds)
-__global__ void gs_reduce_kernel(const double* __restrict__ part, int nblk, GmState* __restrict__ st, int pass)
+// coef[j] = sum_b part[b][j]; hcol[j] (+)= coef[j]  (pass 0 sets, pass 1 adds).
+// One warp per coefficient: lane l sums blocks l, l + 32, ..., then a fixed
+// butterfly (the same order every time, so the step is deterministic).
+__global__ void __launch_bounds__(256)
+    gs_reduce_kernel(const double* __restrict__ part, int nblk, GmState* __restrict__ st, int pass)
 {
     if (st->done) return;
     const int k = st->k;
-    for (int j = threadIdx.x; j <= k; j += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x >> 5; j <= k; j += nw) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * (kMaxRestart + 1) + j];
-        st->coef[j] = s;
-        st->hcol[j] = (pass == 0) ? s : st->hcol[j] + s;
+        for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * (kMaxRestart + 1) + j];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            st->coef[j] = s;
+            st->hcol[j] = (pass == 0) ? s : st->hcol[j] + s;
+        }
     }
 }
 
@@ -312,7 +319,7 @@ ibim_status gm_ortho(ibim_ctx* c)
     const int64_t len = w->len;
     for (int pass = 0; pass < 2; ++pass) {
         gs_dots_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st, w->part);
-        gs_reduce_kernel<<<1, 128, 0, c->stream>>>(w->part, w->nblk, w->st, pass);
+        gs_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st, pass);
         gs_update_kernel<<<w->nblk, kVecThreads, 0, c->stream>>>(w->V, len, w->st, w->part, pass == 1);
     }
     norm_reduce_kernel<<<1, 256, 0, c->stream>>>(w->part, w->nblk, w->st);

@@ -58,7 +58,7 @@
 namespace ibim {
 
 
-template <int TPT, int MINB, int THREADS, bool ROT>
+template <int TPT, int MINB, int THREADS, bool ROT, int UNR>
 __global__ void __launch_bounds__(THREADS, MINB)
     pair_sym_kernel(const float4* __restrict__ tpos, const float4* __restrict__ tnrm,
                     const float4* __restrict__ src, const float4* __restrict__ frames, int64_t N, int64_t n_pad,
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
             for (int q = 0; q < TPT; ++q) S1[q] = C1[q] = S2[q] = C2[q] = 0.0f;
             if (!idle)
-                tile_sums_sym<TPT, ROT>(T, &tfrm[warp][0], stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64, gi0,
+                tile_sums_sym<TPT, ROT, UNR>(T, &tfrm[warp][0], stg[stage].buf, stg[stage].frm, k, S1, C1, S2, C2, g64, gi0,
                                    THREADS, st * kF32STile, N, Ablk, st * kChunksPerTile, &racc[stage][0]);
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -341,10 +341,10 @@ struct SymArgs {
     Geo64 g64;
 };
 
-template <int TPT, int MINB, int THREADS, bool ROT>
+template <int TPT, int MINB, int THREADS, bool ROT, int UNR>
 static void launch_sym(const SymArgs& a, cudaStream_t st)
 {
-    pair_sym_kernel<TPT, MINB, THREADS, ROT><<<a.s.grid, THREADS, 0, st>>>(
+    pair_sym_kernel<TPT, MINB, THREADS, ROT, UNR><<<a.s.grid, THREADS, 0, st>>>(
         a.tpos, a.tnrm, a.src, a.frames, a.N, a.n_pad, a.s, a.k, a.part, a.yrev, a.err, a.skip, a.g64);
 }
 
@@ -354,11 +354,11 @@ struct SymVariant {
     const void* fn;
     void (*launch)(const SymArgs&, cudaStream_t);
 };
-#define IBIM_SYM_VARIANT(T, M, W, R) \
-    {T, M, W, (R) ? 2 : 1, (const void*)pair_sym_kernel<T, M, W, R>, launch_sym<T, M, W, R>}
+#define IBIM_SYM_VARIANT(T, M, W, R, U) \
+    {T, M, W, (R) ? 2 : 1, (const void*)pair_sym_kernel<T, M, W, R, U>, launch_sym<T, M, W, R, U>}
 static const SymVariant kSymVariants[] = {
-    IBIM_SYM_VARIANT(2, 1, 512, false), IBIM_SYM_VARIANT(1, 1, 512, false),
-    IBIM_SYM_VARIANT(2, 1, 512, true), IBIM_SYM_VARIANT(1, 1, 512, true),
+    IBIM_SYM_VARIANT(2, 1, 512, false, 2), IBIM_SYM_VARIANT(1, 1, 512, false, 2),
+    IBIM_SYM_VARIANT(2, 1, 512, true, 1), IBIM_SYM_VARIANT(1, 1, 512, true, 4),
 };
 #undef IBIM_SYM_VARIANT
 constexpr int kNumSymVariants = (int)(sizeof(kSymVariants) / sizeof(kSymVariants[0]));

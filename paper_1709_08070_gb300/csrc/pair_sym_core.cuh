@@ -354,7 +354,10 @@ __device__ __forceinline__ void warp_sum4_add(float v0, float v1, float v2, floa
 // tile's first chunk.  Forward sums go to the compensated pairs (S, C);
 // reverse sums of every source of the tile go to racc[.] (first block) and
 // racc[sym_rev_off(ROT) + .] (second block) by shared-memory atomics.
-template <int TPT, bool ROT>
+// UNR: unroll depth of the rotation loop.  Measured on the 80k-node sphere:
+// two targets per thread run fastest at 1 (5.65 ms; 5.72 at 2, spills at 4),
+// one target per thread at 4 (5.86 ms; 6.11 at 2, 6.22 at 1).
+template <int TPT, bool ROT, int UNR = 2>
 __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const float4* tfrm, const float4* sb,
                                               const float4* sfrm, const F32Consts& k, float (&S1)[TPT],
                                               float (&C1)[TPT], float (&S2)[TPT], float (&C2)[TPT],
@@ -419,7 +422,7 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                 const int hl = lane & (P - 1);
                 const int nxt = (hl + 1) & (P - 1);
                 float2 nR1 = make_float2(0.0f, 0.0f), R2 = make_float2(0.0f, 0.0f);
-#pragma unroll 2
+#pragma unroll UNR
                 for (int step = 0; step < P; ++step) {
                     const int p = (hl + step) & (P - 1);
                     const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
