@@ -804,6 +804,7 @@ def run_batched(args):
     physs = [ibim.Phys(1.0, 80.0, float(kappas[m]), 0.5, 0) for m in mine]
     outs = [torch.empty(2 * n, dtype=torch.float64, device="cuda") for n in Ns]
     opts = dict(precision=ibim.IBIM_F32C, tol=1e-6, restart=64, maxit=args.batch_rounds, allow_not_converged=True)
+    ibim.ibim_set_batch_variant(args.batch_variant)
     for _ in range(max(1, args.warmup - 2)):
         ibim.ibim_solve_batch(ctxs, physs, outs, **dict(opts, maxit=2))
     stream = torch.cuda.current_stream()
@@ -1039,6 +1040,8 @@ def main():
     ap.add_argument("--batch-rounds", type=int, default=4000,
                     help="with --workload batched: cap on lock-step GMRES rounds (the default lets every molecule "
                          "converge)")
+    ap.add_argument("--batch-variant", type=int, default=-1,
+                    help="with --workload batched: force this batched pair-kernel variant (-1: the first-round tuning)")
     ap.add_argument("--learn-train", type=int, default=2000)
     ap.add_argument("--learn-train-lo", type=int, default=100)
     ap.add_argument("--learn-train-hi", type=int, default=1000)
