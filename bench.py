@@ -670,8 +670,8 @@ def run_treecode(args):
     with the treecode operator (IBIM_F32T, theta 0.7, target-side
     interpolation of the well-separated far clusters): timed applications, the
     direct FP32 operator timed beside it, the operator difference, and one FP32
-    solve to 1e-6 with each operator (energies against each other and against
-    the Kirkwood series).  value = N^2 x applications / time: the interactions
+    solve to 1e-6 with each operator, plain and certified (energies against each
+    other and against the Kirkwood series).  value = N^2 x applications / time: the interactions
     of the operator the treecode approximates; pairs_per_s counts the pair
     evaluations the treecode actually performs."""
     import torch
@@ -753,12 +753,15 @@ def run_treecode(args):
                        "converged": finf["converged"], "gpol_kcal": finf["gpol_kcal"],
                        "gpol_rel_err_vs_series": (finf["gpol_kcal"] - Gs) / Gs if Gs else None})
     ctx.treecode_setup(W["theta"], W["tau_k"] * h, W["target_interp"], W["order"])
-    for name, prec in (("treecode", ibim.IBIM_F32T), ("direct_f32", ibim.IBIM_F32C)):
+    # plain FP32 solves, then certified ones (float-float residual check, refinement)
+    for name, prec, cert in (("treecode", ibim.IBIM_F32T, 0), ("direct_f32", ibim.IBIM_F32C, 0),
+                             ("treecode_certified", ibim.IBIM_F32T, 1), ("direct_f32_certified", ibim.IBIM_F32C, 1)):
         t0 = time.perf_counter()
-        info = ctx.solve(P, d, precision=prec, tol=W["tol"], restart=W["restart"], maxit=1000, certify=0)
+        info = ctx.solve(P, d, precision=prec, tol=W["tol"], restart=W["restart"], maxit=1000, certify=cert)
         torch.cuda.synchronize()
         solves[name] = {"s": time.perf_counter() - t0, "iters": info["iters"], "relres": info["relres"],
-                        "converged": info["converged"], "gpol_kcal": info["gpol_kcal"]}
+                        "converged": info["converged"], "gpol_kcal": info["gpol_kcal"],
+                        "fp64_accurate_applications": info["matvecs_f64"]}
     gt, gd = solves["treecode"]["gpol_kcal"], solves["direct_f32"]["gpol_kcal"]
     extra = {"clocks": ck, "geometry_build_s": build_s, "treecode_setup_s": setup_s,
              "treecode": dict(tinfo, theta=W["theta"], chebyshev_points_per_axis=W["order"], pairs_per_application=pairs,
@@ -767,6 +770,7 @@ def run_treecode(args):
              "direct_f32_ms": direct_ms, "speedup_per_application": direct_ms / float(np.mean(ms)),
              "operator_rel_err_vs_direct_f32": op_err, "solves": solves,
              "speedup_solve": solves["direct_f32"]["s"] / solves["treecode"]["s"],
+             "speedup_certified_solve": solves["direct_f32_certified"]["s"] / solves["treecode_certified"]["s"],
              "gpol_rel_diff_treecode_vs_direct": abs(gt - gd) / abs(gd), "kirkwood_series_kcal": Gs,
              "gpol_rel_err_vs_series": {"treecode": (gt - Gs) / Gs, "direct_f32": (gd - Gs) / Gs},
              "fast_setting": fast}
