@@ -4,7 +4,10 @@
 // The pair geometry (r, |r|, e^{-kappa rho}, g, 3 - B, rho^-3, the theta
 // terms) is the same for the ordered pairs (i <- j) and (j <- i), so one
 // evaluation of an unordered pair gives both contributions: 48 FP32
-// lane-operations per pair (28 shared, 10 per direction) instead of 2 x 36.  Each aligned 32-node block pair
+// lane-operations per pair instead of 2 x 36 (28 shared and 10 per direction
+// in pair_far_sym; 36 shared and 6 per direction in the rotation scheme's
+// pair_far_sym_acc, which forms the factors common to both directions
+// once).  Each aligned 32-node block pair
 // (A, B) is evaluated once: by the warp holding target block A when B > A
 // (both directions), B == A gives the forward direction only (it holds the
 // self pairs), and B < A is skipped (the warp holding B covered it).
@@ -51,6 +54,8 @@
 //     FMAs); after 16 steps each lane holds one pair's sums over its
 //     half-warp, the two halves are added and 16 + 16 lanes add them to the
 //     shared buffer.  Near chunks use the warp reduction in both schemes.
+//     The rotation loop's unroll depth is a variant parameter too (see
+//     tile_sums_sym).
 #include <algorithm>
 
 #include "pair_sym_core.cuh"
