@@ -53,9 +53,11 @@
 //     shuffle per value and step, the adds folded into the pair formula's
 //     FMAs); after 16 steps each lane holds one pair's sums over its
 //     half-warp, the two halves are added and 16 + 16 lanes add them to the
-//     shared buffer.  Near chunks use the warp reduction in both schemes.
-//     The rotation loop's unroll depth is a variant parameter too (see
-//     tile_sums_sym).
+//     shared buffer.  Near chunks take the same walk with the packed near
+//     formula (pair_near_sym_acc: series g, both directions' tube tests as
+//     per-lane selects); the warp-reduction scheme evaluates them with the
+//     scalar near path.  The rotation loop's unroll depth is a variant
+//     parameter too (see tile_sums_sym).
 #include <algorithm>
 
 #include "pair_sym_core.cuh"

@@ -220,6 +220,108 @@ __device__ __forceinline__ void pair_far_sym_acc(float2 Xx, float2 Xy, float2 Xz
     R2 = __ffma2_rn(Pgc, ai, R2);
 }
 
+// Near pairs in the rotation scheme, both directions, packed over the two
+// sources of a payload pair: pair_far_sym_acc's formula with, per lane, g
+// from its series where kappa rho < 0.5 (f = 1 - E = g + E x there), as in
+// near_one, and each direction's tube test (Sec. 2.2.1: rho_P^2 on the
+// target's tangent plane forward, on the source's in reverse).  A
+// regularised direction keeps only K12's tube value: selects zero its a
+// weight and the b weight of its second sum and put the tube value in place
+// of its 1/rho factor, so the products with the powers of 1/rho stay shared.
+// rho^2 is kept >= 1e-12, so that coincident nodes (the self pair among
+// them, always in the tube) leave every product finite.  When any of the
+// four tests lies within kTieBand of a threshold, all four are decided again
+// in FP64 (tube_f64), which the FP32 tests agree with outside the band.
+// i: the target's node index, j: the first source's.
+__device__ __forceinline__ void pair_near_sym_acc(float2 Xx, float2 Xy, float2 Xz, float2 nx, float2 ny, float2 nz,
+                                                  float2 ai, float2 nbi, const float4& A, const float4& B,
+                                                  const float4& C, const float4& D, const FarConsts& c,
+                                                  const F32Consts& k, float2& t1, float2& t2, float2& nR1,
+                                                  float2& R2, const Geo64& g64, int64_t i, int64_t j, int64_t N)
+{
+    const float2 rx = __fadd2_rn(Xx, make_float2(A.x, A.y));
+    const float2 ry = __fadd2_rn(Xy, make_float2(A.z, A.w));
+    const float2 rz = __fadd2_rn(Xz, make_float2(B.x, B.y));
+    const float2 bj = make_float2(B.z, B.w);
+    const float2 mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w), mz = make_float2(D.x, D.y);
+    const float2 aj = make_float2(D.z, D.w);
+    float2 rr = __fmul2_rn(rx, rx);
+    rr = __ffma2_rn(ry, ry, rr);
+    rr = __ffma2_rn(rz, rz, rr);
+    float2 sx = __fmul2_rn(rx, nx);
+    sx = __ffma2_rn(ry, ny, sx);
+    sx = __ffma2_rn(rz, nz, sx);
+    float2 sy = __fmul2_rn(rx, mx);
+    sy = __ffma2_rn(ry, my, sy);
+    sy = __ffma2_rn(rz, mz, sy);
+    float2 cc = __fmul2_rn(nx, mx);
+    cc = __ffma2_rn(ny, my, cc);
+    cc = __ffma2_rn(nz, mz, cc);
+    // tube tests: forward (f) on rho^2 - s_x^2, reverse (r) on rho^2 - s_y^2
+    const float2 rpf = __ffma2_rn(__fmul2_rn(sx, c.neg1), sx, rr);
+    const float2 rpr = __ffma2_rn(__fmul2_rn(sy, c.neg1), sy, rr);
+    const bool in0 = rr.x < k.four_tau2, in1 = rr.y < k.four_tau2;
+    bool tf0 = (rpf.x < k.tau2) & in0, tf1 = (rpf.y < k.tau2) & in1;
+    bool tr0 = (rpr.x < k.tau2) & in0, tr1 = (rpr.y < k.tau2) & in1;
+    const float bt = kTieBand * k.tau2, b4 = kTieBand * k.four_tau2;
+    const bool tie = (fabsf(rpf.x - k.tau2) < bt) | (fabsf(rpf.y - k.tau2) < bt) | (fabsf(rpr.x - k.tau2) < bt) |
+                     (fabsf(rpr.y - k.tau2) < bt) | (fabsf(rr.x - k.four_tau2) < b4) |
+                     (fabsf(rr.y - k.four_tau2) < b4);
+    if (tie && g64.x != nullptr && i < N) {
+        if (j < N) {
+            tf0 = tube_f64(g64, i, j, k.tau2_d, k.four_tau2_d);
+            tr0 = tube_f64(g64, j, i, k.tau2_d, k.four_tau2_d);
+        }
+        if (j + 1 < N) {
+            tf1 = tube_f64(g64, i, j + 1, k.tau2_d, k.four_tau2_d);
+            tr1 = tube_f64(g64, j + 1, i, k.tau2_d, k.four_tau2_d);
+        }
+    }
+    const float2 rrs = make_float2(fmaxf(rr.x, 1.0e-12f), fmaxf(rr.y, 1.0e-12f));
+    const float2 inv = make_float2(ptx::rsqrt_approx(rrs.x), ptx::rsqrt_approx(rrs.y));
+    const float2 rho = __fmul2_rn(rrs, inv);
+    const float2 ea = __fmul2_rn(rho, c.kl2e);
+    const float2 xn = __fmul2_rn(rho, c.nkappa);
+    const float2 E = make_float2(ptx::ex2_approx(ea.x), ptx::ex2_approx(ea.y));
+    const float2 En = __fmul2_rn(E, xn);
+    float2 fn = __fadd2_rn(E, c.neg1);
+    float2 g = __ffma2_rn(fn, c.neg1, En);
+    if (-xn.x < 0.5f) {  // kappa rho < 0.5: series of g, fn = -(g + E x)
+        g.x = g_series(-xn.x);
+        fn.x = En.x - g.x;
+    }
+    if (-xn.y < 0.5f) {
+        g.y = g_series(-xn.y);
+        fn.y = En.y - g.y;
+    }
+    const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));
+    const float2 inv2 = __fmul2_rn(inv, inv);
+    const float2 P = __fmul2_rn(inv2, inv);
+    const float2 Pu1 = __fmul2_rn(P, __ffma2_rn(c.th1, g, c.omth1));
+    const float2 Pu2 = __fmul2_rn(P, __ffma2_rn(c.th2, g, c.omth2));
+    const float2 Pgc = __fmul2_rn(__fmul2_rn(P, g), cc);
+    const float2 Phi = __fmul2_rn(hn, __fmul2_rn(inv2, P));
+    const float2 qf = __fmul2_rn(fn, inv);
+    // forward; a regularised pair adds -K12_tube b only
+    const float2 ajf = make_float2(tf0 ? 0.0f : aj.x, tf1 ? 0.0f : aj.y);
+    const float2 bjt = make_float2(tf0 ? 0.0f : bj.x, tf1 ? 0.0f : bj.y);
+    const float2 qff = make_float2(tf0 ? -k.k12t : qf.x, tf1 ? -k.k12t : qf.y);
+    const float2 sa = __fmul2_rn(ajf, sy);
+    t1 = __ffma2_rn(Pu1, sa, t1);
+    t1 = __ffma2_rn(qff, bj, t1);
+    t2 = __ffma2_rn(sx, __ffma2_rn(Phi, sa, __fmul2_rn(Pu2, bjt)), t2);
+    t2 = __ffma2_rn(Pgc, ajf, t2);
+    // reverse, accumulated (nbi = -b_i)
+    const float2 air = make_float2(tr0 ? 0.0f : ai.x, tr1 ? 0.0f : ai.y);
+    const float2 nbt = make_float2(tr0 ? 0.0f : nbi.x, tr1 ? 0.0f : nbi.y);
+    const float2 qfr = make_float2(tr0 ? -k.k12t : qf.x, tr1 ? -k.k12t : qf.y);
+    const float2 psa = __fmul2_rn(air, sx);
+    nR1 = __ffma2_rn(Pu1, psa, nR1);
+    nR1 = __ffma2_rn(qfr, nbi, nR1);
+    R2 = __ffma2_rn(sy, __ffma2_rn(Phi, psa, __fmul2_rn(Pu2, nbt)), R2);
+    R2 = __ffma2_rn(Pgc, air, R2);
+}
+
 // One ordered near pair (target <- source), scalar: tube test on the target's
 // normal (FP64 re-decision of near-ties), series g when `series`.
 // r = target - source; s_x = r . n_target, s_y = r . m_source, c = n . m.
@@ -353,8 +455,10 @@ __device__ __forceinline__ void warp_sum4_add(float v0, float v1, float v2, floa
 // Ablk[q]: chunk index of target slot q's block; B0: chunk index of the
 // tile's first chunk.  Forward sums go to the compensated pairs (S, C);
 // reverse sums of every source of the tile go to racc[.] (first block) and
-// racc[sym_rev_off(ROT) + .] (second block) by shared-memory atomics.
-// UNR: unroll depth of the rotation loop.  Measured on the 80k-node sphere:
+// racc[sym_rev_off(ROT) + .] (second block) by shared-memory atomics.  ROT:
+// the rotation scheme, far chunks by pair_far_sym_acc and near chunks by
+// pair_near_sym_acc; otherwise the warp reduction, near chunks by the scalar
+// near_pair_sym.  UNR: unroll depth of the rotation loop.  Measured on the 80k-node sphere:
 // two targets per thread run fastest at 1 (5.65 ms; 5.72 at 2, spills at 4),
 // one target per thread at 4 (5.86 ms; 6.11 at 2, 6.22 at 1).
 template <int TPT, bool ROT, int UNR = 2>
@@ -403,7 +507,7 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
         const float4* cb = sb + c * P * kPairF4;
         float* ra = racc + c * kChunk;
         float* rb = racc + sym_rev_off(ROT) + c * kChunk;
-        if (far) {
+        if (far || ROT) {  // the rotation scheme takes near chunks too (pair_near_sym_acc)
             float2 Xx[TPT], Xy[TPT], Xz[TPT];
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -422,19 +526,37 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                 const int hl = lane & (P - 1);
                 const int nxt = (hl + 1) & (P - 1);
                 float2 nR1 = make_float2(0.0f, 0.0f), R2 = make_float2(0.0f, 0.0f);
+                if (far) {
 #pragma unroll UNR
-                for (int step = 0; step < P; ++step) {
-                    const int p = (hl + step) & (P - 1);
-                    const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
+                    for (int step = 0; step < P; ++step) {
+                        const int p = (hl + step) & (P - 1);
+                        const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
 #pragma unroll
-                    for (int q = 0; q < TPT; ++q)
-                        pair_far_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B, C, D,
-                                         fc, t1[q], t2[q], nR1, R2);
-                    // pair p goes to lane hl - 1 at the next step: its sums follow it
-                    nR1.x = __shfl_sync(0xffffffffu, nR1.x, nxt, P);
-                    nR1.y = __shfl_sync(0xffffffffu, nR1.y, nxt, P);
-                    R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
-                    R2.y = __shfl_sync(0xffffffffu, R2.y, nxt, P);
+                        for (int q = 0; q < TPT; ++q)
+                            pair_far_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B, C,
+                                             D, fc, t1[q], t2[q], nR1, R2);
+                        // pair p goes to lane hl - 1 at the next step: its sums follow it
+                        nR1.x = __shfl_sync(0xffffffffu, nR1.x, nxt, P);
+                        nR1.y = __shfl_sync(0xffffffffu, nR1.y, nxt, P);
+                        R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
+                        R2.y = __shfl_sync(0xffffffffu, R2.y, nxt, P);
+                    }
+                } else {
+                    const int64_t jc = j0 + (int64_t)c * kChunk;
+#pragma unroll 1
+                    for (int step = 0; step < P; ++step) {
+                        const int p = (hl + step) & (P - 1);
+                        const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
+#pragma unroll
+                        for (int q = 0; q < TPT; ++q)
+                            pair_near_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B,
+                                              C, D, fc, k, t1[q], t2[q], nR1, R2, g64, gi0 + (int64_t)q * qstride,
+                                              jc + 2 * p, N);
+                        nR1.x = __shfl_sync(0xffffffffu, nR1.x, nxt, P);
+                        nR1.y = __shfl_sync(0xffffffffu, nR1.y, nxt, P);
+                        R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
+                        R2.y = __shfl_sync(0xffffffffu, R2.y, nxt, P);
+                    }
                 }
                 // lane hl holds pair hl's sums over its half-warp; add the other half's
                 nR1.x += __shfl_xor_sync(0xffffffffu, nR1.x, P);

@@ -14,9 +14,10 @@ launch configuration the benchmark times -- and at one CTA per SM) and below
 FP32 solves.  A few rows decided wrongly at the tube
 boundary would pass a 2-norm over tens of thousands of rows but not this.
 
-Cases: every row of the Born sphere (R = 2, h = 0.25, band 3h) and of a
-small level-set globule (14 atoms, about 4.5k nodes) at kappa = 0.1257 and
-kappa = 0; 2,048 seeded rows of the 80k-node Kirkwood sphere.  (The
+Cases: every row of the Born sphere (R = 2, h = 0.25, band 3h) at kappa =
+0.1257 and 0 and with tube rule 1 at kappa = 0.2, and of a small level-set
+globule (14 atoms, about 4.5k nodes) at kappa = 0.1257 and kappa = 0; 2,048
+seeded rows of the 80k-node Kirkwood sphere.  (The
 2,000-atom and 10,000-atom globules are in test_gpu_levelset.py.)
 """
 import numpy as np
@@ -82,28 +83,30 @@ def _run_all(ctx, P, p_gpu, check):
         check(y, prec, "prec %d variant %s ctas/SM %d" % (prec, v, bps))
 
 
-def _all_rows(ctx, xs, nrm, w, perm, kappa, eps_in, tau, seed):
+def _all_rows(ctx, xs, nrm, w, perm, kappa, eps_in, tau, seed, rule=0):
     N = ctx.N
-    P = ibim.Phys(eps_in, 80.0, kappa, tau, 0)
-    Po = oracle.Phys(eps_in, 80.0, kappa, tau, 0)
+    P = ibim.Phys(eps_in, 80.0, kappa, tau, rule)
+    Po = oracle.Phys(eps_in, 80.0, kappa, tau, rule)
     p = inputs.random_vector(2 * N, seed=seed)
     yo = oracle.matvec(xs, nrm, w, Po, p)
     yo_g = _to_gpu(yo, perm, N)
 
     def check(y, prec, what):
-        _assert_blocks(y[:N], y[N:], yo_g[:N], yo_g[N:], TOL[prec], "N %d kappa %g %s" % (N, kappa, what))
+        _assert_blocks(y[:N], y[N:], yo_g[:N], yo_g[N:], TOL[prec], "N %d kappa %g rule %d %s" % (N, kappa, rule, what))
 
     _run_all(ctx, P, _to_gpu(p, perm, N), check)
 
 
-@pytest.mark.parametrize("kappa", [0.1257, 0.0])
-def test_born_sphere_every_row_every_variant(kappa):
+@pytest.mark.parametrize("kappa,rule", [(0.1257, 0), (0.0, 0), (0.2, 1)])
+def test_born_sphere_every_row_every_variant(kappa, rule):
+    """Rule 1 (the literal tangent-plane test, unbounded in distance) sends
+    every chunk pair through the near path."""
     R, h = 2.0, 0.25
     ctx = ibim.Context.sphere(R, h=h, band_eps=3 * h)
     try:
         g = oracle.sphere_nodes(R, h=h, eps=3 * h)
         perm = _match(ctx.nodes()["ijk"], g["ijk"])
-        _all_rows(ctx, g["xs"], g["nrm"], g["w"], perm, kappa, 1.0, h, seed=51)
+        _all_rows(ctx, g["xs"], g["nrm"], g["w"], perm, kappa, 1.0, h, seed=51, rule=rule)
     finally:
         ctx.close()
 
