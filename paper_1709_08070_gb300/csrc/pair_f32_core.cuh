@@ -190,78 +190,77 @@ static __device__ __noinline__ bool tube_f64(const Geo64& g, int64_t i, int64_t 
 // FP32 tube test defers to tube_f64.
 constexpr float kTieBand = 1e-5f;
 
-// Near pairs: TPT targets against the two sources of a payload pair, scalar,
-// with the tube test (FP64 re-decision of near-ties) and the series form of
-// g when any lane of the warp has kappa rho < 0.5.
-template <int TPT>
-__device__ __forceinline__ void near_pair(const float3 (&X)[TPT], const float2 (&nx)[TPT], const float2 (&ny)[TPT],
-                                          const float2 (&nz)[TPT], const float4& A, const float4& B,
-                                          const float4& C, const float4& D, const F32Consts& k, float2 (&t1)[TPT],
-                                          float2 (&t2)[TPT], const Geo64& g64, int64_t gi0, int qstride, int64_t j,
-                                          int64_t N)
+// Near pairs, packed over the two sources of a payload pair (one target):
+// pair_far2's formula with, per lane, g from its series where kappa rho <
+// 0.5 (f = 1 - E = g + E x there) and the tube test (Sec. 2.2.1): a
+// regularised pair keeps only K12's tube value, by selects on rho^-3 and on
+// the 1/rho factor of the first sum.  rho^2 is kept >= 1e-12, so that
+// coincident nodes (the self pair among them, always in the tube) leave
+// every product finite.  When a test lies within kTieBand of a threshold,
+// both sources are decided again in FP64 (tube_f64), which the FP32 test
+// agrees with outside the band.  i: the target's node index, j: the first
+// source's.
+__device__ __forceinline__ void pair_near2(float2 Xx, float2 Xy, float2 Xz, float2 nx, float2 ny, float2 nz,
+                                           const float4& A, const float4& B, const float4& C, const float4& D,
+                                           const FarConsts& c, const F32Consts& k, float2& t1, float2& t2,
+                                           const Geo64& g64, int64_t i, int64_t j, int64_t N)
 {
-    const float yx[2] = {A.x, A.y}, yy[2] = {A.z, A.w}, yz[2] = {B.x, B.y}, bb[2] = {B.z, B.w};
-    const float mx[2] = {C.x, C.y}, my[2] = {C.z, C.w}, mz[2] = {D.x, D.y};
-    float rr[TPT][2], sx[TPT][2], sa[TPT][2], ca[TPT][2], inv[TPT][2], x[TPT][2], E[TPT][2];
-    bool tube[TPT][2];
-    bool need = false;
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float rx = X[q].x + yx[e], ry = X[q].y + yy[e], rz = X[q].z + yz[e];
-            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            rr[q][e] = r2;
-            sx[q][e] = fmaf(rx, nx[q].x, fmaf(ry, ny[q].x, rz * nz[q].x));
-            sa[q][e] = fmaf(rx, mx[e], fmaf(ry, my[e], rz * mz[e]));
-            ca[q][e] = fmaf(nx[q].x, mx[e], fmaf(ny[q].x, my[e], nz[q].x * mz[e]));
-            const float rp2 = fmaf(-sx[q][e], sx[q][e], r2);
-            tube[q][e] = (rp2 < k.tau2) & (r2 < k.four_tau2);
-            const bool tie = (fabsf(rp2 - k.tau2) < kTieBand * k.tau2) |
-                             (fabsf(r2 - k.four_tau2) < kTieBand * k.four_tau2);
-            const int64_t i = gi0 + (int64_t)q * qstride;
-            if (tie && g64.x != nullptr && i < N && j + e < N)
-                tube[q][e] = tube_f64(g64, i, j + e, k.tau2_d, k.four_tau2_d);
-            const float rrs = fmaxf(r2, 1.0e-30f);
-            inv[q][e] = ptx::rsqrt_approx(rrs);
-            const float rho = rrs * inv[q][e];
-            x[q][e] = k.kappa * rho;
-            E[q][e] = ptx::ex2_approx(rho * k.kl2e);
-            need |= (x[q][e] < 0.5f);
-        }
+    const float2 rx = __fadd2_rn(Xx, make_float2(A.x, A.y));
+    const float2 ry = __fadd2_rn(Xy, make_float2(A.z, A.w));
+    const float2 rz = __fadd2_rn(Xz, make_float2(B.x, B.y));
+    const float2 b = make_float2(B.z, B.w);
+    const float2 mx = make_float2(C.x, C.y), my = make_float2(C.z, C.w), mz = make_float2(D.x, D.y);
+    float2 rr = __fmul2_rn(rx, rx);
+    rr = __ffma2_rn(ry, ry, rr);
+    rr = __ffma2_rn(rz, rz, rr);
+    float2 sx = __fmul2_rn(rx, nx);
+    sx = __ffma2_rn(ry, ny, sx);
+    sx = __ffma2_rn(rz, nz, sx);
+    float2 sa = __fmul2_rn(rx, mx);
+    sa = __ffma2_rn(ry, my, sa);
+    sa = __ffma2_rn(rz, mz, sa);
+    float2 ca = __fmul2_rn(nx, mx);
+    ca = __ffma2_rn(ny, my, ca);
+    ca = __ffma2_rn(nz, mz, ca);
+    const float2 rp = __ffma2_rn(__fmul2_rn(sx, c.neg1), sx, rr);
+    bool t0 = (rp.x < k.tau2) & (rr.x < k.four_tau2), t1b = (rp.y < k.tau2) & (rr.y < k.four_tau2);
+    const float bt = kTieBand * k.tau2, b4 = kTieBand * k.four_tau2;
+    const bool tie = (fabsf(rp.x - k.tau2) < bt) | (fabsf(rp.y - k.tau2) < bt) | (fabsf(rr.x - k.four_tau2) < b4) |
+                     (fabsf(rr.y - k.four_tau2) < b4);
+    if (tie && g64.x != nullptr && i < N) {
+        if (j < N) t0 = tube_f64(g64, i, j, k.tau2_d, k.four_tau2_d);
+        if (j + 1 < N) t1b = tube_f64(g64, i, j + 1, k.tau2_d, k.four_tau2_d);
     }
-    const bool series = __any_sync(0xffffffffu, need);
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float xe = x[q][e];
-            const float Ex = E[q][e] * xe;
-            float f = 1.0f - E[q][e];
-            float g = f - Ex;
-            if (series && xe < 0.5f) {
-                g = g_series(xe);
-                f = g + Ex;
-            }
-            const float hh = fmaf(3.0f, g, -Ex * xe);
-            const float iv = inv[q][e];
-            const float inv2 = iv * iv;
-            const float i3 = tube[q][e] ? 0.0f : inv2 * iv;
-            const float Q = tube[q][e] ? k.k12t : f * iv;
-            const float u1 = fmaf(k.th1, g, k.omth1);
-            const float u2 = fmaf(k.th2, g, k.omth2);
-            const float d1 = fmaf(i3 * u1, sa[q][e], -Q * bb[e]);
-            const float v = fmaf(u2, bb[e], -(hh * inv2) * sa[q][e]);
-            const float d2 = i3 * fmaf(g, ca[q][e], sx[q][e] * v);
-            if (e == 0) {
-                t1[q].x += d1;
-                t2[q].x += d2;
-            } else {
-                t1[q].y += d1;
-                t2[q].y += d2;
-            }
-        }
+    const float2 rrs = make_float2(fmaxf(rr.x, 1.0e-12f), fmaxf(rr.y, 1.0e-12f));
+    const float2 inv = make_float2(ptx::rsqrt_approx(rrs.x), ptx::rsqrt_approx(rrs.y));
+    const float2 rho = __fmul2_rn(rrs, inv);
+    const float2 ea = __fmul2_rn(rho, c.kl2e);
+    const float2 xn = __fmul2_rn(rho, c.nkappa);
+    const float2 E = make_float2(ptx::ex2_approx(ea.x), ptx::ex2_approx(ea.y));
+    const float2 En = __fmul2_rn(E, xn);
+    float2 fn = __fadd2_rn(E, c.neg1);
+    float2 g = __ffma2_rn(fn, c.neg1, En);
+    if (-xn.x < 0.5f) {  // kappa rho < 0.5: series of g, fn = -(g + E x)
+        g.x = g_series(-xn.x);
+        fn.x = En.x - g.x;
     }
+    if (-xn.y < 0.5f) {
+        g.y = g_series(-xn.y);
+        fn.y = En.y - g.y;
+    }
+    const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));
+    const float2 inv2 = __fmul2_rn(inv, inv);
+    const float2 P3 = __fmul2_rn(inv2, inv);
+    const float2 P = make_float2(t0 ? 0.0f : P3.x, t1b ? 0.0f : P3.y);
+    const float2 qf0 = __fmul2_rn(fn, inv);
+    const float2 qf = make_float2(t0 ? -k.k12t : qf0.x, t1b ? -k.k12t : qf0.y);
+    const float2 u1 = __ffma2_rn(c.th1, g, c.omth1);
+    const float2 u2 = __ffma2_rn(c.th2, g, c.omth2);
+    t1 = __ffma2_rn(P, __fmul2_rn(u1, sa), t1);
+    t1 = __ffma2_rn(qf, b, t1);
+    const float2 v = __ffma2_rn(__fmul2_rn(hn, inv2), sa, __fmul2_rn(u2, b));
+    const float2 w = __ffma2_rn(sx, v, __fmul2_rn(g, ca));
+    t2 = __ffma2_rn(P, w, t2);
 }
 
 // Per-thread target slots: position in the target block's frame and the
@@ -333,12 +332,23 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 for (int q = 0; q < TPT; ++q)
                     pair_far2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, t1[q], t2[q]);
             }
-        } else {
+        } else {  // near chunk: the packed near formula, tube test per lane
+            float2 Xx[TPT], Xy[TPT], Xz[TPT];
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+                Xx[q] = f2(X[q].x);
+                Xy[q] = f2(X[q].y);
+                Xz[q] = f2(X[q].z);
+            }
+            const int64_t jc = j0 + (int64_t)c * kChunk;
+#pragma unroll 1
             for (int p = 0; p < kPairsPerChunk; ++p) {
                 const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
                 const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
-                near_pair<TPT>(X, T.nx, T.ny, T.nz, A, B, C, D, k, t1, t2, g64, gi0, qstride,
-                               j0 + (int64_t)c * kChunk + 2 * p, N);
+#pragma unroll
+                for (int q = 0; q < TPT; ++q)
+                    pair_near2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, k, t1[q], t2[q], g64,
+                               gi0 + (int64_t)q * qstride, jc + 2 * p, N);
             }
         }
 #pragma unroll
