@@ -485,7 +485,8 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
         }
         if (!any) continue;
         float3 X[TPT];
-        bool far = k.rule0 != 0;
+        bool far = k.rule0 != 0, allact = true;
+        bool farq[TPT];  // per slot (one target block per warp and slot: warp-uniform)
         {
             const float4 mh = sfrm[2 * c];
             const float4 ml = sfrm[2 * c + 1];
@@ -498,7 +499,9 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                 const float dz = (th.z - mh.z) + (tl.z - ml.z);
                 X[q] = make_float3(T.x[q].x + dx, T.x[q].y + dy, T.x[q].z + dz);
                 const float lim = k.far_dist + th.w + mh.w;
-                far = far && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim);
+                farq[q] = (k.rule0 != 0) && (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim);
+                far = far && farq[q];
+                allact = allact && act[q];
             }
         }
         float2 t1[TPT], t2[TPT];
@@ -526,7 +529,7 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                 const int hl = lane & (P - 1);
                 const int nxt = (hl + 1) & (P - 1);
                 float2 nR1 = make_float2(0.0f, 0.0f), R2 = make_float2(0.0f, 0.0f);
-                if (far) {
+                if (far && allact) {
 #pragma unroll UNR
                     for (int step = 0; step < P; ++step) {
                         const int p = (hl + step) & (P - 1);
@@ -541,17 +544,23 @@ __device__ __forceinline__ void tile_sums_sym(const SymTargets<TPT>& T, const fl
                         R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
                         R2.y = __shfl_sync(0xffffffffu, R2.y, nxt, P);
                     }
-                } else {
+                } else {  // a near slot or an inactive one: per slot (uniform branches)
                     const int64_t jc = j0 + (int64_t)c * kChunk;
-#pragma unroll 1
+#pragma unroll 2
                     for (int step = 0; step < P; ++step) {
                         const int p = (hl + step) & (P - 1);
                         const float4 A = cb[p], B = cb[P + p], C = cb[2 * P + p], D = cb[3 * P + p];
 #pragma unroll
-                        for (int q = 0; q < TPT; ++q)
-                            pair_near_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B,
-                                              C, D, fc, k, t1[q], t2[q], nR1, R2, g64, gi0 + (int64_t)q * qstride,
-                                              jc + 2 * p, N);
+                        for (int q = 0; q < TPT; ++q) {
+                            if (!act[q]) continue;
+                            if (TPT > 1 && farq[q])  // (one slot: this loop runs near chunks only)
+                                pair_far_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A, B,
+                                                 C, D, fc, t1[q], t2[q], nR1, R2);
+                            else
+                                pair_near_sym_acc(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], aq[q], nbq[q], A,
+                                                  B, C, D, fc, k, t1[q], t2[q], nR1, R2, g64,
+                                                  gi0 + (int64_t)q * qstride, jc + 2 * p, N);
+                        }
                         nR1.x = __shfl_sync(0xffffffffu, nR1.x, nxt, P);
                         nR1.y = __shfl_sync(0xffffffffu, nR1.y, nxt, P);
                         R2.x = __shfl_sync(0xffffffffu, R2.x, nxt, P);
