@@ -457,8 +457,11 @@ __device__ __forceinline__ void warp_sum4_add(float v0, float v1, float v2, floa
 // reverse sums of every source of the tile go to racc[.] (first block) and
 // racc[sym_rev_off(ROT) + .] (second block) by shared-memory atomics.  ROT:
 // the rotation scheme, far chunks by pair_far_sym_acc and near chunks by
-// pair_near_sym_acc; otherwise the warp reduction, near chunks by the scalar
-// near_pair_sym.  UNR: unroll depth of the rotation loop.  Measured on the 80k-node sphere:
+// pair_near_sym_acc, decided per target slot (each slot's 32 targets are one
+// block of the warp, so the choice is warp-uniform; inactive slots are
+// skipped there); otherwise the warp reduction, near chunks by the scalar
+// near_pair_sym.  UNR: unroll depth of the rotation loop over far chunks.
+// Measured on the 80k-node sphere (before the packed near path):
 // two targets per thread run fastest at 1 (5.65 ms; 5.72 at 2, spills at 4),
 // one target per thread at 4 (5.86 ms; 6.11 at 2, 6.22 at 1).
 template <int TPT, bool ROT, int UNR = 2>
