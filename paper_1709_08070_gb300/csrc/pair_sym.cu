@@ -296,39 +296,56 @@ __global__ void pack_sym_kernel(const float4* __restrict__ pos, const float4* __
 }
 
 // y = Lambda p + (1/(4 pi)) (forward partials of the row + reverse sums).
-__global__ void fixup_sym_kernel(const double* __restrict__ part, SymSchedule s, int ttile, int64_t N, int64_t n_pad,
-                                 double lambda1, double lambda2, VecRef in, OutRef out,
-                                 const double* __restrict__ yrev, const int* __restrict__ skip)
+// kFixParts threads per target, each summing a fixed share of the row's slots
+// (a row near the end of the step sequence has one slot per small segment),
+// then the shares in a fixed order: deterministic.  A block holds kFixTargets
+// consecutive targets (a divisor of every target tile, so one row) for each
+// share, so that a warp's loads of one slot are contiguous.
+constexpr int kFixParts = 4, kFixTargets = 64;
+__global__ void __launch_bounds__(kFixParts * kFixTargets)
+    fixup_sym_kernel(const double* __restrict__ part, SymSchedule s, int ttile, int64_t N, int64_t n_pad,
+                     double lambda1, double lambda2, VecRef in, OutRef out, const double* __restrict__ yrev,
+                     const int* __restrict__ skip)
 {
     if (skip != nullptr && *skip) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    __shared__ double sh1[kFixParts][kFixTargets], sh2[kFixParts][kFixTargets];
+    const int tl = threadIdx.x % kFixTargets, pr = threadIdx.x / kFixTargets;
+    const int64_t i = (int64_t)blockIdx.x * kFixTargets + tl;
+    double a1 = 0.0, a2 = 0.0;
+    if (i < N) {
+        const int64_t t = i / ttile;
+        const int64_t l = i - t * ttile;
+        int64_t start, rho;
+        sym_row_start(s, t, start, rho);
+        const int64_t c0 = sym_seg_of(s, start);
+        const int64_t n = sym_seg_of(s, start + sym_row_len(s, t) - 1) - c0 + 1;
+        const int64_t q0 = c0 + (n * pr) / kFixParts, q1 = c0 + (n * (pr + 1)) / kFixParts;
+        // four slots per round with their loads independent (the row's slots are
+        // consecutive, 2 ttile doubles apart)
+        const int64_t ts = 2 * (int64_t)ttile;
+        const double* src = part + (q0 + rho) * ts + l;
+        int64_t c = q0;
+        for (; c + 4 <= q1; c += 4, src += 4 * ts) {
+            const double x0 = src[0], x1 = src[ts], x2 = src[2 * ts], x3 = src[3 * ts];
+            const double y0 = src[ttile], y1 = src[ts + ttile], y2 = src[2 * ts + ttile], y3 = src[3 * ts + ttile];
+            a1 += (x0 + x1) + (x2 + x3);
+            a2 += (y0 + y1) + (y2 + y3);
+        }
+        for (; c < q1; ++c, src += ts) {
+            a1 += src[0];
+            a2 += src[ttile];
+        }
+    }
+    sh1[pr][tl] = a1;
+    sh2[pr][tl] = a2;
+    __syncthreads();
+    if (pr != 0 || i >= N) return;
     const double* p = in.base + (in.kidx ? (int64_t)(*in.kidx + in.koff) * in.stride : 0);
     double* y = out.base + (out.kidx ? (int64_t)(*out.kidx + out.koff) * out.stride : 0);
-    const int64_t t = i / ttile;
-    const int64_t l = i - t * ttile;
-    int64_t start, rho;
-    sym_row_start(s, t, start, rho);
-    const int64_t c0 = sym_seg_of(s, start);
-    const int64_t c1 = sym_seg_of(s, start + sym_row_len(s, t) - 1);
-    double a1 = yrev[i], a2 = yrev[n_pad + i];
-    // four slots per round with their loads independent (the row's slots are
-    // consecutive, 2 ttile doubles apart); a fixed order, so deterministic
-    const double* src = part + (c0 + rho) * 2 * ttile + l;
-    const int64_t ts = 2 * (int64_t)ttile;
-    int64_t c = c0;
-    for (; c + 3 <= c1; c += 4, src += 4 * ts) {
-        const double x0 = src[0], x1 = src[ts], x2 = src[2 * ts], x3 = src[3 * ts];
-        const double y0 = src[ttile], y1 = src[ts + ttile], y2 = src[2 * ts + ttile], y3 = src[3 * ts + ttile];
-        a1 += (x0 + x1) + (x2 + x3);
-        a2 += (y0 + y1) + (y2 + y3);
-    }
-    for (; c <= c1; ++c, src += ts) {
-        a1 += src[0];
-        a2 += src[ttile];
-    }
-    y[i] = lambda1 * p[i] + kInv4Pi * a1;
-    y[N + i] = lambda2 * p[N + i] + kInv4Pi * a2;
+    const double f1 = yrev[i] + ((sh1[0][tl] + sh1[1][tl]) + (sh1[2][tl] + sh1[3][tl]));
+    const double f2 = yrev[n_pad + i] + ((sh2[0][tl] + sh2[1][tl]) + (sh2[2][tl] + sh2[3][tl]));
+    y[i] = lambda1 * p[i] + kInv4Pi * f1;
+    y[N + i] = lambda2 * p[N + i] + kInv4Pi * f2;
 }
 
 // ------------------------------------------------------------------ host side
@@ -460,8 +477,8 @@ ibim_status sym_fixup_tiles(ibim_ctx* c, int ttile, int grid_cap, const PairCons
                             const int* d_skip)
 {
     const SymSchedule s = make_sym_schedule(c->N, ttile, grid_cap);
-    const int bs = 256;
-    fixup_sym_kernel<<<(unsigned)((c->N + bs - 1) / bs), bs, 0, c->stream>>>(
+    static_assert(kFixParts == 4 && kF32STile % kFixTargets == 0, "fixup shares");
+    fixup_sym_kernel<<<(unsigned)((c->N + kFixTargets - 1) / kFixTargets), kFixParts * kFixTargets, 0, c->stream>>>(
         c->d_part, s, ttile, c->N, padded_nodes(c->N), k.lambda1, k.lambda2, in, out, c->d_yrev, d_skip);
     count_launch(c);
     IBIM_CUDA(cudaGetLastError());
