@@ -145,3 +145,30 @@ def test_kirkwood_sphere_sampled_rows_every_variant():
         _run_all(ctx, P, _to_gpu(p, perm, N), check)
     finally:
         ctx.close()
+
+
+def test_coincident_nodes_every_variant():
+    """A caller cloud with coincident nodes (distinct nodes at one position,
+    as grid nodes on one normal line project to one surface point): those
+    pairs lie in the tube at rho = 0, in the same and in different chunks.
+    Every operator configuration against the oracle on every row."""
+    xs, nr, w = inputs.sphere_cloud(600, radius=3.0, seed=77)
+    dup = np.arange(0, 600, 37)
+    xs2 = np.concatenate([xs, xs[dup], xs[dup[:4]]])
+    nr2 = np.concatenate([nr, nr[dup], nr[dup[:4]]])
+    w2 = np.concatenate([w, 0.5 * w[dup], 0.25 * w[dup[:4]]])
+    ctx = ibim.Context.from_nodes(xs2, nr2, w2, h=0.25)
+    try:
+        N = ctx.N
+        assert N == xs2.shape[0]
+        P = ibim.Phys(2.0, 80.0, 0.1257, 0.25, 0)
+        Po = oracle.Phys(2.0, 80.0, 0.1257, 0.25, 0)
+        p = inputs.random_vector(2 * N, seed=78)
+        yo = oracle.matvec(xs2, nr2, w2, Po, p)
+
+        def check(y, prec, what):
+            _assert_blocks(y[:N], y[N:], yo[:N], yo[N:], TOL[prec], "coincident N %d %s" % (N, what))
+
+        _run_all(ctx, P, p, check)
+    finally:
+        ctx.close()
