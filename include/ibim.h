@@ -243,8 +243,9 @@ typedef struct {
  * FP64-accurate residual misses tol, the iteration solves the correction
  * equation A e = r from e = 0 (restart residuals r - A e, noise relative to
  * |r|) and adds e before the next check (iterative refinement).  A cycle that
- * converges by its own estimate while the restart residual does not (the FP32
- * operator's accuracy, about 1e-8 of |A p|) leads to the check at once.
+ * converges by its own estimate leads to the FP64-accurate check at once (no
+ * FP32 restart residual first: it could only confirm the estimate or show the
+ * FP32 operator's accuracy, about 1e-8 of |A p|).
  * d_p: device 2N doubles; start vector on entry when opts->start == 3,
  * solution [psi; psin] on exit.  Needs charges.  Returns IBIM_ERR_NOT_CONVERGED
  * (info filled) when maxit is reached above tol.

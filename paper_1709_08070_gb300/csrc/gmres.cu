@@ -574,11 +574,12 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
     // residuals g - A_in x of the whole system would pull the iterate back to
     // A_in's own solution, which misses the tolerance whenever A_in differs
     // from A_out by more than the inner target, e.g. a treecode operator.)
-    // A cycle that meets the inner target by its own estimate while the next
-    // restart residual does not has reached the inner operator's accuracy
-    // floor (the FP32 operator is linear only to about 1e-8 of |A x|): the
-    // check follows at once instead of further cycles that cannot go lower.
-    bool check = false, refining = false, at_floor = false;
+    // A cycle that meets the inner target by its own estimate is followed by
+    // the check at once: a restart residual with A_in could only confirm the
+    // estimate (then the check follows) or show A_in's accuracy floor (the
+    // FP32 operator is linear only to about 1e-8 of |A x|; further cycles
+    // could not go lower, so the check follows as well).
+    bool check = false, refining = false;
     while (!converged) {
         const int kmax = std::min(m, o.maxit - iters);
         const int prec_r = (check || kmax <= 0) ? prec_out : prec_in;
@@ -598,13 +599,11 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
             converged = true;
             break;
         }
-        if (prec_r != prec_out && (beta <= inner_target || at_floor)) {
+        if (prec_r != prec_out && beta <= inner_target) {
             check = true;
-            at_floor = false;
             continue;
         }
         check = false;
-        at_floor = false;
         if (kmax <= 0) break;
         if (prec_r != prec_in) {  // failed check: the cycle below starts on r = g - A_out x
             IBIM_CUDA(cudaMemcpyAsync(w->xb, w->x, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
@@ -617,7 +616,7 @@ ibim_status gmres_solve(ibim_ctx* c, const ibim_phys& p, const ibim_solve_opts& 
         IBIM_TRY(run_cycle(c, k, prec_in, use_graph, &steps, &conv));
         iters += steps;
         ++cycles;
-        at_floor = prec_out != prec_in && conv != 0;
+        check = prec_out != prec_in && conv != 0;
         info->matvecs_f32 += (prec_in == IBIM_F32C || prec_in == IBIM_F32T) ? steps : 0;
         info->matvecs_f64 += (prec_in == IBIM_F64 || prec_in == IBIM_FF) ? steps : 0;
         if (steps > 0) {
