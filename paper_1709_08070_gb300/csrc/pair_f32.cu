@@ -33,9 +33,10 @@
 // regularisation tube (tube rule 0) and the cancellation in g is harmless, so
 // the chunk runs a branch-free loop with no tube masks on packed float2
 // operands, one lane per source of a payload pair (the FP32 pipe then does
-// two interactions per issued instruction).  Otherwise every pair gets the
-// tube test and, when any lane of the warp has x < 0.5, g from its Taylor
-// series (from the exponential series).  The decision is warp-uniform.
+// two interactions per issued instruction).  Otherwise the chunk runs the
+// same packed formula with, per lane, the tube test (selects on rho^-3 and the
+// 1/rho factor) and, where x < 0.5, g from its Taylor series (pair_near2).
+// The decision is warp-uniform.
 //
 // Accumulation: per target the two sums run in FP32 over one 32-source chunk
 // (fused into the FMAs, even and odd sources apart), each chunk sum is
