@@ -107,7 +107,7 @@ def test_trained_start_saves_gmres_iterations():
     loss = net.train(1500, batch_nodes=4096, lr=2e-3)
     print("warm-start training loss %.3e -> %.3e" % (loss0, loss))
     assert loss < 0.5 * loss0
-    saved = []
+    saved, zero = [], []
     for s in range(4):
         ctx, P = _molecule("sphere" if s % 2 else "globule", 5000 + s)
         d0 = torch.empty(2 * ctx.N, dtype=torch.float64, device="cuda")
@@ -118,7 +118,9 @@ def test_trained_start_saves_gmres_iterations():
         assert i0["converged"] and i1["converged"]
         assert abs(i1["gpol"] - i0["gpol"]) <= 1e-4 * abs(i0["gpol"])
         saved.append(i0["iters"] - i1["iters"])
+        zero.append(i0["iters"])
         print("held-out N=%d iters zero %d learned %d" % (ctx.N, i0["iters"], i1["iters"]))
         ctx.close()
-    assert sum(saved) > 0 and min(saved) >= 0, saved
+    # measured: 21 of 109 iterations saved (19 %) over these four molecules
+    assert sum(saved) >= 0.1 * sum(zero) and min(saved) >= 0, (saved, zero)
     net.close()
