@@ -294,6 +294,9 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
         float3 X[TPT];
         const bool forced = LIST && force_far;
         bool far = (have_frames && k.rule0) || forced;
+        bool farq[TPT];  // per slot (one target block per warp and slot: warp-uniform)
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) farq[q] = far;
         if (have_frames) {
             const float4 mh = sfrm[2 * c];
             const float4 ml = sfrm[2 * c + 1];
@@ -306,7 +309,8 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 const float dz = (th.z - mh.z) + (tl.z - ml.z);
                 X[q] = make_float3(T.x[q].x + dx, T.x[q].y + dy, T.x[q].z + dz);
                 const float lim = k.far_dist + th.w + mh.w;
-                far = far && (forced || (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim));
+                farq[q] = farq[q] && (forced || (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= lim * lim));
+                far = far && farq[q];
             }
         } else {
 #pragma unroll
@@ -332,7 +336,7 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 for (int q = 0; q < TPT; ++q)
                     pair_far2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, t1[q], t2[q]);
             }
-        } else {  // near chunk: the packed near formula, tube test per lane
+        } else {  // near chunk: the packed near formula (tube test per lane) for the near slots
             float2 Xx[TPT], Xy[TPT], Xz[TPT];
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -346,9 +350,13 @@ __device__ __forceinline__ void tile_sums(const Targets<TPT>& T, const float4* t
                 const float4 A = cb[kPairF4 * p], B = cb[kPairF4 * p + 1];
                 const float4 C = cb[kPairF4 * p + 2], D = cb[kPairF4 * p + 3];
 #pragma unroll
-                for (int q = 0; q < TPT; ++q)
-                    pair_near2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, k, t1[q], t2[q], g64,
-                               gi0 + (int64_t)q * qstride, jc + 2 * p, N);
+                for (int q = 0; q < TPT; ++q) {
+                    if (TPT > 1 && farq[q])  // (one slot: this loop runs near chunks only)
+                        pair_far2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, t1[q], t2[q]);
+                    else
+                        pair_near2(Xx[q], Xy[q], Xz[q], T.nx[q], T.ny[q], T.nz[q], A, B, C, D, fc, k, t1[q], t2[q],
+                                   g64, gi0 + (int64_t)q * qstride, jc + 2 * p, N);
+                }
             }
         }
 #pragma unroll
