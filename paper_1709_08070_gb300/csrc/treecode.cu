@@ -501,7 +501,7 @@ __device__ __forceinline__ void pair_field2(float2 Xx, float2 Xy, float2 Xz, con
     const float2 fn = __fadd2_rn(E, c.neg1);               // -(1 - E)
     const float2 g = __ffma2_rn(fn, c.neg1, En);           // 1 - A
     const float2 hn = __ffma2_rn(g, c.neg3, __fmul2_rn(En, xn));  // -(3 - B)
-    const float2 inv2 = make_float2(ptx::rcp_approx(rr.x), ptx::rcp_approx(rr.y));
+    const float2 inv2 = __fmul2_rn(inv, inv);
     const float2 P = __fmul2_rn(inv2, inv);
     const float2 u1 = __ffma2_rn(c.th1, g, c.omth1);
     const float2 u2 = __ffma2_rn(c.th2, g, c.omth2);
