@@ -150,6 +150,14 @@ def test_treecode_on_built_sphere_operator_and_solve(interp):
         assert ic["converged"] and res < 1e-6 and abs(ic["relres"] - res) <= 1e-9
         assert ic["matvecs_f64"] <= 4 and ic["iters"] <= 3 * it["iters"]
         assert abs(ic["gpol"] - i32["gpol"]) < 2e-6 * abs(i32["gpol"])
+    # far below the treecode's own error: each refinement step gains about
+    # that error's factor, so a few checks reach it
+    ic = ctx.solve(P, d, precision=ibim.IBIM_F32T, certify=1, tol=1e-8, restart=64, maxit=400)
+    ctx.matvec(P, d, y64, precision=ibim.IBIM_F64)
+    res = float(torch.linalg.norm(g - y64)) / gn
+    print("certified treecode solve to 1e-8: iterations %d, FP64-accurate applications %d, direct FP64 %.3e"
+          % (ic["iters"], ic["matvecs_f64"], res))
+    assert ic["converged"] and res < 1e-8 and abs(ic["relres"] - res) <= 1e-11 and ic["matvecs_f64"] <= 5
     ctx.close()
 
 
